@@ -1,0 +1,200 @@
+"""Pins for the CPU oracle, independent of the oracle itself.
+
+Each pin checks the oracle against something the paper or the mathematics
+fixes: the worked examples of Section 2.1/2.2 (tests/golden/), closed forms,
+brute force against Python's own bytes ordering, invariants (permutation,
+ISA[SA[j]] = j, BWT inversion) and a textbook BWT. A planted-mutant build of
+the oracle for each plausible mistake must fail at least one pin.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from conftest import ints, read_golden
+
+
+def py_sa(t: bytes):
+    """Suffix order by Python's bytes comparison (lexicographic, unsigned,
+    a proper prefix first): an implementation independent of oracle.c."""
+    return sorted(range(len(t)), key=lambda i: t[i:])
+
+
+# ---- pin functions: each returns a list of failure messages -------------
+
+def pin_examples(o):
+    bad = []
+    g = read_golden("ex1_ex2_bdacbdacb.txt")
+    t, sa = g["text"].encode(), ints(g["sa"])
+    if list(o.naive_sa(t)) != sa:
+        bad.append("Ex1 naive")
+    for h0 in (1, 2, 3):
+        if list(o.pd_sa(t, h0=h0)[0]) != sa:
+            bad.append(f"Ex1 pd h0={h0}")
+    _, isa, rounds, trace = o.pd_sa(t, h0=int(g["h0"]), trace_cap=8)
+    want = [ints(g[f"names_{k}"]) for k in range(3)]
+    if rounds != int(g["rounds"]) or [list(r) for r in trace] != want:
+        bad.append(f"Ex2 names {trace.tolist()} rounds {rounds}")
+    if list(isa) != want[-1]:
+        bad.append("Ex2 final ISA")
+    g3 = read_golden("ex3_dbacbacbd.txt")
+    t3 = g3["text"].encode()
+    if list(o.naive_sa(t3)) != ints(g3["sa"]) or list(o.pd_sa(t3)[0]) != ints(g3["sa"]):
+        bad.append("Ex3")
+    sub = bytes(ints(g3["sub_text_bytes"]))
+    if list(o.naive_sa(sub)) != ints(g3["sub_sa"]) or list(o.pd_sa(sub)[0]) != ints(g3["sub_sa"]):
+        bad.append("Ex3 sub-problem")
+    return bad
+
+
+def pin_closed_forms(o):
+    bad = []
+    for n in list(range(0, 40)) + [257, 1000]:
+        t = b"a" * n
+        want = list(range(n - 1, -1, -1))  # a^n: shorter suffixes first
+        for name, sa in (("naive", o.naive_sa(t)), ("pd", o.pd_sa(t)[0]),
+                         ("pd2", o.pd_sa(t, h0=2)[0])):
+            if list(sa) != want:
+                bad.append(f"a^{n} {name}")
+                break
+    for m in (1, 2, 3, 10, 50):
+        t = b"ab" * m
+        want = list(range(2 * m - 2, -1, -2)) + list(range(2 * m - 1, 0, -2))
+        if list(o.naive_sa(t)) != want or list(o.pd_sa(t)[0]) != want:
+            bad.append(f"(ab)^{m}")
+    rng = np.random.default_rng(7)
+    for n in (1, 2, 17, 256):
+        t = rng.permutation(256)[:n].astype(np.uint8)
+        want = list(np.argsort(t, kind="stable"))  # all distinct: by first char
+        if list(o.naive_sa(t)) != want or list(o.pd_sa(t)[0]) != want:
+            bad.append(f"distinct n={n}")
+    return bad
+
+
+def pin_bruteforce(o, max_ab=12, max_4=6):
+    bad = []
+    for alpha, top in ((b"ab", max_ab), (bytes([0, 1, 2, 255]), max_4)):
+        for L in range(1, top + 1):
+            for tup in itertools.product(alpha, repeat=L):
+                t = bytes(tup)
+                want = py_sa(t)
+                if list(o.naive_sa(t)) != want:
+                    bad.append(f"naive {t!r}")
+                for h0 in (1, 2):
+                    if list(o.pd_sa(t, h0=h0)[0]) != want:
+                        bad.append(f"pd h0={h0} {t!r}")
+                if bad:
+                    return bad
+    return bad
+
+
+def pin_random(o):
+    bad = []
+    for seed in range(6):
+        for recipe, n in (("dna", 3000), ("zipf_repeats", 4096), ("markov", 5000),
+                          ("bytes", 2000), ("zipf", 3000)):
+            t = gen.text(recipe, 100 + seed, n)
+            tb = t.tobytes()
+            want = py_sa(tb) if n <= 3000 else list(o.naive_sa(t))
+            sa, isa, _, _ = o.pd_sa(t)
+            if list(sa) != want:
+                bad.append(f"pd {recipe} seed {seed}")
+            if not np.array_equal(isa[sa], np.arange(n, dtype=np.uint32)):
+                bad.append(f"ISA[SA] {recipe}")
+    return bad
+
+
+def pin_checker(o):
+    bad = []
+    for seed in range(4):
+        t = gen.text("dna", 500 + seed, 600).tobytes()
+        good = np.array(py_sa(t), dtype=np.uint32)
+        if o.check_sa(t, good)[0] != 0:
+            bad.append("rejects a correct SA")
+        for j in (0, 1, 299, 598):
+            s = good.copy()
+            s[j], s[j + 1] = s[j + 1], s[j]
+            if o.check_sa(t, s)[0] == 0:
+                bad.append(f"accepts adjacent swap at {j}")
+        s = good.copy()
+        s[10] = s[20]
+        if o.check_sa(t, s)[0] != 1:
+            bad.append("accepts a duplicate")
+        s = good.copy()
+        s[5] = 600
+        if o.check_sa(t, s)[0] != 1:
+            bad.append("accepts out of range")
+        s = good.copy()
+        s[100], s[400] = s[400], s[100]
+        if o.check_sa(t, s)[0] == 0:
+            bad.append("accepts a far swap")
+    t = b"aaaa"
+    if o.check_sa(t, np.array([0, 1, 2, 3], dtype=np.uint32))[0] == 0:
+        bad.append("accepts a^4 in text order")
+    if o.check_sa(t, np.array([3, 2, 1, 0], dtype=np.uint32))[0] != 0:
+        bad.append("rejects a^4")
+    return bad
+
+
+def pin_bwt(o):
+    bad = []
+    t = b"banana"  # textbook: BWT(banana$) = annb$aa
+    b, p = o.bwt(t, np.array(py_sa(t), dtype=np.uint32))
+    if bytes(b) != b"annb\x00aa" or p != 4:
+        bad.append(f"banana {bytes(b)!r} {p}")
+    for recipe in ("dna", "zipf_repeats", "markov", "bytes"):
+        t = gen.text(recipe, 9, 4096)
+        sa = o.pd_sa(t)[0]
+        b, p = o.bwt(t, sa)
+        try:
+            if not np.array_equal(o.bwt_invert(b, p), t):
+                bad.append(f"roundtrip {recipe}")
+        except ValueError:
+            bad.append(f"roundtrip {recipe} failed")
+    return bad
+
+
+def pin_rank(o):
+    bad = []
+    t = gen.text("zipf_repeats", 3, 2048)
+    isa = np.empty(2048, dtype=np.int64)
+    isa[np.array(py_sa(t.tobytes()))] = np.arange(2048)
+    for i in (0, 1, 77, 1024, 2047):
+        if o.suffix_rank(t, i) != isa[i]:
+            bad.append(f"rank {i}")
+    return bad
+
+
+PINS = [pin_examples, pin_closed_forms, pin_bruteforce, pin_random, pin_checker,
+        pin_bwt, pin_rank]
+
+
+@pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
+def test_oracle_pins(orc, pin):
+    assert pin(orc) == []
+
+
+@pytest.mark.parametrize("mutant", oracle.MUTANTS)
+def test_every_planted_mistake_fails_a_pin(mutant):
+    m = oracle.Oracle(mutant)
+    failed = []
+    for pin in PINS:
+        if pin is pin_bruteforce:
+            res = pin(m, max_ab=8, max_4=4)
+        else:
+            res = pin(m)
+        if res:
+            failed.append(pin.__name__)
+            break
+    assert failed, f"mutant {mutant} passes every pin"
+
+
+def test_empty_and_tiny(orc):
+    assert orc.naive_sa(b"").size == 0
+    assert orc.pd_sa(b"")[0].size == 0
+    assert list(orc.pd_sa(b"x")[0]) == [0]
+    assert list(orc.pd_sa(b"ba")[0]) == [1, 0]
+    assert list(orc.pd_sa(b"\x00\x00")[0]) == [1, 0]
+    assert orc.check_sa(b"", np.zeros(0, dtype=np.uint32))[0] == 0
