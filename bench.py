@@ -1,0 +1,312 @@
+"""Benchmark of gbsa on one GB300: input MB/s suffix-sorted and the HBM
+roofline fraction of the dominant kernel.
+
+Default workload (one step = one whole suffix-array build through the C-ABI):
+a single text of n = 2^28 bytes, a 1 MiB seeded Zipf(1.1) base over the
+bytes 1..255 repeated 256 times with 0.1% random substitutions per copy
+(long repeats force many doubling rounds); uint32 SA. Inputs are resident
+in HBM when the timed region starts; the text (256 MiB) and the working set
+(about 10 GiB) exceed the 129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload plain|batched] [--n N]
+
+--impl reference times the CPU oracle (oracle/, prefix doubling with
+discarding, one host core) on a bounded sample of the same workload.
+Under torchrun with N > 1 processes each rank runs an independent replica
+(the single-text build does not shard); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PLAIN_N = 1 << 28
+PLAIN_SEED = 2001
+CPU_SAMPLE_N = 1 << 23
+REF_STEP_N = 1 << 20
+FALLBACK_HBM_GBS = 6800.0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def ncu_traffic(kernel_file: str, kernel: str):
+    """DRAM bytes per item from the committed ncu summary of `kernel`, if the
+    kernel source is unchanged since it was captured (else None)."""
+    src = os.path.join(ROOT, "paper_1610_03007_gb300", "csrc", kernel_file)
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", f"ncu_{kernel}.md")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        text = f.read()
+    m_sha = re.search(r"source_sha256_16:\s*([0-9a-f]{16})", text)
+    m_b = re.search(r"dram_bytes_per_item:\s*([0-9.]+)", text)
+    if not (m_sha and m_b) or m_sha.group(1) != sha:
+        return None
+    return float(m_b.group(1))
+
+
+def cpu_baseline():
+    """The oracle as it stands, one host core, on a bounded sample: the same
+    recipe at n = 2^23."""
+    import gen
+    import oracle
+    t = gen.text("zipf_repeats", PLAIN_SEED, CPU_SAMPLE_N)
+    o = oracle.get()
+    t0 = time.perf_counter()
+    o.pd_sa(t)
+    dt = time.perf_counter() - t0
+    return {"value": CPU_SAMPLE_N / dt / 1e6, "unit": "MB/s", "cores": 1, "kind": "oracle",
+            "sample": f"zipf_repeats recipe at n=2^23 (base 32 KiB x 256 copies), one "
+                      f"prefix-doubling-with-discarding build, {dt:.1f} s on "
+                      f"{os.cpu_count()} visible host cores (1 used)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import gen
+    import oracle
+    o = oracle.get()
+    t = gen.text("zipf_repeats", PLAIN_SEED, REF_STEP_N)
+    for _ in range(args.warmup):
+        o.pd_sa(t)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.pd_sa(t)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = REF_STEP_N / dt / 1e6
+    sample = (f"each step: the CPU oracle (prefix doubling with discarding, 1 core) on the "
+              f"zipf_repeats recipe at n=2^20 (4 KiB base x 256 copies)")
+    line = {"metric": "input MB/s suffix-sorted", "value": value, "unit": "MB/s",
+            "impl": "reference", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "single text n=2^28 Zipf(1.1) bytes, 1 MiB base x256, "
+                                   "0.1% substitutions (sampled at n=2^20 for the CPU oracle)",
+                       "n": REF_STEP_N},
+            "cpu_baseline": {"value": value, "unit": "MB/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "MB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_plain(args):
+    import torch
+
+    import gen
+    import paper_1610_03007_gb300 as gbsa
+    from paper_1610_03007_gb300 import _build
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    _build.build()
+    gbsa.load()
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        pg = dist
+    n = args.n or PLAIN_N
+    t_host = gen.text("zipf_repeats", PLAIN_SEED, n)
+    dev = torch.device("cuda", local)
+    text = torch.from_numpy(t_host).to(dev)
+    ws = torch.empty(gbsa.workspace_bytes(n), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(profile=False):
+        return gbsa.sa_build_ex(text, workspace=ws, profile=profile)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kern = {}
+    launches = 0
+    bytes_model = 0
+    ev0.record(stream)
+    for _ in range(args.steps):
+        _, _, st, _ = step(profile=True)
+        launches += st["launches"]
+        bytes_model += st["bytes_model"]
+        for k, v in st["kernels"].items():
+            a = kern.setdefault(k, {"ms": 0.0, "launches": 0, "bytes": 0})
+            a["ms"] += v["ms"]
+            a["launches"] += v["launches"]
+            a["bytes"] += v["bytes"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if pg:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = sampler.stop()
+    stats = st
+
+    # End to end through the host entry point: pinned host text in, host SA
+    # out, copies inside the timed region.
+    h_text = torch.from_numpy(t_host).pin_memory()
+    h_sa = torch.empty(n, dtype=torch.int32).pin_memory()
+    del ws
+    torch.cuda.empty_cache()
+    gbsa.sa_build_host_ptr(h_text.data_ptr(), n, h_sa.data_ptr())
+    torch.cuda.synchronize()
+    e_steps = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(e_steps):
+        gbsa.sa_build_host_ptr(h_text.data_ptr(), n, h_sa.data_ptr())
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) / e_steps * 1e3
+
+    if rank != 0:
+        if pg:
+            pg.barrier()
+        return
+    hbm, peak_kind = peaks()
+    dom = max(kern.items(), key=lambda kv: kv[1]["ms"])
+    dname, d = dom
+    achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
+    traffic_per_item = ncu_traffic("k_sort.cu", "onesweep") if dname == "onesweep" else None
+    avg_bytes = d["bytes"] / max(d["launches"], 1)
+    traffic = None
+    if traffic_per_item is not None:
+        traffic = traffic_per_item * (avg_bytes / 24.0)
+    value = n * world / (ms * 1e-3) / 1e6
+    path_gbs = bytes_model / args.steps / (ms * 1e-3) / 1e9
+    line = {
+        "metric": "input MB/s suffix-sorted", "value": value, "unit": "MB/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": "single text n=2^28 bytes: 1 MiB Zipf(1.1) base over bytes 1..255 "
+                               "x256 copies, 0.1% substitutions per copy; uint32 SA",
+                   "n": n, "seed": PLAIN_SEED, "rounds": stats["rounds"],
+                   "l2": "inputs larger than L2 (256 MiB text, ~10 GiB working set); no flush",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+                     "peak_kind": peak_kind,
+                     "bytes_per_launch": avg_bytes,
+                     "ms_per_launch": d["ms"] / max(d["launches"], 1)},
+        "path_roofline": {"bytes_per_step": bytes_model / args.steps, "achieved_gbs": path_gbs,
+                          "frac_measured": path_gbs / hbm, "frac_8tbs": path_gbs / 8000.0},
+        "kernels": {k: {"ms_per_step": v["ms"] / args.steps,
+                        "launches_per_step": v["launches"] / args.steps,
+                        "gbs": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
+                    for k, v in kern.items() if v["launches"]},
+        "e2e": {"value": n / (e2e_ms * 1e-3) / 1e6, "unit": "MB/s", "h2d_bytes_per_step": n,
+                "d2h_bytes_per_step": 4 * n, "ms_per_step": e2e_ms},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    line["cpu_baseline"] = cpu_baseline() if (world == 1 and not args.no_cpu) else None
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="plain", choices=["plain"])
+    ap.add_argument("--n", type=int, default=0, help="override the text length (testing)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_plain(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/* gbsa — suffix-array construction on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: prefix doubling with discarding (Bingmann, Gog & Kurpicz,
+ * "Scalable Construction of Text Indexes", arXiv 1610.03007, Section 2.1,
+ * Algorithms 1, 4 and 5), in inverse-suffix-array form, every step in
+ * hand-written CUDA kernels: packed-character initial keys, a one-sweep LSD
+ * radix sort with decoupled look-back, boundary flags with a device-wide
+ * max-scan for renaming, and stream compaction for discarding.
+ *
+ * Problem statement (Section 2): for a text T of length n over bytes, the
+ * suffix array SA is the permutation of [0,n) with
+ * T[SA[i],n) <=lex T[SA[j],n) for i <= j. Bytes compare as unsigned values
+ * 0..255 and the end of the text is smaller than every byte (the sentinel $
+ * of Section 2.1), so a proper prefix sorts first. Because all suffixes
+ * differ, SA is unique; the result is an exact integer permutation.
+ *
+ * Conventions for every entry point:
+ *  - Pointers are DEVICE pointers unless the parameter says HOST.
+ *  - All GPU work is ordered on `stream` (a cudaStream_t; NULL = the legacy
+ *    default stream). The call returns after the result is complete on the
+ *    device: it synchronises `stream` once per doubling round to read the
+ *    number of suffixes still active.
+ *  - The caller owns every buffer it passes. The library never frees them
+ *    and keeps no pointer to them after returning.
+ *  - Errors are reported only by the return code; no state is left behind
+ *    except that a CUDA error may be sticky in the context (SA_ERR_CUDA).
+ *  - Indices and ranks are uint32; n may be at most SA_MAX_N = 2^31.
+ *  - Thread safety: calls on different streams with different workspaces
+ *    may run concurrently.
+ */
+#ifndef GBSA_H
+#define GBSA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t, declared here so this header needs no CUDA
+ * include. */
+typedef struct CUstream_st *gbsa_stream_t;
+
+typedef enum {
+  SA_OK = 0,
+  SA_ERR_INVALID_ARG = 1, /* NULL pointer with n > 0, bad offsets, ...     */
+  SA_ERR_TOO_LARGE = 2,   /* n (or the batch total) above SA_MAX_N         */
+  SA_ERR_OOM = 3,         /* workspace allocation failed or ws_bytes short */
+  SA_ERR_CUDA = 4,        /* a CUDA runtime call or kernel launch failed   */
+  SA_ERR_TIMEOUT = 5,     /* a bounded device-side wait (decoupled
+                             look-back) expired; the context stays usable  */
+  SA_ERR_INTERNAL = 6     /* an internal consistency check failed          */
+} sa_status;
+
+#define SA_MAX_N (1ull << 31)
+#define SA_MAX_ROUNDS 64
+
+/* Optional knobs for sa_build_ex / sa_build_batched_ex. Zero-initialise and
+ * set only what is needed; all-zero means the defaults. */
+typedef struct {
+  /* Characters packed into the initial 64-bit keys. 0 = as many as fit
+   * (floor((64 - segment bits) / bits per character)). A smaller value
+   * reproduces the paper's 2-character initial names (Algorithm 1). */
+  uint32_t h0_chars;
+  /* Maximum polls of one decoupled look-back wait before the kernel gives
+   * up with SA_ERR_TIMEOUT. 0 = default (about one second). */
+  uint32_t spin_limit;
+  /* Test hook: when 1, the first tile of the first radix pass never
+   * publishes its counts, so the next tile's bounded wait must expire and
+   * the call must return SA_ERR_TIMEOUT. 0 in normal use. */
+  uint32_t inject_stall;
+  /* If not NULL: DEVICE buffer of trace_cap * n uint32. The name (ISA
+   * value) of every position after the initial naming and after each
+   * refinement round k is written to trace_isa[k*n .. k*n+n) for
+   * k < trace_cap (single text only). */
+  uint32_t *trace_isa;
+  uint32_t trace_cap;
+  /* When 1, CUDA events are recorded on `stream` around every kernel launch
+   * and the per-kernel-class times, launch counts and algorithmic bytes are
+   * returned in sa_stats (adds a few microseconds per launch). */
+  uint32_t profile;
+} sa_options;
+
+/* Kernel classes of the per-kernel statistics. */
+enum {
+  SA_K_BYTE_HIST = 0, /* alphabet histogram                  */
+  SA_K_PACK = 1,      /* initial packed keys                 */
+  SA_K_DIGIT_HIST = 2,/* radix digit histograms              */
+  SA_K_PLAN = 3,      /* radix plan (one block)              */
+  SA_K_ONESWEEP = 4,  /* radix passes (kept passes only)     */
+  SA_K_RENAME = 5,    /* rename + unique + compaction        */
+  SA_K_GATHER = 6,    /* partner-name gather                 */
+  SA_K_OUTPUT = 7,    /* output fix-ups                      */
+  SA_K_CLASSES = 8
+};
+
+/* Per-build statistics (HOST struct filled by the _ex calls). */
+typedef struct {
+  uint32_t rounds;          /* doubling rounds including round 0          */
+  uint32_t sigma;           /* distinct byte values in the input          */
+  uint32_t bits_per_char;   /* b = ceil(log2 sigma), at least 1           */
+  uint32_t chars_per_key;   /* c0: characters in the initial keys         */
+  uint64_t active[SA_MAX_ROUNDS];  /* m_r: suffixes sorted in round r     */
+  uint64_t unique[SA_MAX_ROUNDS];  /* u_r: suffixes that became unique    */
+  uint32_t passes[SA_MAX_ROUNDS];  /* radix passes executed in round r    */
+  uint32_t key_bits[SA_MAX_ROUNDS];/* significant key bits in round r     */
+  uint64_t groups[SA_MAX_ROUNDS];  /* groups of equal names left after r  */
+  /* Algorithmic bytes moved (reads + writes, 4 bytes per random access)
+   * summed over all kernels and rounds; the model is documented with the
+   * kernels. */
+  uint64_t bytes_model;
+  /* Kernel launches issued by the build (all classes, skipped radix passes
+   * included). */
+  uint32_t launches;
+  /* With sa_options.profile = 1, per kernel class (SA_K_*): summed
+   * event-timed milliseconds, launches timed, and algorithmic bytes. */
+  double kernel_ms[SA_K_CLASSES];
+  uint64_t kernel_launches[SA_K_CLASSES];
+  uint64_t kernel_bytes[SA_K_CLASSES];
+} sa_stats;
+
+/* Suffix array of one text (Section 2; Algorithm 5).
+ * text   : DEVICE, n bytes, read only.
+ * n      : length, 0 <= n <= SA_MAX_N.
+ * sa_out : DEVICE, n uint32, written with SA.
+ * The workspace (about 41 bytes per character) is allocated from a
+ * library-private stream-ordered pool on `stream` and returned to it.
+ * n = 0 writes nothing; n = 1 writes sa_out[0] = 0. */
+sa_status sa_build(const uint8_t *text, uint64_t n, uint32_t *sa_out,
+                   gbsa_stream_t stream);
+
+/* Workspace size sa_build_ex needs for a text of n bytes. */
+size_t sa_workspace_bytes(uint64_t n);
+
+/* sa_build with an optional ISA output, a caller-owned workspace, options
+ * and statistics.
+ * isa_out   : DEVICE, n uint32 or NULL; receives ISA (ISA[SA[j]] = j).
+ * workspace : DEVICE, ws_bytes >= sa_workspace_bytes(n), 256-byte aligned,
+ *             or NULL to allocate internally. Contents need no
+ *             initialisation and are garbage afterwards.
+ * opt, stats: HOST, either may be NULL. */
+sa_status sa_build_ex(const uint8_t *text, uint64_t n, uint32_t *sa_out,
+                      uint32_t *isa_out, void *workspace, size_t ws_bytes,
+                      const sa_options *opt, sa_stats *stats,
+                      gbsa_stream_t stream);
+
+/* Suffix arrays of `count` independent texts in one launch sequence.
+ * texts   : DEVICE, the texts concatenated, offsets[count] bytes.
+ * offsets : HOST, count+1 uint64, offsets[0] = 0, non-decreasing; text k is
+ *           texts[offsets[k] .. offsets[k+1]). Empty texts are allowed.
+ * sa_out  : DEVICE, offsets[count] uint32. The SA of text k is written to
+ *           sa_out[offsets[k] .. offsets[k+1]) with LOCAL indices
+ *           (0 .. len_k - 1).
+ * Every text has its own end sentinel; texts never compare with each other.
+ * offsets[count] may be at most SA_MAX_N and count at most 2^20. */
+sa_status sa_build_batched(const uint8_t *texts, const uint64_t *offsets,
+                           uint32_t count, uint32_t *sa_out,
+                           gbsa_stream_t stream);
+
+/* Workspace size sa_build_batched_ex needs. offsets: HOST, count+1. */
+size_t sa_batched_workspace_bytes(const uint64_t *offsets, uint32_t count);
+
+/* sa_build_batched with a caller-owned workspace, options and statistics
+ * (same rules as sa_build_ex; trace_isa is ignored). */
+sa_status sa_build_batched_ex(const uint8_t *texts, const uint64_t *offsets,
+                              uint32_t count, uint32_t *sa_out, void *workspace,
+                              size_t ws_bytes, const sa_options *opt,
+                              sa_stats *stats, gbsa_stream_t stream);
+
+/* End-to-end build from HOST memory: copies host_text (HOST, n bytes) to the
+ * device on `stream`, builds, and copies SA back to host_sa (HOST, n
+ * uint32). Pinned host buffers give the fastest copies; pageable buffers
+ * work. Device memory (text, SA and workspace) comes from the library pool. */
+sa_status sa_build_host(const uint8_t *host_text, uint64_t n, uint32_t *host_sa,
+                        gbsa_stream_t stream);
+
+/* Stable LSD radix sort of (key, value) pairs by key bits
+ * [begin_bit, end_bit), the building block of the sort step (Algorithm 1,
+ * "Sort triples by name pair"). One-sweep passes of 8-bit digits with
+ * decoupled look-back; digits that are equal for all keys are skipped.
+ * keys, vals : DEVICE, m entries each; sorted in place (the library copies
+ *              back if the result lands in the workspace buffers).
+ * workspace  : DEVICE, >= sa_sort_workspace_bytes(m), or NULL (pool).
+ * 0 <= begin_bit < end_bit <= 64, m <= SA_MAX_N. */
+sa_status sa_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t m,
+                        uint32_t begin_bit, uint32_t end_bit, void *workspace,
+                        size_t ws_bytes, gbsa_stream_t stream);
+size_t sa_sort_workspace_bytes(uint64_t m);
+
+/* Human-readable name of a status code (static string). */
+const char *sa_status_string(sa_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

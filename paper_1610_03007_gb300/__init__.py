@@ -1,0 +1,250 @@
+"""gbsa — suffix arrays on one GB300 by prefix doubling with discarding.
+
+Thin ctypes binding over the C-ABI of libgbsa.so (include/gbsa.h): it only
+marshals arguments. Every step of the method runs in the library's CUDA
+kernels; PyTorch supplies device memory and the current stream. There is no
+CPU fallback: if libgbsa.so is missing or no GPU is present, the calls raise.
+
+Method: Bingmann, Gog & Kurpicz, "Scalable Construction of Text Indexes"
+(arXiv 1610.03007), Section 2.1, Algorithms 1, 4 and 5.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgbsa.so")
+
+SA_OK = 0
+STATUS_NAMES = {0: "SA_OK", 1: "SA_ERR_INVALID_ARG", 2: "SA_ERR_TOO_LARGE", 3: "SA_ERR_OOM",
+                4: "SA_ERR_CUDA", 5: "SA_ERR_TIMEOUT", 6: "SA_ERR_INTERNAL"}
+SA_ERR_TIMEOUT = 5
+SA_MAX_N = 1 << 31
+SA_MAX_ROUNDS = 64
+
+# Symbols include/gbsa.h declares; the loader checks that all are exported.
+EXPORTED = ("sa_build", "sa_workspace_bytes", "sa_build_ex", "sa_build_batched",
+            "sa_batched_workspace_bytes", "sa_build_batched_ex", "sa_build_host",
+            "sa_sort_pairs", "sa_sort_workspace_bytes", "sa_status_string")
+
+
+class SAError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}")
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("h0_chars", ctypes.c_uint32), ("spin_limit", ctypes.c_uint32),
+                ("inject_stall", ctypes.c_uint32), ("trace_isa", ctypes.c_void_p),
+                ("trace_cap", ctypes.c_uint32), ("profile", ctypes.c_uint32)]
+
+
+KERNEL_CLASSES = ("byte_hist", "pack", "digit_hist", "plan", "onesweep", "rename", "gather",
+                  "output")
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_uint32), ("sigma", ctypes.c_uint32),
+                ("bits_per_char", ctypes.c_uint32), ("chars_per_key", ctypes.c_uint32),
+                ("active", ctypes.c_uint64 * SA_MAX_ROUNDS),
+                ("unique", ctypes.c_uint64 * SA_MAX_ROUNDS),
+                ("passes", ctypes.c_uint32 * SA_MAX_ROUNDS),
+                ("key_bits", ctypes.c_uint32 * SA_MAX_ROUNDS),
+                ("groups", ctypes.c_uint64 * SA_MAX_ROUNDS),
+                ("bytes_model", ctypes.c_uint64),
+                ("launches", ctypes.c_uint32),
+                ("kernel_ms", ctypes.c_double * 8),
+                ("kernel_launches", ctypes.c_uint64 * 8),
+                ("kernel_bytes", ctypes.c_uint64 * 8)]
+
+    def to_dict(self) -> dict:
+        r = self.rounds
+        return {"rounds": r, "sigma": self.sigma, "bits_per_char": self.bits_per_char,
+                "chars_per_key": self.chars_per_key,
+                "active": list(self.active[:r]), "unique": list(self.unique[:r]),
+                "passes": list(self.passes[:r]), "key_bits": list(self.key_bits[:r]),
+                "groups": list(self.groups[:r]), "bytes_model": int(self.bytes_model),
+                "launches": int(self.launches),
+                "kernels": {name: {"ms": self.kernel_ms[k], "launches": int(self.kernel_launches[k]),
+                                   "bytes": int(self.kernel_bytes[k])}
+                            for k, name in enumerate(KERNEL_CLASSES)}}
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libgbsa.so (built by __graft_entry__.build()); raises if absent."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"gbsa CUDA library not built: {p} is missing "
+                           "(run `python -c 'import __graft_entry__ as g; g.build()'`)")
+    lib = ctypes.CDLL(p)
+    missing = [s for s in EXPORTED if not hasattr(lib, s)]
+    if missing:
+        raise RuntimeError(f"{p} lacks symbols {missing}")
+    vp, u64, u32, sz = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_size_t
+    lib.sa_build.argtypes = [vp, u64, vp, vp]
+    lib.sa_workspace_bytes.argtypes = [u64]
+    lib.sa_workspace_bytes.restype = sz
+    lib.sa_build_ex.argtypes = [vp, u64, vp, vp, vp, sz, ctypes.POINTER(Options),
+                                ctypes.POINTER(Stats), vp]
+    lib.sa_build_batched.argtypes = [vp, vp, u32, vp, vp]
+    lib.sa_batched_workspace_bytes.argtypes = [vp, u32]
+    lib.sa_batched_workspace_bytes.restype = sz
+    lib.sa_build_batched_ex.argtypes = [vp, vp, u32, vp, vp, sz, ctypes.POINTER(Options),
+                                        ctypes.POINTER(Stats), vp]
+    lib.sa_build_host.argtypes = [vp, u64, vp, vp]
+    lib.sa_sort_pairs.argtypes = [vp, vp, u64, u32, u32, vp, sz, vp]
+    lib.sa_sort_workspace_bytes.argtypes = [u64]
+    lib.sa_sort_workspace_bytes.restype = sz
+    lib.sa_status_string.argtypes = [ctypes.c_int]
+    lib.sa_status_string.restype = ctypes.c_char_p
+    for f in ("sa_build", "sa_build_ex", "sa_build_batched", "sa_build_batched_ex",
+              "sa_build_host", "sa_sort_pairs"):
+        getattr(lib, f).restype = ctypes.c_int
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _check(status: int, where: str):
+    if status != SA_OK:
+        raise SAError(status, where)
+
+
+def _dev_u8(t):
+    torch = _torch()
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.uint8 and t.dim() == 1):
+        raise TypeError("text must be a 1-D torch.uint8 CUDA tensor")
+    return t.contiguous()
+
+
+def workspace_bytes(n: int) -> int:
+    return int(load().sa_workspace_bytes(n))
+
+
+def sa_build(text, sa_out=None, stream=None):
+    """SA of one text (torch uint8 CUDA tensor). Returns int32 (uint32 bits)."""
+    torch = _torch()
+    lib = load()
+    t = _dev_u8(text)
+    n = t.numel()
+    if sa_out is None:
+        sa_out = torch.empty(n, dtype=torch.int32, device=t.device)
+    _check(lib.sa_build(t.data_ptr(), n, sa_out.data_ptr() if n else None, _stream(stream)),
+           "sa_build")
+    return sa_out
+
+
+def sa_build_ex(text, *, isa=False, workspace=None, h0_chars=0, spin_limit=0,
+                inject_stall=0, trace_cap=0, profile=False, stream=None):
+    """sa_build with options. Returns (sa, isa or None, stats dict, trace or None).
+
+    workspace: a uint8 CUDA tensor of at least workspace_bytes(n) bytes, or
+    None to let torch's caching allocator provide one."""
+    torch = _torch()
+    lib = load()
+    t = _dev_u8(text)
+    n = t.numel()
+    dev = t.device
+    sa = torch.empty(n, dtype=torch.int32, device=dev)
+    isa_t = torch.empty(n, dtype=torch.int32, device=dev) if isa else None
+    wsb = int(lib.sa_workspace_bytes(n))
+    if workspace is None:
+        workspace = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    trace = torch.zeros((trace_cap, n), dtype=torch.int32, device=dev) if trace_cap else None
+    opt = Options(h0_chars, spin_limit, inject_stall,
+                  trace.data_ptr() if trace is not None and n else None, trace_cap,
+                  1 if profile else 0)
+    st = Stats()
+    rc = lib.sa_build_ex(t.data_ptr(), n, sa.data_ptr() if n else None,
+                         isa_t.data_ptr() if isa_t is not None and n else None,
+                         workspace.data_ptr(), workspace.numel(), ctypes.byref(opt),
+                         ctypes.byref(st), _stream(stream))
+    _check(rc, "sa_build_ex")
+    return sa, isa_t, st.to_dict(), trace
+
+
+def sa_build_batched(texts, offsets, sa_out=None, workspace=None, stream=None, stats=False,
+                     profile=False):
+    """SAs of many texts in one launch sequence.
+
+    texts: 1-D uint8 CUDA tensor (the texts concatenated); offsets: host
+    sequence of count+1 byte offsets. Returns int32 SAs with local indices at
+    the same offsets (and the stats dict when stats=True)."""
+    torch = _torch()
+    lib = load()
+    t = _dev_u8(texts)
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.uint64))
+    count = off.size - 1
+    N = int(off[-1]) if count >= 0 else 0
+    if sa_out is None:
+        sa_out = torch.empty(N, dtype=torch.int32, device=t.device)
+    wsb = int(lib.sa_batched_workspace_bytes(off.ctypes.data, count))
+    if workspace is None and N:
+        workspace = torch.empty(wsb, dtype=torch.uint8, device=t.device)
+    st = Stats()
+    opt = Options(0, 0, 0, None, 0, 1 if profile else 0)
+    rc = lib.sa_build_batched_ex(t.data_ptr(), off.ctypes.data, count,
+                                 sa_out.data_ptr() if N else None,
+                                 workspace.data_ptr() if workspace is not None else None,
+                                 workspace.numel() if workspace is not None else 0,
+                                 ctypes.byref(opt), ctypes.byref(st), _stream(stream))
+    _check(rc, "sa_build_batched")
+    return (sa_out, st.to_dict()) if stats else sa_out
+
+
+def sa_build_host(text: np.ndarray, sa_out: np.ndarray | None = None, stream=None) -> np.ndarray:
+    """End-to-end build from host memory (host text in, host SA out)."""
+    lib = load()
+    a = np.ascontiguousarray(text, dtype=np.uint8)
+    if sa_out is None:
+        sa_out = np.empty(a.size, dtype=np.uint32)
+    _check(lib.sa_build_host(a.ctypes.data, a.size, sa_out.ctypes.data, _stream(stream)),
+           "sa_build_host")
+    return sa_out
+
+
+def sa_build_host_ptr(host_text_ptr: int, n: int, host_sa_ptr: int, stream=None):
+    """sa_build_host on raw (e.g. pinned torch) host pointers."""
+    _check(load().sa_build_host(host_text_ptr, n, host_sa_ptr, _stream(stream)), "sa_build_host")
+
+
+def sa_sort_pairs(keys, vals, begin_bit=0, end_bit=64, workspace=None, stream=None):
+    """Stable in-place LSD radix sort of (int64 keys as uint64, int32 vals as
+    uint32) CUDA tensors by key bits [begin_bit, end_bit)."""
+    torch = _torch()
+    lib = load()
+    m = keys.numel()
+    assert vals.numel() == m and keys.is_cuda and vals.is_cuda
+    if workspace is None and m > 1:
+        workspace = torch.empty(int(lib.sa_sort_workspace_bytes(m)), dtype=torch.uint8,
+                                device=keys.device)
+    _check(lib.sa_sort_pairs(keys.data_ptr(), vals.data_ptr(), m, begin_bit, end_bit,
+                             workspace.data_ptr() if workspace is not None else None,
+                             workspace.numel() if workspace is not None else 0,
+                             _stream(stream)), "sa_sort_pairs")
+    return keys, vals
+
+
+def status_string(s: int) -> str:
+    return load().sa_status_string(s).decode()

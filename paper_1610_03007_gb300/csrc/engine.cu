@@ -1,0 +1,703 @@
+// Round driver and C-ABI of gbsa: prefix doubling with discarding in
+// inverse-suffix-array form (Section 2.1, Algorithms 1, 4 and 5).
+//
+// Round 0 (initial names, Algorithm 1's first lines):
+//   byte histogram -> alphabet (host) -> packed keys -> radix sort ->
+//   rename/unique/compact.
+// Round r >= 1 (one doubling step, h = c0 * 2^(r-1) characters resolved):
+//   partner-name gather -> radix sort of (group, partner) keys ->
+//   rename/unique/compact.
+// The loop ends when no suffix is active (every name unique; the paper's
+// loop bound is one round short, so the count decides). SA is complete then:
+// each suffix wrote SA[name] = i when its name became unique.
+//
+// Host <-> device per round: one 32-byte read of the control block (active
+// count, group count, pass count, error word) after the rename.
+//
+// Data layout in HBM (N characters in S texts, gapped positions N + S):
+//   keys A/B u64[N], vals A/B u32[N], active list u64[N] (g << 32 | i'),
+//   ISA u32[N + S + 1] (end slots hold 0xFFFFFFFF), group bases u32[N/2+1]
+//   x2, look-back status u64[tiles * 256] (sort) and u64[tiles * 3]
+//   (rename), control block, plan, histograms: about 41 bytes per character.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "../../include/gbsa.h"
+#include "launch.h"
+
+#define GBSA_API extern "C" __attribute__((visibility("default")))
+
+namespace gbsa {
+namespace {
+
+constexpr uint32_t DEFAULT_SPIN_LIMIT = 1u << 20;  // ~1 s with the 1 us back-off cap
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Layout {
+  size_t ctrl, plan, hist, dbase, bytehist, code, segoff;
+  size_t ka, kb, va, vb, act, isa, base0, base1, st_sort, st_ren, total;
+  size_t st_sort_bytes, st_ren_bytes;
+};
+
+Layout make_layout(uint64_t N, uint32_t S) {
+  Layout L{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = o;
+    o += align256(bytes);
+    return r;
+  };
+  const uint64_t Nm = N ? N : 1;
+  L.ctrl = take(sizeof(Ctrl));
+  L.plan = take(sizeof(SortPlan));
+  L.hist = take(MAX_PASSES * RADIX * 4);
+  L.dbase = take(MAX_PASSES * RADIX * 4);
+  L.bytehist = take(RADIX * 4);
+  L.code = take(RADIX);
+  L.segoff = take(((size_t)S + 1) * 4);
+  L.ka = take(Nm * 8);
+  L.kb = take(Nm * 8);
+  L.va = take(Nm * 4);
+  L.vb = take(Nm * 4);
+  L.act = take(Nm * 8);
+  L.isa = take((N + S + 1) * 4);
+  L.base0 = take((Nm / 2 + 1) * 4);
+  L.base1 = take((Nm / 2 + 1) * 4);
+  const uint64_t ts = std::max<uint64_t>(1, (N + SORT_TILE - 1) / SORT_TILE);
+  L.st_sort_bytes = ts * RADIX * 8;
+  L.st_sort = take(L.st_sort_bytes);
+  const uint64_t tr = std::max<uint64_t>(1, (N + RENAME_TILE - 1) / RENAME_TILE);
+  L.st_ren_bytes = tr * 3 * 8;
+  L.st_ren = take(L.st_ren_bytes);
+  L.total = o;
+  return L;
+}
+
+uint32_t bits_for(uint64_t v) {  // bits to hold values 0..v
+  uint32_t b = 0;
+  while (b < 64 && (v >> b) != 0) ++b;
+  return b;
+}
+
+int sm_count() {
+  static std::mutex mu;
+  static std::map<int, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+  std::lock_guard<std::mutex> g(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int n = 152;
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  cache[dev] = n;
+  return n;
+}
+
+// Library-private stream-ordered pool (never trimmed, so repeated builds
+// reuse its memory without touching the process-wide default pool).
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t st) {
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    auto it = pools.find(dev);
+    if (it == pools.end()) {
+      cudaMemPoolProps props{};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      e = cudaMemPoolCreate(&pool, &props);
+      if (e != cudaSuccess) return e;
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+      pools[dev] = pool;
+    } else {
+      pool = it->second;
+    }
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
+struct PoolBuf {
+  void *p = nullptr;
+  cudaStream_t st = nullptr;
+  ~PoolBuf() {
+    if (p) cudaFreeAsync(p, st);
+  }
+};
+
+#define CK(x)                                  \
+  do {                                         \
+    cudaError_t e_ = (x);                      \
+    if (e_ != cudaSuccess) return SA_ERR_CUDA; \
+  } while (0)
+
+struct HostCtrl {
+  uint32_t error, err_where, m_next, g_next, passes, pass_mask, pad[2];
+};
+
+struct Build {
+  // inputs
+  const uint8_t *text = nullptr;
+  uint64_t N = 0;
+  uint32_t S = 1;
+  std::vector<uint32_t> off;  // S+1 ungapped offsets
+  uint32_t *sa = nullptr;
+  uint32_t *isa_out = nullptr;
+  sa_options opt{};
+  sa_stats *stats = nullptr;
+  cudaStream_t st = nullptr;
+  // workspace
+  uint8_t *ws = nullptr;
+  Layout L{};
+  Ctrl *ctrl = nullptr;
+  SortPlan *plan = nullptr;
+  uint32_t *hist = nullptr, *dbase = nullptr, *bytehist = nullptr, *segoff = nullptr;
+  uint8_t *code = nullptr;
+  uint64_t *ka = nullptr, *kb = nullptr, *act = nullptr, *st_sort = nullptr, *st_ren = nullptr;
+  uint32_t *va = nullptr, *vb = nullptr, *isa = nullptr, *base[2] = {nullptr, nullptr};
+  // launch bookkeeping
+  uint32_t epoch = 0, slot = 0;
+  uint32_t spin = DEFAULT_SPIN_LIMIT;
+  bool inject_pending = false;
+  uint64_t bytes = 0;
+  uint32_t launches = 0;
+  // per-kernel profiling (events on the build's stream)
+  struct Rec {
+    int cls, pass;
+    uint64_t bytes;
+    cudaEvent_t a, b;
+  };
+  bool prof = false;
+  std::vector<cudaEvent_t> evpool;
+  size_t evused = 0;
+  std::vector<Rec> recs;
+
+  ~Build() {
+    for (cudaEvent_t e : evpool) cudaEventDestroy(e);
+  }
+
+  template <class T>
+  T *at(size_t off_) {
+    return reinterpret_cast<T *>(ws + off_);
+  }
+
+  void carve() {
+    ctrl = at<Ctrl>(L.ctrl);
+    plan = at<SortPlan>(L.plan);
+    hist = at<uint32_t>(L.hist);
+    dbase = at<uint32_t>(L.dbase);
+    bytehist = at<uint32_t>(L.bytehist);
+    code = at<uint8_t>(L.code);
+    segoff = at<uint32_t>(L.segoff);
+    ka = at<uint64_t>(L.ka);
+    kb = at<uint64_t>(L.kb);
+    va = at<uint32_t>(L.va);
+    vb = at<uint32_t>(L.vb);
+    act = at<uint64_t>(L.act);
+    isa = at<uint32_t>(L.isa);
+    base[0] = at<uint32_t>(L.base0);
+    base[1] = at<uint32_t>(L.base1);
+    st_sort = at<uint64_t>(L.st_sort);
+    st_ren = at<uint64_t>(L.st_ren);
+  }
+
+  cudaError_t event(cudaEvent_t &e) {
+    if (evused == evpool.size()) {
+      cudaEvent_t x;
+      cudaError_t r = cudaEventCreate(&x);
+      if (r != cudaSuccess) return r;
+      evpool.push_back(x);
+    }
+    e = evpool[evused++];
+    return cudaEventRecord(e, st);
+  }
+
+  // Issues one kernel launch; with profiling, brackets it with events.
+  // `bytes` is the launch's algorithmic traffic (radix passes: counted only
+  // if the device plan kept the pass; rename: settled at the round's sync).
+  template <class F>
+  sa_status launch(int cls, int pass, uint64_t nbytes, F f) {
+    ++launches;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (prof) CK(event(a));
+    CK(f());
+    if (prof) {
+      CK(event(b));
+      recs.push_back({cls, pass, nbytes, a, b});
+    }
+    return SA_OK;
+  }
+
+  // After a stream sync: fold the recorded launches into the statistics.
+  sa_status flush(uint32_t pass_mask, uint64_t rename_bytes_now) {
+    if (!prof || !stats) {
+      recs.clear();
+      evused = 0;
+      return SA_OK;
+    }
+    for (const Rec &r : recs) {
+      if (r.cls == SA_K_ONESWEEP && !((pass_mask >> r.pass) & 1u)) continue;
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, r.a, r.b));
+      stats->kernel_ms[r.cls] += ms;
+      stats->kernel_launches[r.cls] += 1;
+      stats->kernel_bytes[r.cls] += r.cls == SA_K_RENAME ? rename_bytes_now : r.bytes;
+    }
+    recs.clear();
+    evused = 0;
+    return SA_OK;
+  }
+
+  sa_status next_launch(uint32_t *&ctr, uint32_t &ep) {
+    if (slot == (uint32_t)TILE_COUNTERS) {
+      CK(cudaMemsetAsync(ctrl->tile_ctr, 0, sizeof(ctrl->tile_ctr), st));
+      slot = 0;
+    }
+    ctr = &ctrl->tile_ctr[slot++];
+    ep = ++epoch;
+    return SA_OK;
+  }
+
+  sa_status read_ctrl(HostCtrl &hc) {
+    CK(cudaMemcpyAsync(&hc, ctrl, sizeof(HostCtrl), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (hc.error == ERR_TIMEOUT) return SA_ERR_TIMEOUT;
+    if (hc.error != ERR_NONE) return SA_ERR_INTERNAL;
+    return SA_OK;
+  }
+
+  // Radix sort of (ka, va)[0, m) by the digits of spec; result where the
+  // device plan says (plan->kfinal / vfinal).
+  sa_status sort(uint32_t m, const DigitSpec &spec) {
+    CK(cudaMemsetAsync(hist, 0, (size_t)spec.P * RADIX * 4, st));
+    sa_status s = launch(SA_K_DIGIT_HIST, 0, 8ull * m, [&] {
+      return launch_digit_histogram(ka, m, spec, hist, sm_count(), st);
+    });
+    if (s != SA_OK) return s;
+    s = launch(SA_K_PLAN, 0, (uint64_t)spec.P * RADIX * 8, [&] {
+      return launch_sort_plan(hist, dbase, spec, m, ka, kb, va, vb, plan, ctrl, st);
+    });
+    if (s != SA_OK) return s;
+    for (uint32_t p = 0; p < spec.P; ++p) {
+      PassArgs pa{};
+      pa.plan = plan;
+      pa.p = (int)p;
+      pa.shift = spec.shift[p];
+      pa.bits = spec.bits[p];
+      pa.digit_base = dbase + p * RADIX;
+      pa.m = m;
+      pa.status = st_sort;
+      s = next_launch(pa.tile_ctr, pa.epoch);
+      if (s != SA_OK) return s;
+      pa.ctrl = ctrl;
+      pa.spin_limit = spin;
+      pa.inject = inject_pending ? 1u : 0u;
+      s = launch(SA_K_ONESWEEP, (int)p, 24ull * m, [&] { return launch_onesweep(pa, st); });
+      if (s != SA_OK) return s;
+    }
+    inject_pending = false;
+    bytes += 8ull * m;  // histogram read
+    return SA_OK;
+  }
+
+  static DigitSpec spec_for(uint32_t total_bits) {
+    DigitSpec s{};
+    s.P = (total_bits + RADIX_BITS - 1) / RADIX_BITS;
+    for (uint32_t p = 0; p < s.P; ++p) {
+      s.shift[p] = (uint8_t)(p * RADIX_BITS);
+      s.bits[p] = (uint8_t)std::min<uint32_t>(RADIX_BITS, total_bits - p * RADIX_BITS);
+    }
+    return s;
+  }
+
+  sa_status rename(uint32_t m, bool round0, uint32_t cb, uint32_t c0, uint32_t W, int bi,
+                   uint32_t g_in) {
+    RenameArgs ra{};
+    ra.plan = plan;
+    ra.m = m;
+    ra.round0 = round0 ? 1u : 0u;
+    ra.cb = cb;
+    ra.c0 = c0;
+    ra.seg_off = segoff;
+    ra.S = S;
+    ra.W = W;
+    ra.base_in = base[bi];
+    ra.g_in = g_in;
+    ra.isa = isa;
+    ra.isa_len = N + S + 1;
+    ra.N = (uint32_t)N;
+    ra.sa = sa;
+    ra.act_out = act;
+    ra.base_out = base[bi ^ 1];
+    ra.status = st_ren;
+    sa_status s = next_launch(ra.tile_ctr, ra.epoch);
+    if (s != SA_OK) return s;
+    ra.ctrl = ctrl;
+    ra.spin_limit = spin;
+    return launch(SA_K_RENAME, 0, 0, [&] { return launch_rename(ra, st); });
+  }
+
+  // Rename reads 12 bytes per item plus 4 per item for the ISA write, 4 per
+  // unique item (SA), 8 per survivor and 4 per surviving group.
+  static uint64_t rename_bytes(uint32_t m, const HostCtrl &hc) {
+    const uint64_t u = m - hc.m_next;
+    return 16ull * m + 4 * u + 8ull * hc.m_next + 4ull * hc.g_next;
+  }
+
+  void record(uint32_t r, uint32_t m, const HostCtrl &hc, uint32_t kbits) {
+    if (!stats || r >= SA_MAX_ROUNDS) return;
+    stats->active[r] = m;
+    stats->unique[r] = m - hc.m_next;
+    stats->passes[r] = hc.passes;
+    stats->key_bits[r] = kbits;
+    stats->groups[r] = hc.g_next;
+  }
+
+  sa_status run() {
+    const uint32_t N32 = (uint32_t)N;
+    carve();
+    prof = opt.profile != 0 && stats != nullptr;
+    // Clear what must start at zero; the ISA starts all-ones so every end
+    // slot reads as the sentinel.
+    CK(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
+    CK(cudaMemsetAsync(st_sort, 0, L.st_sort_bytes, st));
+    CK(cudaMemsetAsync(st_ren, 0, L.st_ren_bytes, st));
+    CK(cudaMemsetAsync(bytehist, 0, RADIX * 4, st));
+    CK(cudaMemsetAsync(isa, 0xFF, (N + S + 1) * 4, st));
+    CK(cudaMemcpyAsync(segoff, off.data(), ((size_t)S + 1) * 4, cudaMemcpyHostToDevice, st));
+
+    // ---- A0: alphabet ----
+    sa_status s = launch(SA_K_BYTE_HIST, 0, N, [&] {
+      return launch_byte_histogram(text, N, bytehist, sm_count(), st);
+    });
+    if (s != SA_OK) return s;
+    uint32_t hh[RADIX];
+    CK(cudaMemcpyAsync(hh, bytehist, sizeof(hh), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    s = flush(0, 0);
+    if (s != SA_OK) return s;
+    uint8_t hcode[RADIX];
+    uint32_t sigma = 0;
+    for (int c = 0; c < RADIX; ++c) {
+      hcode[c] = (uint8_t)sigma;  // order-preserving dense code
+      if (hh[c]) ++sigma;
+    }
+    const uint32_t b = std::max<uint32_t>(1, bits_for(sigma - 1));
+    const uint32_t segbits = S > 1 ? bits_for(S - 1) : 0;
+    uint32_t c0 = (64 - segbits) / b;
+    if (opt.h0_chars) c0 = std::min(c0, opt.h0_chars);
+    const uint32_t cb = c0 * b;
+    CK(cudaMemcpyAsync(code, hcode, sizeof(hcode), cudaMemcpyHostToDevice, st));
+    bytes += N;
+    if (stats) {
+      stats->sigma = sigma;
+      stats->bits_per_char = b;
+      stats->chars_per_key = c0;
+    }
+
+    // ---- round 0: initial names ----
+    PackArgs pk{};
+    pk.text = text;
+    pk.N = N32;
+    pk.seg_off = segoff;
+    pk.S = S;
+    pk.code = code;
+    pk.b = b;
+    pk.c0 = c0;
+    pk.cb = cb;
+    pk.keys = ka;
+    pk.vals = va;
+    s = launch(SA_K_PACK, 0, 13ull * N, [&] { return launch_pack(pk, st); });
+    if (s != SA_OK) return s;
+    bytes += 13ull * N;
+    const uint32_t bits0 = cb + segbits;
+    inject_pending = opt.inject_stall != 0;
+    s = sort(N32, spec_for(bits0));
+    if (s != SA_OK) return s;
+    s = rename(N32, true, cb, c0, 0, 1, 0);  // writes base[0]
+    if (s != SA_OK) return s;
+    if (opt.trace_isa && opt.trace_cap > 0 && S == 1)
+      CK(cudaMemcpyAsync(opt.trace_isa, isa, N * 4, cudaMemcpyDeviceToDevice, st));
+    HostCtrl hc{};
+    s = read_ctrl(hc);
+    if (s != SA_OK) return s;
+    uint32_t m = N32;
+    s = flush(hc.pass_mask, rename_bytes(m, hc));
+    if (s != SA_OK) return s;
+    record(0, m, hc, bits0);
+    bytes += (uint64_t)hc.passes * 24 * m + rename_bytes(m, hc);
+
+    // ---- rounds r >= 1: one doubling step each ----
+    const uint32_t W = bits_for(N);  // r2 in [0, N]
+    uint64_t h = c0;
+    int bi = 0;
+    uint32_t round = 1;
+    while (hc.m_next > 0) {
+      if (round >= SA_MAX_ROUNDS || h > N) return SA_ERR_INTERNAL;
+      m = hc.m_next;
+      const uint32_t G = hc.g_next;
+      s = launch(SA_K_GATHER, 0, 24ull * m, [&] {
+        return launch_gather(act, m, (uint32_t)h, W, isa, N + S + 1, ka, va, st);
+      });
+      if (s != SA_OK) return s;
+      bytes += 24ull * m;
+      const uint32_t kbits = W + (G > 1 ? bits_for(G - 1) : 0);
+      s = sort(m, spec_for(kbits));
+      if (s != SA_OK) return s;
+      s = rename(m, false, 0, 0, W, bi, G);
+      if (s != SA_OK) return s;
+      bi ^= 1;
+      if (opt.trace_isa && round < opt.trace_cap && S == 1)
+        CK(cudaMemcpyAsync(opt.trace_isa + (size_t)round * N, isa, N * 4,
+                           cudaMemcpyDeviceToDevice, st));
+      s = read_ctrl(hc);
+      if (s != SA_OK) return s;
+      s = flush(hc.pass_mask, rename_bytes(m, hc));
+      if (s != SA_OK) return s;
+      record(round, m, hc, kbits);
+      bytes += (uint64_t)hc.passes * 24 * m + rename_bytes(m, hc);
+      h *= 2;
+      ++round;
+    }
+    // ---- output ----
+    if (S > 1) {
+      s = launch(SA_K_OUTPUT, 0, 8ull * N, [&] { return launch_sa_to_local(sa, N32, segoff, S, st); });
+      if (s != SA_OK) return s;
+      bytes += 8ull * N;
+    }
+    if (isa_out) {
+      s = launch(SA_K_OUTPUT, 0, 8ull * N, [&] {
+        return launch_isa_to_local(isa, isa_out, N32, segoff, S, st);
+      });
+      if (s != SA_OK) return s;
+      bytes += 8ull * N;
+    }
+    if (prof) {
+      CK(cudaStreamSynchronize(st));
+      s = flush(0, 0);
+      if (s != SA_OK) return s;
+    }
+    if (stats) {
+      stats->rounds = round;
+      stats->bytes_model = bytes;
+      stats->launches = launches;
+    }
+    return SA_OK;
+  }
+};
+
+sa_status check_offsets(const uint64_t *offsets, uint32_t count) {
+  if (!offsets || count == 0) return SA_ERR_INVALID_ARG;
+  if (offsets[0] != 0) return SA_ERR_INVALID_ARG;
+  for (uint32_t k = 0; k < count; ++k)
+    if (offsets[k + 1] < offsets[k]) return SA_ERR_INVALID_ARG;
+  if (offsets[count] > SA_MAX_N) return SA_ERR_TOO_LARGE;
+  return SA_OK;
+}
+
+sa_status run_with_workspace(Build &B, void *workspace, size_t ws_bytes) {
+  B.L = make_layout(B.N, B.S);
+  if (B.opt.spin_limit) B.spin = B.opt.spin_limit;
+  PoolBuf own;
+  if (workspace) {
+    if (ws_bytes < B.L.total || ((uintptr_t)workspace & 255)) return SA_ERR_OOM;
+    B.ws = (uint8_t *)workspace;
+  } else {
+    own.st = B.st;
+    if (pool_alloc(&own.p, B.L.total, B.st) != cudaSuccess) {
+      own.p = nullptr;
+      cudaGetLastError();
+      return SA_ERR_OOM;
+    }
+    B.ws = (uint8_t *)own.p;
+  }
+  if (B.stats) memset(B.stats, 0, sizeof(sa_stats));
+  return B.run();
+}
+
+}  // namespace
+}  // namespace gbsa
+
+using namespace gbsa;
+
+GBSA_API size_t sa_workspace_bytes(uint64_t n) { return make_layout(n, 1).total; }
+
+GBSA_API size_t sa_batched_workspace_bytes(const uint64_t *offsets, uint32_t count) {
+  if (check_offsets(offsets, count) != SA_OK) return 0;
+  return make_layout(offsets[count], count).total;
+}
+
+GBSA_API sa_status sa_build_ex(const uint8_t *text, uint64_t n, uint32_t *sa_out,
+                               uint32_t *isa_out, void *workspace, size_t ws_bytes,
+                               const sa_options *opt, sa_stats *stats, gbsa_stream_t stream) {
+  if (n > SA_MAX_N) return SA_ERR_TOO_LARGE;
+  if (n > 0 && (!text || !sa_out)) return SA_ERR_INVALID_ARG;
+  if (stats) memset(stats, 0, sizeof(sa_stats));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n == 0) return SA_OK;
+  if (n == 1) {
+    if (cudaMemsetAsync(sa_out, 0, 4, st) != cudaSuccess) return SA_ERR_CUDA;
+    if (isa_out && cudaMemsetAsync(isa_out, 0, 4, st) != cudaSuccess) return SA_ERR_CUDA;
+    if (stats) stats->rounds = 1;
+    return SA_OK;
+  }
+  Build B;
+  B.text = text;
+  B.N = n;
+  B.S = 1;
+  B.off = {0u, (uint32_t)n};
+  B.sa = sa_out;
+  B.isa_out = isa_out;
+  if (opt) B.opt = *opt;
+  B.stats = stats;
+  B.st = st;
+  return run_with_workspace(B, workspace, ws_bytes);
+}
+
+GBSA_API sa_status sa_build(const uint8_t *text, uint64_t n, uint32_t *sa_out,
+                            gbsa_stream_t stream) {
+  return sa_build_ex(text, n, sa_out, nullptr, nullptr, 0, nullptr, nullptr, stream);
+}
+
+GBSA_API sa_status sa_build_batched_ex(const uint8_t *texts, const uint64_t *offsets,
+                                       uint32_t count, uint32_t *sa_out, void *workspace,
+                                       size_t ws_bytes, const sa_options *opt,
+                                       sa_stats *stats, gbsa_stream_t stream) {
+  sa_status s = check_offsets(offsets, count);
+  if (s != SA_OK) return s;
+  if (count > (1u << 20)) return SA_ERR_TOO_LARGE;
+  const uint64_t N = offsets[count];
+  if (stats) memset(stats, 0, sizeof(sa_stats));
+  if (N == 0) return SA_OK;
+  if (!texts || !sa_out) return SA_ERR_INVALID_ARG;
+  Build B;
+  B.text = texts;
+  B.N = N;
+  B.S = count;
+  B.off.resize((size_t)count + 1);
+  for (uint32_t k = 0; k <= count; ++k) B.off[k] = (uint32_t)offsets[k];
+  B.sa = sa_out;
+  if (opt) {
+    B.opt = *opt;
+    B.opt.trace_isa = nullptr;
+    B.opt.trace_cap = 0;
+  }
+  B.stats = stats;
+  B.st = (cudaStream_t)stream;
+  return run_with_workspace(B, workspace, ws_bytes);
+}
+
+GBSA_API sa_status sa_build_batched(const uint8_t *texts, const uint64_t *offsets, uint32_t count,
+                                    uint32_t *sa_out, gbsa_stream_t stream) {
+  return sa_build_batched_ex(texts, offsets, count, sa_out, nullptr, 0, nullptr, nullptr, stream);
+}
+
+GBSA_API sa_status sa_build_host(const uint8_t *host_text, uint64_t n, uint32_t *host_sa,
+                                 gbsa_stream_t stream) {
+  if (n > SA_MAX_N) return SA_ERR_TOO_LARGE;
+  if (n > 0 && (!host_text || !host_sa)) return SA_ERR_INVALID_ARG;
+  if (n == 0) return SA_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t tb = align256(n), sb = align256(n * 4);
+  const size_t wb = sa_workspace_bytes(n);
+  PoolBuf buf;
+  buf.st = st;
+  if (pool_alloc(&buf.p, tb + sb + wb, st) != cudaSuccess) {
+    buf.p = nullptr;
+    cudaGetLastError();
+    return SA_ERR_OOM;
+  }
+  uint8_t *d_text = (uint8_t *)buf.p;
+  uint32_t *d_sa = (uint32_t *)((uint8_t *)buf.p + tb);
+  void *d_ws = (uint8_t *)buf.p + tb + sb;
+  if (cudaMemcpyAsync(d_text, host_text, n, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return SA_ERR_CUDA;
+  sa_status s = sa_build_ex(d_text, n, d_sa, nullptr, d_ws, wb, nullptr, nullptr, stream);
+  if (s != SA_OK) return s;
+  if (cudaMemcpyAsync(host_sa, d_sa, n * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return SA_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return SA_ERR_CUDA;
+  return SA_OK;
+}
+
+GBSA_API size_t sa_sort_workspace_bytes(uint64_t m) {
+  const uint64_t mm = m ? m : 1;
+  const uint64_t tiles = (mm + SORT_TILE - 1) / SORT_TILE;
+  return align256(sizeof(Ctrl)) + align256(sizeof(SortPlan)) + 2 * align256(MAX_PASSES * RADIX * 4) +
+         align256(mm * 8) + align256(mm * 4) + align256(tiles * RADIX * 8);
+}
+
+GBSA_API sa_status sa_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t m, uint32_t begin_bit,
+                                 uint32_t end_bit, void *workspace, size_t ws_bytes,
+                                 gbsa_stream_t stream) {
+  if (m > SA_MAX_N) return SA_ERR_TOO_LARGE;
+  if (begin_bit >= end_bit || end_bit > 64) return SA_ERR_INVALID_ARG;
+  if (m > 0 && (!keys || !vals)) return SA_ERR_INVALID_ARG;
+  if (m <= 1) return SA_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t need = sa_sort_workspace_bytes(m);
+  PoolBuf own;
+  uint8_t *ws = (uint8_t *)workspace;
+  if (ws) {
+    if (ws_bytes < need || ((uintptr_t)ws & 255)) return SA_ERR_OOM;
+  } else {
+    own.st = st;
+    if (pool_alloc(&own.p, need, st) != cudaSuccess) {
+      own.p = nullptr;
+      cudaGetLastError();
+      return SA_ERR_OOM;
+    }
+    ws = (uint8_t *)own.p;
+  }
+  const uint64_t tiles = (m + SORT_TILE - 1) / SORT_TILE;
+  size_t o = 0;
+  auto take = [&](size_t bytes) { uint8_t *r = ws + o; o += align256(bytes); return r; };
+  Build B;
+  B.st = st;
+  B.ctrl = (Ctrl *)take(sizeof(Ctrl));
+  B.plan = (SortPlan *)take(sizeof(SortPlan));
+  B.hist = (uint32_t *)take(MAX_PASSES * RADIX * 4);
+  B.dbase = (uint32_t *)take(MAX_PASSES * RADIX * 4);
+  B.kb = (uint64_t *)take(m * 8);
+  B.vb = (uint32_t *)take(m * 4);
+  B.st_sort = (uint64_t *)take(tiles * RADIX * 8);
+  B.ka = keys;
+  B.va = vals;
+  CK(cudaMemsetAsync(B.ctrl, 0, sizeof(Ctrl), st));
+  CK(cudaMemsetAsync(B.st_sort, 0, tiles * RADIX * 8, st));
+  DigitSpec spec{};
+  const uint32_t span = end_bit - begin_bit;
+  spec.P = (span + RADIX_BITS - 1) / RADIX_BITS;
+  for (uint32_t p = 0; p < spec.P; ++p) {
+    spec.shift[p] = (uint8_t)(begin_bit + p * RADIX_BITS);
+    spec.bits[p] = (uint8_t)std::min<uint32_t>(RADIX_BITS, end_bit - spec.shift[p]);
+  }
+  sa_status s = B.sort((uint32_t)m, spec);
+  if (s != SA_OK) return s;
+  CK(launch_copy_back(B.plan, keys, vals, (uint32_t)m, sm_count(), st));
+  HostCtrl hc{};
+  return B.read_ctrl(hc);
+}
+
+GBSA_API const char *sa_status_string(sa_status s) {
+  switch (s) {
+    case SA_OK: return "SA_OK";
+    case SA_ERR_INVALID_ARG: return "SA_ERR_INVALID_ARG";
+    case SA_ERR_TOO_LARGE: return "SA_ERR_TOO_LARGE";
+    case SA_ERR_OOM: return "SA_ERR_OOM";
+    case SA_ERR_CUDA: return "SA_ERR_CUDA";
+    case SA_ERR_TIMEOUT: return "SA_ERR_TIMEOUT";
+    case SA_ERR_INTERNAL: return "SA_ERR_INTERNAL";
+  }
+  return "SA_ERR_UNKNOWN";
+}

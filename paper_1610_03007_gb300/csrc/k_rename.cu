@@ -1,0 +1,218 @@
+// Steps A3 + A4 — new names, uniqueness and discarding, in one pass over the
+// sorted (key, position) pairs of a round.
+//
+//  - Boundary flag (CmpName, Section 2.1, Algorithm 2): f_j = 1 iff key_j
+//    differs from key_{j-1} (f_0 = 1). In round 0 every tail suffix (fewer
+//    than c0 characters left; see k_pack.cu) and the item after it also get
+//    f = 1, so each tail is a group of its own.
+//  - Head rank (PrefixSum with max, Algorithm 1): s_j = max over j' <= j of
+//    (f_j' ? j' : 0), a device-wide max-scan with decoupled look-back.
+//  - New name (NameDiscarding, Algorithms 5/6, in head-rank form): round 0
+//    new_j = s_j; later rounds new_j = r + (s_j - group start), stored as
+//    base[g] + s_j with base[g] = r - group start of group g.
+//  - Unique (Algorithm 6): new_j differs from both neighbours, i.e.
+//    f_j and f_{j+1} (f_m = 1).
+//  - Discarding (Algorithm 5): ISA[i] = new for every item; a unique item is
+//    final and writes SA[new] = i; the others are compacted, in order, into
+//    the next active list with their group ordinal g', and each group's head
+//    records base'[g'] = new - its position in that list. Offsets come from
+//    two device-wide sums (survivors, group heads) with decoupled look-back.
+//
+// All partner names of a round were gathered by an earlier kernel, so the
+// ISA writes here never race with reads of the same round.
+//
+// Bound: HBM. 12 bytes read per item; 4 bytes random ISA write per item,
+// 4 bytes random SA write per unique item, 8 bytes per survivor.
+#include "launch.h"
+
+namespace gbsa {
+
+constexpr int RN_BLOCK = 256;
+constexpr int RN_ITEMS = 16;
+constexpr int RN_TILE = RN_BLOCK * RN_ITEMS;
+constexpr int RN_WARPS = RN_BLOCK / 32;
+static_assert(RN_TILE == RENAME_TILE, "tile size mismatch");
+
+struct RnSmem {
+  uint64_t keys[RN_TILE + RN_TILE / 16];  // element e at e + e/16 (no bank conflicts)
+  uint32_t vals[RN_TILE + RN_TILE / 32];  // element e at e + e/32
+  uint64_t prev_key, next_key;
+  uint32_t prev_val, next_val;
+  uint32_t tmp[RN_WARPS + 1];
+  uint32_t carry[3];
+  uint32_t tile, bail;
+};
+
+__device__ __forceinline__ uint32_t kidx(uint32_t e) { return e + (e >> 4); }
+__device__ __forceinline__ uint32_t vidx(uint32_t e) { return e + (e >> 5); }
+
+__global__ void __launch_bounds__(RN_BLOCK) k_rename(RenameArgs a) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  RnSmem &S = *reinterpret_cast<RnSmem *>(smem_raw);
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    S.tile = atomicAdd(a.tile_ctr, 1u);
+    S.bail = has_error(a.ctrl) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (S.bail) return;
+  const uint32_t tile = S.tile;
+  const uint64_t *__restrict__ K = a.plan->kfinal;
+  const uint32_t *__restrict__ V = a.plan->vfinal;
+  const uint32_t base = tile * RN_TILE;
+  const uint32_t count = min((uint32_t)RN_TILE, a.m - base);
+
+  // Coalesced load of the tile plus one item of halo on each side.
+  for (int k = 0; k < RN_ITEMS; ++k) {
+    const uint32_t e = k * RN_BLOCK + tid;
+    if (e < count) {
+      S.keys[kidx(e)] = K[base + e];
+      S.vals[vidx(e)] = V[base + e];
+    }
+  }
+  if (tid == 0) {
+    S.prev_key = base > 0 ? K[base - 1] : 0ull;
+    S.prev_val = base > 0 ? V[base - 1] : 0u;
+    const bool has_next = base + count < a.m;
+    S.next_key = has_next ? K[base + count] : 0ull;
+    S.next_val = has_next ? V[base + count] : 0u;
+  }
+  __syncthreads();
+
+  // Items tid*16 .. tid*16+15 of the tile, with neighbours -1 and +16.
+  const uint32_t l0 = tid * RN_ITEMS;
+  uint64_t key[RN_ITEMS + 2];
+  uint32_t val[RN_ITEMS + 2];
+#pragma unroll
+  for (int k = 0; k < RN_ITEMS + 2; ++k) {
+    const int64_t l = (int64_t)l0 + k - 1;
+    if (l < 0) {
+      key[k] = S.prev_key;
+      val[k] = S.prev_val;
+    } else if (l < (int64_t)count) {
+      key[k] = S.keys[kidx((uint32_t)l)];
+      val[k] = S.vals[vidx((uint32_t)l)];
+    } else {
+      key[k] = S.next_key;
+      val[k] = S.next_val;
+    }
+  }
+  // Round 0: does the suffix at gapped position v (key k) have fewer than
+  // c0 characters left in its text?
+  auto tail = [&](uint64_t k, uint32_t v) -> bool {
+    const uint32_t s = a.S > 1 ? (uint32_t)(k >> a.cb) : 0u;
+    const uint32_t off = __ldg(a.seg_off + s);
+    const uint32_t len = __ldg(a.seg_off + s + 1) - off;
+    return len - (v - (off + s)) < a.c0;
+  };
+  // f[k] = boundary flag of item l0 + k (k = 0..16).
+  bool f[RN_ITEMS + 1];
+  bool is_tail[RN_ITEMS + 2];
+  if (a.round0) {
+#pragma unroll
+    for (int k = 0; k < RN_ITEMS + 2; ++k) is_tail[k] = tail(key[k], val[k]);
+  }
+#pragma unroll
+  for (int k = 0; k <= RN_ITEMS; ++k) {
+    const uint64_t j = (uint64_t)base + l0 + k;
+    bool b = (j == 0) || (j >= a.m) || key[k + 1] != key[k];
+    if (a.round0 && j > 0 && j < a.m) b = b || is_tail[k + 1] || is_tail[k];
+    f[k] = b;
+  }
+  uint32_t th_head = 0, th_surv = 0, th_hs = 0;
+#pragma unroll
+  for (int k = 0; k < RN_ITEMS; ++k) {
+    if (l0 + k < count) {
+      const bool uniq = f[k] && f[k + 1];
+      if (f[k]) th_head = base + l0 + k;
+      if (!uniq) {
+        ++th_surv;
+        if (f[k]) ++th_hs;
+      }
+    }
+  }
+  uint32_t tot_head, tot_surv, tot_hs;
+  const uint32_t ex_head = block_exclusive<RN_BLOCK>(th_head, OpMax(), 0u, S.tmp, tot_head);
+  const uint32_t ex_surv = block_exclusive<RN_BLOCK>(th_surv, OpAdd(), 0u, S.tmp, tot_surv);
+  const uint32_t ex_hs = block_exclusive<RN_BLOCK>(th_hs, OpAdd(), 0u, S.tmp, tot_hs);
+
+  // Three device-wide scans: max head position, survivors, group heads.
+  if ((tid & 31) == 0 && tid < 96) {
+    const uint32_t which = tid >> 5;
+    const uint32_t agg = which == 0 ? tot_head : (which == 1 ? tot_surv : tot_hs);
+    uint64_t *st = a.status + (uint64_t)tile * 3 + which;
+    uint32_t carry = 0;
+    bool ok = true;
+    if (tile == 0) {
+      status_store(st, status_word(a.epoch, ST_INC, agg));
+    } else {
+      status_store(st, status_word(a.epoch, ST_AGG, agg));
+      if (which == 0)
+        ok = look_back(a.status, 3, which, tile, a.epoch, OpMax(), carry, a.ctrl, a.spin_limit);
+      else
+        ok = look_back(a.status, 3, which, tile, a.epoch, OpAdd(), carry, a.ctrl, a.spin_limit);
+      if (ok) {
+        const uint32_t inc = which == 0 ? (carry > agg ? carry : agg) : carry + agg;
+        status_store(st, status_word(a.epoch, ST_INC, inc));
+      }
+    }
+    if (!ok) S.bail = 1;
+    S.carry[which] = carry;
+  }
+  __syncthreads();
+  if (S.bail) return;
+  if (tid == 0 && base + count == a.m) {
+    a.ctrl->m_next = S.carry[1] + tot_surv;
+    a.ctrl->g_next = S.carry[2] + tot_hs;
+  }
+
+  uint32_t run_head = S.carry[0] > ex_head ? S.carry[0] : ex_head;
+  uint32_t run_surv = S.carry[1] + ex_surv;
+  uint32_t run_hs = S.carry[2] + ex_hs;
+#pragma unroll
+  for (int k = 0; k < RN_ITEMS; ++k) {
+    if (l0 + k < count) {
+      const uint32_t j = base + l0 + k;
+      if (f[k]) run_head = j;
+      const uint64_t kk = key[k + 1];
+      const uint32_t ip = val[k + 1];
+      const uint32_t g = a.round0 ? 0u : (uint32_t)(kk >> a.W);
+      if (!a.round0 && g >= a.g_in) {  // never taken unless a logic error
+        raise_error(a.ctrl, ERR_INTERNAL, 4);
+        continue;
+      }
+      const uint32_t name = a.round0 ? run_head : __ldg(a.base_in + g) + run_head;
+      if (name >= a.N || ip >= a.isa_len) {  // never taken unless a logic error
+        raise_error(a.ctrl, ERR_INTERNAL, 3);
+        continue;
+      }
+      a.isa[ip] = name;
+      if (f[k] && f[k + 1]) {
+        a.sa[name] = ip;
+      } else {
+        if (f[k]) {
+          ++run_hs;
+          a.base_out[run_hs - 1] = name - run_surv;
+        }
+        a.act_out[run_surv] = ((uint64_t)(run_hs - 1) << 32) | ip;
+        ++run_surv;
+      }
+    }
+  }
+}
+
+cudaError_t launch_rename(const RenameArgs &a, cudaStream_t stream) {
+  if (a.m == 0) return cudaSuccess;
+  static bool configured = false;
+  const int smem = (int)sizeof(RnSmem);
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_rename, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const uint32_t tiles = (a.m + RN_TILE - 1) / RN_TILE;
+  k_rename<<<tiles, RN_BLOCK, smem, stream>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace gbsa

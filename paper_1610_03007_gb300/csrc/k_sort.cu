@@ -1,0 +1,307 @@
+// Step A2 — stable LSD radix sort of (64-bit key, 32-bit value) pairs: the
+// "sort triples by name pair" step of prefix doubling (Section 2.1,
+// Algorithm 1; Algorithm 5 sorts only the undiscarded items).
+//
+// One-sweep structure (Adinets & Merrill, "Onesweep: A Faster Least
+// Significant Digit Radix Sort for GPUs", 2022), written from that
+// description:
+//   1. k_digit_histogram: one read of all keys builds the 256-bin histogram
+//      of every digit position at once.
+//   2. k_sort_plan (one block): exclusive digit offsets per pass; a digit
+//      position whose keys all share one value is skipped; the source and
+//      destination buffers of the remaining passes ping-pong A <-> B.
+//   3. k_onesweep per kept pass: each tile of 4096 items ranks its items by
+//      digit (warp ballots give the peers of equal digit, so the local order
+//      is stable), publishes its per-digit counts, finds its per-digit
+//      global offsets by decoupled look-back over the preceding tiles, stages
+//      the tile in shared memory in digit order and writes each digit run
+//      with consecutive addresses.
+//
+// Bound: HBM. Per pass: 12 bytes read + 12 bytes written per item; the
+// histogram reads 8 bytes per item once per sort.
+#include "launch.h"
+
+namespace gbsa {
+
+// ---- 1. histogram of every digit position --------------------------------
+
+constexpr int DH_BLOCK = 256;
+
+__global__ void __launch_bounds__(DH_BLOCK)
+k_digit_histogram(const uint64_t *__restrict__ keys, uint32_t m, DigitSpec spec,
+                  uint32_t *__restrict__ hist) {
+  __shared__ uint32_t s_hist[MAX_PASSES][RADIX];
+  for (int x = threadIdx.x; x < MAX_PASSES * RADIX; x += DH_BLOCK) (&s_hist[0][0])[x] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const uint32_t P = spec.P;
+  const uint64_t stride = (uint64_t)gridDim.x * DH_BLOCK;
+  // Every lane of a warp runs the same number of iterations so the votes
+  // below see the whole warp; lanes past the end carry no item.
+  const uint64_t warp_base = (uint64_t)blockIdx.x * DH_BLOCK + (threadIdx.x & ~31u);
+  for (uint64_t w0 = warp_base; w0 < m; w0 += stride) {
+    const uint64_t j = w0 + lane;
+    const bool valid = j < m;
+    const uint64_t key = valid ? keys[j] : 0ull;
+    const uint32_t nvalid = __popc(__ballot_sync(0xffffffffu, valid));
+    for (uint32_t p = 0; p < P; ++p) {
+      const uint32_t d = digit_of(key, spec.shift[p], spec.bits[p]);
+      const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
+      // Runs of equal digits are common (sorted group ids): one atomic per warp.
+      if (__all_sync(0xffffffffu, !valid || d == d0)) {
+        if (lane == 0) atomicAdd(&s_hist[p][d0], nvalid);
+      } else if (valid) {
+        atomicAdd(&s_hist[p][d], 1u);
+      }
+    }
+  }
+  __syncthreads();
+  for (uint32_t x = threadIdx.x; x < P * RADIX; x += DH_BLOCK) {
+    uint32_t v = (&s_hist[0][0])[x];
+    if (v) atomicAdd(&hist[x], v);
+  }
+}
+
+cudaError_t launch_digit_histogram(const uint64_t *keys, uint32_t m, const DigitSpec &spec,
+                                   uint32_t *hist, int num_sms, cudaStream_t stream) {
+  if (m == 0 || spec.P == 0) return cudaSuccess;
+  uint64_t want = ((uint64_t)m + DH_BLOCK - 1) / DH_BLOCK;
+  uint64_t cap = (uint64_t)num_sms * 8;
+  unsigned grid = (unsigned)(want > cap ? cap : want);
+  k_digit_histogram<<<grid, DH_BLOCK, 0, stream>>>(keys, m, spec, hist);
+  return cudaGetLastError();
+}
+
+// ---- 2. plan ---------------------------------------------------------------
+
+__global__ void __launch_bounds__(RADIX)
+k_sort_plan(const uint32_t *__restrict__ hist, uint32_t *__restrict__ digit_base, DigitSpec spec,
+            uint32_t m, uint64_t *ka, uint64_t *kb, uint32_t *va, uint32_t *vb,
+            SortPlan *plan, Ctrl *ctrl) {
+  __shared__ uint32_t s_tmp[RADIX / 32 + 1];
+  __shared__ uint32_t s_active[MAX_PASSES];
+  const uint32_t d = threadIdx.x;
+  for (uint32_t p = 0; p < spec.P; ++p) {
+    const uint32_t c = hist[p * RADIX + d];
+    uint32_t total;
+    const uint32_t excl = block_exclusive<RADIX>(c, OpAdd(), 0u, s_tmp, total);
+    digit_base[p * RADIX + d] = excl;
+    // A digit position is constant iff one bin holds every key.
+    const int constant = __syncthreads_or(c == m);
+    if (d == 0) s_active[p] = constant ? 0u : 1u;
+  }
+  __syncthreads();
+  if (d == 0) {
+    uint32_t cur = 0, kept = 0, mask = 0;
+    uint64_t *k[2] = {ka, kb};
+    uint32_t *v[2] = {va, vb};
+    for (uint32_t p = 0; p < MAX_PASSES; ++p) {
+      const uint32_t act = p < spec.P ? s_active[p] : 0u;
+      plan->active[p] = act;
+      plan->ksrc[p] = k[cur];
+      plan->vsrc[p] = v[cur];
+      plan->kdst[p] = k[cur ^ 1];
+      plan->vdst[p] = v[cur ^ 1];
+      if (act) {
+        cur ^= 1;
+        ++kept;
+        mask |= 1u << p;
+      }
+    }
+    plan->n_active = kept;
+    plan->final_idx = cur;
+    plan->kfinal = k[cur];
+    plan->vfinal = v[cur];
+    ctrl->passes = kept;
+    ctrl->pass_mask = mask;
+  }
+}
+
+cudaError_t launch_sort_plan(const uint32_t *hist, uint32_t *digit_base, const DigitSpec &spec,
+                             uint32_t m, uint64_t *ka, uint64_t *kb, uint32_t *va,
+                             uint32_t *vb, SortPlan *plan, Ctrl *ctrl, cudaStream_t stream) {
+  k_sort_plan<<<1, RADIX, 0, stream>>>(hist, digit_base, spec, m, ka, kb, va, vb, plan, ctrl);
+  return cudaGetLastError();
+}
+
+// ---- 3. one-sweep pass -----------------------------------------------------
+
+constexpr int OS_BLOCK = 256;  // == RADIX: thread d owns digit d in the look-back
+constexpr int OS_ITEMS = 16;
+constexpr int OS_TILE = OS_BLOCK * OS_ITEMS;
+constexpr int OS_WARPS = OS_BLOCK / 32;
+static_assert(OS_TILE == SORT_TILE, "tile size mismatch");
+static_assert(OS_BLOCK == RADIX, "one thread per digit");
+
+struct OsSmem {
+  uint64_t keys[OS_TILE];
+  uint32_t vals[OS_TILE];
+  uint32_t whist[OS_WARPS][RADIX];  // per-warp counts, then per-warp prefixes
+  uint32_t start[RADIX];            // tile-local start of each digit run
+  uint32_t goff[RADIX];             // global index of a run = goff + local index
+  uint32_t tmp[OS_WARPS + 1];
+  uint32_t tile;
+  uint32_t bail;
+};
+
+// Lanes of the warp holding the same digit (8 ballots, one per digit bit).
+__device__ __forceinline__ uint32_t peers_of(uint32_t d) {
+  uint32_t peers = 0xffffffffu;
+#pragma unroll
+  for (int b = 0; b < RADIX_BITS; ++b) {
+    const uint32_t bit = (d >> b) & 1u;
+    const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+    peers &= bit ? bal : ~bal;
+  }
+  return peers;
+}
+
+__global__ void __launch_bounds__(OS_BLOCK) k_onesweep(PassArgs a) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  OsSmem &S = *reinterpret_cast<OsSmem *>(smem_raw);
+  if (!a.plan->active[a.p]) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    S.tile = atomicAdd(a.tile_ctr, 1u);
+    S.bail = has_error(a.ctrl) ? 1u : 0u;
+  }
+  for (int x = tid; x < OS_WARPS * RADIX; x += OS_BLOCK) (&S.whist[0][0])[x] = 0;
+  __syncthreads();
+  if (S.bail) return;
+  const uint32_t tile = S.tile;
+  const uint64_t *__restrict__ ksrc = a.plan->ksrc[a.p];
+  const uint32_t *__restrict__ vsrc = a.plan->vsrc[a.p];
+  uint64_t *__restrict__ kdst = a.plan->kdst[a.p];
+  uint32_t *__restrict__ vdst = a.plan->vdst[a.p];
+  const uint64_t base = (uint64_t)tile * OS_TILE;
+  const uint32_t count = (uint32_t)min((uint64_t)OS_TILE, (uint64_t)a.m - base);
+
+  // Rank: warp-striped items, item k of lane l at warp*512 + k*32 + l, so
+  // the order (warp, k, lane) is the input order inside the tile.
+  uint64_t key[OS_ITEMS];
+  uint32_t pos[OS_ITEMS];
+  uint32_t *wh = S.whist[warp];
+  const uint32_t lt = lanemask_lt();
+  const uint32_t dmax = (1u << a.bits) - 1u;
+#pragma unroll
+  for (int k = 0; k < OS_ITEMS; ++k) {
+    const uint32_t li = warp * (32 * OS_ITEMS) + k * 32 + lane;
+    const bool valid = li < count;
+    key[k] = valid ? ksrc[base + li] : ~0ull;
+    // Items past the end take the largest digit and come last in the tile.
+    const uint32_t d = valid ? digit_of(key[k], a.shift, a.bits) : dmax;
+    const uint32_t peers = peers_of(d);
+    const uint32_t before = wh[d];
+    __syncwarp();
+    const uint32_t lower = peers & lt;
+    if (lower == 0) wh[d] = before + __popc(peers);
+    __syncwarp();
+    pos[k] = before + __popc(lower);
+  }
+  __syncthreads();
+
+  // Thread d: counts of digit d per warp -> per-warp exclusive prefixes.
+  const uint32_t d = tid;
+  uint32_t total = 0;
+#pragma unroll
+  for (int w = 0; w < OS_WARPS; ++w) {
+    const uint32_t c = S.whist[w][d];
+    S.whist[w][d] = total;
+    total += c;
+  }
+  const uint32_t invalid = OS_TILE - count;
+  const uint32_t mine = total - (d == dmax ? invalid : 0u);  // this tile's real count
+  uint32_t tile_total;
+  const uint32_t start = block_exclusive<OS_BLOCK>(total, OpAdd(), 0u, S.tmp, tile_total);
+  S.start[d] = start;
+
+  // Publish and look back (thread d owns the status word of digit d).
+  uint64_t *st = a.status + (uint64_t)tile * RADIX + d;
+  if (a.inject && tile == 0) {
+    // Test hook: this tile never publishes, so the next tile's wait expires.
+    if (d == 0) S.bail = 1;
+  } else if (tile == 0) {
+    status_store(st, status_word(a.epoch, ST_INC, mine));
+    S.goff[d] = a.digit_base[d] - start;
+  } else {
+    status_store(st, status_word(a.epoch, ST_AGG, mine));
+    uint32_t excl = 0;
+    if (look_back(a.status, RADIX, d, tile, a.epoch, OpAdd(), excl, a.ctrl, a.spin_limit)) {
+      status_store(st, status_word(a.epoch, ST_INC, excl + mine));
+      S.goff[d] = a.digit_base[d] + excl - start;
+    } else {
+      S.bail = 1;
+    }
+  }
+  __syncthreads();
+  if (S.bail) return;
+
+  // Stage the tile in digit order, then write each digit run contiguously.
+#pragma unroll
+  for (int k = 0; k < OS_ITEMS; ++k) {
+    const uint32_t li = warp * (32 * OS_ITEMS) + k * 32 + lane;
+    const uint32_t dk = li < count ? digit_of(key[k], a.shift, a.bits) : dmax;
+    pos[k] += S.start[dk] + S.whist[warp][dk];
+    S.keys[pos[k]] = key[k];
+  }
+#pragma unroll
+  for (int k = 0; k < OS_ITEMS; ++k) {
+    const uint32_t li = warp * (32 * OS_ITEMS) + k * 32 + lane;
+    S.vals[pos[k]] = li < count ? vsrc[base + li] : 0u;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < OS_ITEMS; ++k) {
+    const uint32_t q = k * OS_BLOCK + tid;
+    if (q < count) {
+      const uint64_t kk = S.keys[q];
+      const uint32_t g = S.goff[digit_of(kk, a.shift, a.bits)] + q;
+      if (g < a.m) {
+        kdst[g] = kk;
+        vdst[g] = S.vals[q];
+      } else {  // never taken unless the histogram and the pass disagree
+        raise_error(a.ctrl, ERR_INTERNAL, 2);
+      }
+    }
+  }
+}
+
+cudaError_t launch_onesweep(const PassArgs &a, cudaStream_t stream) {
+  if (a.m == 0) return cudaSuccess;
+  static bool configured = false;  // per process; the attribute is per function
+  const int smem = (int)sizeof(OsSmem);
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const uint64_t tiles = ((uint64_t)a.m + OS_TILE - 1) / OS_TILE;
+  k_onesweep<<<(unsigned)tiles, OS_BLOCK, smem, stream>>>(a);
+  return cudaGetLastError();
+}
+
+// ---- copy-back for the standalone sort ------------------------------------
+
+// When the last kept pass left the result in buffer B, copy it to A (the
+// caller's arrays). The decision is read from the device plan.
+__global__ void k_copy_back(const SortPlan *__restrict__ plan, uint64_t *__restrict__ ka,
+                            uint32_t *__restrict__ va, uint32_t m) {
+  if (plan->final_idx == 0) return;
+  const uint64_t *kb = plan->kfinal;
+  const uint32_t *vb = plan->vfinal;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m;
+       j += (uint64_t)gridDim.x * blockDim.x) {
+    ka[j] = kb[j];
+    va[j] = vb[j];
+  }
+}
+
+cudaError_t launch_copy_back(const SortPlan *plan, uint64_t *ka, uint32_t *va, uint32_t m,
+                             int num_sms, cudaStream_t stream) {
+  if (m == 0) return cudaSuccess;
+  uint64_t want = ((uint64_t)m + 255) / 256, cap = (uint64_t)num_sms * 8;
+  k_copy_back<<<(unsigned)(want > cap ? cap : want), 256, 0, stream>>>(plan, ka, va, m);
+  return cudaGetLastError();
+}
+
+}  // namespace gbsa

@@ -1,0 +1,104 @@
+// Host-side launchers of the gbsa kernels (one .cu file per step of the
+// method). All launches are asynchronous on `stream`.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace gbsa {
+
+// ---- step A0: alphabet (k_alphabet.cu) ----------------------------------
+// hist[256] += occurrences of each byte value in text[0, n). hist must be
+// zeroed by the caller.
+cudaError_t launch_byte_histogram(const uint8_t *text, uint64_t n, uint32_t *hist,
+                                  int num_sms, cudaStream_t stream);
+
+// ---- step A1: initial keys (k_pack.cu) ----------------------------------
+struct PackArgs {
+  const uint8_t *text;     // concatenated texts
+  uint32_t N;              // total characters
+  const uint32_t *seg_off; // S+1 ungapped offsets (device)
+  uint32_t S;              // number of texts
+  const uint8_t *code;     // dense order-preserving code of each byte (device)
+  uint32_t b;              // bits per character
+  uint32_t c0;             // characters per key
+  uint32_t cb;             // c0 * b (segment id sits above these bits)
+  uint64_t *keys;          // out: N keys, tail-first order per text
+  uint32_t *vals;          // out: N gapped positions
+};
+cudaError_t launch_pack(const PackArgs &a, cudaStream_t stream);
+
+// ---- step A2: radix sort (k_sort.cu) ------------------------------------
+// hist[P*256] += digit counts of keys[0, m) for the digits in spec.
+cudaError_t launch_digit_histogram(const uint64_t *keys, uint32_t m, const DigitSpec &spec,
+                                   uint32_t *hist, int num_sms, cudaStream_t stream);
+// Exclusive digit offsets, constant-digit skipping and buffer ping-pong.
+cudaError_t launch_sort_plan(const uint32_t *hist, uint32_t *digit_base, const DigitSpec &spec,
+                             uint32_t m, uint64_t *ka, uint64_t *kb, uint32_t *va,
+                             uint32_t *vb, SortPlan *plan, Ctrl *ctrl, cudaStream_t stream);
+// One stable one-sweep pass over digit p of the plan.
+struct PassArgs {
+  const SortPlan *plan;
+  int p;
+  uint32_t shift, bits;
+  const uint32_t *digit_base;  // 256 entries for this pass
+  uint32_t m;
+  uint64_t *status;  // >= tiles * 256 words
+  uint32_t epoch;
+  uint32_t *tile_ctr;
+  Ctrl *ctrl;
+  uint32_t spin_limit;
+  uint32_t inject;
+};
+constexpr int SORT_TILE = 256 * 16;
+cudaError_t launch_onesweep(const PassArgs &a, cudaStream_t stream);
+// Copies the plan's final buffer back to (ka, va) when it is buffer B.
+cudaError_t launch_copy_back(const SortPlan *plan, uint64_t *ka, uint32_t *va, uint32_t m,
+                             int num_sms, cudaStream_t stream);
+
+// ---- steps A3+A4: rename, unique test, discard (k_rename.cu) ------------
+struct RenameArgs {
+  const SortPlan *plan;      // sorted keys / gapped positions
+  uint32_t m;
+  uint32_t round0;           // 1: initial naming with the end-of-text rules
+  uint32_t cb;               // round 0: segment id = key >> cb (cb < 64)
+  uint32_t c0;               // round 0: characters per key
+  const uint32_t *seg_off;   // S+1 ungapped offsets
+  uint32_t S;
+  uint32_t W;                // later rounds: group ordinal g = key >> W
+  const uint32_t *base_in;   // later rounds: name - start of group g
+  uint32_t g_in;             // later rounds: groups in base_in (bounds guard)
+  uint32_t *isa;             // gapped ISA
+  uint64_t isa_len;          // entries of isa (bounds guard)
+  uint32_t N;                // total characters = entries of sa (bounds guard)
+  uint32_t *sa;              // SA of gapped positions
+  uint64_t *act_out;         // survivors: (g' << 32) | i'
+  uint32_t *base_out;        // name - start of each surviving group
+  uint64_t *status;          // >= 3 * tiles words
+  uint32_t epoch;
+  uint32_t *tile_ctr;
+  Ctrl *ctrl;
+  uint32_t spin_limit;
+};
+constexpr int RENAME_TILE = 256 * 16;
+cudaError_t launch_rename(const RenameArgs &a, cudaStream_t stream);
+
+// ---- step A5: partner names (k_gather.cu) -------------------------------
+// keys[j] = (g << W) | (ISA[i'+h] + 1 mod 2^32), vals[j] = i' for the
+// active list act[j] = (g << 32) | i'.
+// isa_len = entries of the ISA array (the gather index is clamped to it).
+cudaError_t launch_gather(const uint64_t *act, uint32_t m, uint32_t h, uint32_t W,
+                          const uint32_t *isa, uint64_t isa_len, uint64_t *keys, uint32_t *vals,
+                          cudaStream_t stream);
+
+// ---- output (k_gather.cu) ------------------------------------------------
+// Batched: sa[r] -= gapped start of the text that rank r belongs to.
+cudaError_t launch_sa_to_local(uint32_t *sa, uint32_t N, const uint32_t *seg_off, uint32_t S,
+                               cudaStream_t stream);
+// isa_out[p] = isa[p + s] - off_s for text s (single text: a copy).
+cudaError_t launch_isa_to_local(const uint32_t *isa, uint32_t *isa_out, uint32_t N,
+                                const uint32_t *seg_off, uint32_t S, cudaStream_t stream);
+
+}  // namespace gbsa

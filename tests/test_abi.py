@@ -1,0 +1,70 @@
+"""The C-ABI library (no GPU needed): it builds for sm_103a, loads, exports
+every entry point include/gbsa.h declares, and rejects bad arguments on
+the host before touching a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1610_03007_gb300 import _build
+    _build.build()
+    import paper_1610_03007_gb300 as gbsa
+    return gbsa.load()
+
+
+def declared_symbols():
+    with open(os.path.join(ROOT, "include", "gbsa.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(sa_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for s in ("sa_build", "sa_build_batched", "sa_build_ex", "sa_workspace_bytes",
+              "sa_status_string", "sa_build_host", "sa_sort_pairs"):
+        assert s in syms
+
+
+def test_every_declared_symbol_is_exported(lib):
+    import paper_1610_03007_gb300 as gbsa
+    syms = declared_symbols()
+    missing = [s for s in syms if not hasattr(lib, s)]
+    assert not missing
+    assert sorted(gbsa.EXPORTED) == syms
+
+
+def test_status_strings(lib):
+    import paper_1610_03007_gb300 as gbsa
+    for code, name in gbsa.STATUS_NAMES.items():
+        assert gbsa.status_string(code) == name
+
+
+def test_host_side_argument_checks(lib):
+    # These return before any CUDA call, so they run without a GPU.
+    assert lib.sa_build(None, (1 << 31) + 1, None, None) == 2      # too large
+    assert lib.sa_build(None, 10, None, None) == 1                 # null pointers
+    assert lib.sa_build(None, 0, None, None) == 0                  # empty text: ok
+    off = np.array([0, 5, 3], dtype=np.uint64)                     # decreasing
+    assert lib.sa_build_batched(None, off.ctypes.data, 2, None, None) == 1
+    off = np.array([1, 5], dtype=np.uint64)                        # offsets[0] != 0
+    assert lib.sa_build_batched(None, off.ctypes.data, 1, None, None) == 1
+    off = np.array([0, (1 << 31) + 1], dtype=np.uint64)
+    assert lib.sa_build_batched(None, off.ctypes.data, 1, None, None) == 2
+    assert lib.sa_sort_pairs(None, None, 10, 8, 8, None, 0, None) == 1   # empty bit range
+    assert lib.sa_sort_pairs(None, None, 10, 0, 65, None, 0, None) == 1
+
+
+def test_workspace_model(lib):
+    # About 41 bytes per character: keys A/B, values A/B, active list, ISA,
+    # group bases and look-back status.
+    for n in (1 << 20, 1 << 28, 1 << 31):
+        b = lib.sa_workspace_bytes(n)
+        assert 40 * n < b < 42 * n

@@ -1,0 +1,167 @@
+"""GPU parity: sa_build (through the C-ABI) against the CPU oracle, bit-exact.
+
+Every input is seeded and synthetic. The oracle runs prefix doubling with
+discarding (oracle/oracle.c); the GPU result must equal it element by
+element: SA, ISA and, with the same initial prefix length, the names of
+every position after every round.
+"""
+import numpy as np
+import pytest
+
+import gen
+from conftest import ints, read_golden
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1610_03007_gb300 as gbsa
+    assert torch.cuda.is_available()
+    return gbsa
+
+
+def dev_text(t):
+    import torch
+    a = np.frombuffer(bytes(t), dtype=np.uint8) if isinstance(t, (bytes, bytearray)) else t
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def gpu_sa(gb, t):
+    import torch
+    sa = gb.sa_build(dev_text(t))
+    torch.cuda.synchronize()
+    return sa.cpu().numpy().view(np.uint32)
+
+
+def test_paper_example_1_and_2(gb, orc):
+    g = read_golden("ex1_ex2_bdacbdacb.txt")
+    t = g["text"].encode()
+    assert list(gpu_sa(gb, t)) == ints(g["sa"])
+    # Example 2's names after every round, with the paper's 2-character
+    # initial names.
+    sa, isa, stats, trace = gb.sa_build_ex(dev_text(t), isa=True, h0_chars=2, trace_cap=8)
+    rows = [list(r) for r in trace[: stats["rounds"]].cpu().numpy()]
+    assert rows == [ints(g[f"names_{k}"]) for k in range(3)]
+    assert list(isa.cpu().numpy()) == ints(g["names_2"])
+
+
+def test_paper_example_3(gb):
+    g = read_golden("ex3_dbacbacbd.txt")
+    assert list(gpu_sa(gb, g["text"].encode())) == ints(g["sa"])
+    assert list(gpu_sa(gb, bytes(ints(g["sub_text_bytes"])))) == ints(g["sub_sa"])
+
+
+def test_degenerate_inputs(gb, orc):
+    assert gpu_sa(gb, b"").size == 0
+    assert list(gpu_sa(gb, b"x")) == [0]
+    for n in list(range(2, 70)) + [4095, 4096, 4097, 10000]:
+        for ch in (b"a", b"\x00", b"\xff"):
+            t = ch * n
+            assert list(gpu_sa(gb, t)) == list(range(n - 1, -1, -1)), (ch, n)
+    for m in (1, 2, 33, 1000, 2049):
+        t = b"ab" * m
+        want = list(range(2 * m - 2, -1, -2)) + list(range(2 * m - 1, 0, -2))
+        assert list(gpu_sa(gb, t)) == want
+    t = np.random.default_rng(1).permutation(256).astype(np.uint8)
+    assert np.array_equal(gpu_sa(gb, t), np.argsort(t))
+    # texts ending in runs of the smallest code (the end-of-text rule)
+    for tail in (b"\x00\x00", b"\x00" * 40, b"A" * 70):
+        t = b"CAGT" * 300 + tail
+        assert np.array_equal(gpu_sa(gb, t), orc.pd_sa(t)[0])
+
+
+def test_bruteforce_short_strings(gb, orc):
+    import itertools
+    for L in range(1, 11):
+        for tup in itertools.product(b"\x00\x01", repeat=L):
+            t = bytes(tup)
+            assert np.array_equal(gpu_sa(gb, t), orc.pd_sa(t)[0]), t
+
+
+@pytest.mark.parametrize("recipe", ["dna", "zipf_repeats", "markov", "zipf", "bytes"])
+@pytest.mark.parametrize("n", [1, 7, 100, 4095, 4097, 12289, 100003])
+def test_random_inputs(gb, orc, recipe, n):
+    t = gen.text(recipe, 7 * n + 1, n)
+    assert np.array_equal(gpu_sa(gb, t), orc.pd_sa(t)[0])
+
+
+@pytest.mark.parametrize("recipe,n", [("dna", 1 << 20), ("zipf_repeats", 1 << 20),
+                                      ("markov", 1 << 20), ("zipf_repeats", (1 << 21) + 12345)])
+def test_every_round_matches_the_oracle(gb, orc, recipe, n):
+    """Names after every round equal the oracle's with the same initial
+    prefix length (the key's c0 characters); SA and ISA equal at the end."""
+    t = gen.text(recipe, 31337, n)
+    sa, isa, stats, trace = gb.sa_build_ex(dev_text(t), isa=True, trace_cap=24)
+    c0 = stats["chars_per_key"]
+    osa, oisa, orounds, otrace = orc.pd_sa(t, h0=c0, trace_cap=24)
+    assert stats["rounds"] == orounds + 1
+    g = trace[: stats["rounds"]].cpu().numpy().view(np.uint32)
+    for k in range(stats["rounds"]):
+        assert np.array_equal(g[k], otrace[k]), f"round {k}"
+    assert np.array_equal(sa.cpu().numpy().view(np.uint32), osa)
+    assert np.array_equal(isa.cpu().numpy().view(np.uint32), oisa)
+
+
+def test_workload_1_full_size(gb, orc):
+    """Uniform DNA, n = 2^20: 32 characters per key resolve it in round 0."""
+    t = gen.text("dna", 1001, 1 << 20)
+    sa, _, stats, _ = gb.sa_build_ex(dev_text(t))
+    assert stats["chars_per_key"] == 32 and stats["bits_per_char"] == 2
+    assert np.array_equal(sa.cpu().numpy().view(np.uint32), orc.pd_sa(t)[0])
+
+
+@pytest.mark.parametrize("recipe", ["zipf_repeats", "markov"])
+def test_scaled_workloads_elementwise(gb, orc, recipe):
+    t = gen.text(recipe, 2002, 1 << 22)
+    assert np.array_equal(gpu_sa(gb, t), orc.pd_sa(t)[0])
+
+
+def test_workload_2_full_size_properties(gb, orc):
+    """n = 2^28 repeated Zipf text, in the benchmark's launch configuration:
+    the linear-time checker (permutation + adjacent order through the ranks),
+    direct comparison of sampled adjacent suffixes, and the oracle's rank of
+    sampled suffixes computed one by one."""
+    import torch
+    n = 1 << 28
+    t = gen.text("zipf_repeats", 2001, n)
+    d = dev_text(t)
+    ws = torch.empty(gb.workspace_bytes(n), dtype=torch.uint8, device="cuda")
+    sa, _, stats, _ = gb.sa_build_ex(d, workspace=ws)
+    s = sa.cpu().numpy().view(np.uint32)
+    del ws, sa, d
+    assert stats["rounds"] > 5
+    assert orc.check_sa(t, s) == (0, -1)
+    rng = np.random.default_rng(5)
+    assert orc.check_adjacent(t, s, rng.integers(0, n - 1, 20000)) == 0
+    isa_of = {}
+    for j in rng.integers(0, n, 3):
+        isa_of[int(s[j])] = int(j)
+    for i, j in isa_of.items():
+        assert orc.suffix_rank(t, i) == j
+
+
+def test_isa_output(gb):
+    t = gen.text("markov", 5, 300000)
+    sa, isa, _, _ = gb.sa_build_ex(dev_text(t), isa=True)
+    s = sa.cpu().numpy().view(np.uint32)
+    r = isa.cpu().numpy().view(np.uint32)
+    assert np.array_equal(r[s], np.arange(t.size, dtype=np.uint32))
+
+
+def test_host_entry_point(gb, orc):
+    t = gen.text("zipf_repeats", 77, 500000)
+    assert np.array_equal(gb.sa_build_host(t), orc.pd_sa(t)[0])
+
+
+def test_repeated_builds_reuse_workspace(gb, orc):
+    import torch
+    ws = torch.empty(gb.workspace_bytes(1 << 18), dtype=torch.uint8, device="cuda")
+    for seed in range(3):
+        for recipe in ("dna", "zipf_repeats"):
+            t = gen.text(recipe, seed, 1 << 18)
+            sa, _, _, _ = gb.sa_build_ex(dev_text(t), workspace=ws)
+            assert np.array_equal(sa.cpu().numpy().view(np.uint32), orc.pd_sa(t)[0])
