@@ -188,6 +188,25 @@ sa_status sa_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t m,
                         size_t ws_bytes, gbsa_stream_t stream);
 size_t sa_sort_workspace_bytes(uint64_t m);
 
+/* sa_build without any device memory allocation, for callers that must not
+ * allocate when they build: for example code running beside a serving
+ * engine or framework allocator that already reserved the GPU's memory, a
+ * latency-sensitive path that cannot afford cudaMalloc's implicit
+ * synchronisation, or a plug-in whose host forbids device allocation.
+ * The paper has no counterpart; this is a packaging of the same build.
+ * text, n, sa_out, stream: as for sa_build. n may be at most 2^18
+ * (262144); larger n returns SA_ERR_TOO_LARGE.
+ * The workspace is a 12 MiB array in the library's own device memory, held
+ * on every GPU that loads the library until the process exits. The first
+ * call on a device looks up that array's device address (a CUDA runtime
+ * query, once per device); make that first call before any stream capture
+ * begins on the device. All calls share the one array: calls whose GPU work
+ * overlaps race and give garbage, so serialise them (one stream, or an
+ * event between streams). Leftover contents from the previous call are
+ * harmless: every build clears what it needs. */
+sa_status sa_build_noalloc(const uint8_t *text, uint64_t n, uint32_t *sa_out,
+                           gbsa_stream_t stream);
+
 /* Human-readable name of a status code (static string). */
 const char *sa_status_string(sa_status s);
 

@@ -28,7 +28,8 @@ SA_MAX_ROUNDS = 64
 # Symbols include/gbsa.h declares; the loader checks that all are exported.
 EXPORTED = ("sa_build", "sa_workspace_bytes", "sa_build_ex", "sa_build_batched",
             "sa_batched_workspace_bytes", "sa_build_batched_ex", "sa_build_host",
-            "sa_sort_pairs", "sa_sort_workspace_bytes", "sa_status_string")
+            "sa_sort_pairs", "sa_sort_workspace_bytes", "sa_status_string",
+            "sa_build_noalloc")
 
 
 class SAError(RuntimeError):
@@ -102,13 +103,14 @@ def load(path: str | None = None):
     lib.sa_build_batched_ex.argtypes = [vp, vp, u32, vp, vp, sz, ctypes.POINTER(Options),
                                         ctypes.POINTER(Stats), vp]
     lib.sa_build_host.argtypes = [vp, u64, vp, vp]
+    lib.sa_build_noalloc.argtypes = [vp, u64, vp, vp]
     lib.sa_sort_pairs.argtypes = [vp, vp, u64, u32, u32, vp, sz, vp]
     lib.sa_sort_workspace_bytes.argtypes = [u64]
     lib.sa_sort_workspace_bytes.restype = sz
     lib.sa_status_string.argtypes = [ctypes.c_int]
     lib.sa_status_string.restype = ctypes.c_char_p
     for f in ("sa_build", "sa_build_ex", "sa_build_batched", "sa_build_batched_ex",
-              "sa_build_host", "sa_sort_pairs"):
+              "sa_build_host", "sa_sort_pairs", "sa_build_noalloc"):
         getattr(lib, f).restype = ctypes.c_int
     if path is None:
         _lib = lib
