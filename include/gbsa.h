@@ -90,9 +90,12 @@ enum {
   SA_K_PLAN = 3,      /* radix plan (one block)              */
   SA_K_ONESWEEP = 4,  /* radix passes (kept passes only)     */
   SA_K_RENAME = 5,    /* rename + unique + compaction        */
-  SA_K_GATHER = 6,    /* partner-name gather                 */
+  SA_K_GATHER = 6,    /* partner-name gather (large groups)  */
   SA_K_OUTPUT = 7,    /* output fix-ups                      */
-  SA_K_CLASSES = 8
+  SA_K_REFINE = 8,    /* small-group refine (rounds >= 1)    */
+  SA_K_SCATTER = 9,   /* deferred ISA updates                */
+  SA_K_CLASSIFY = 10, /* group classification, tile map      */
+  SA_K_CLASSES = 11
 };
 
 /* Per-build statistics (HOST struct filled by the _ex calls). */
@@ -124,7 +127,7 @@ typedef struct {
  * text   : DEVICE, n bytes, read only.
  * n      : length, 0 <= n <= SA_MAX_N.
  * sa_out : DEVICE, n uint32, written with SA.
- * The workspace (about 41 bytes per character) is allocated from a
+ * The workspace (about 61 bytes per character) is allocated from a
  * library-private stream-ordered pool on `stream` and returned to it.
  * n = 0 writes nothing; n = 1 writes sa_out[0] = 0. */
 sa_status sa_build(const uint8_t *text, uint64_t n, uint32_t *sa_out,
@@ -196,7 +199,7 @@ size_t sa_sort_workspace_bytes(uint64_t m);
  * The paper has no counterpart; this is a packaging of the same build.
  * text, n, sa_out, stream: as for sa_build. n may be at most 2^18
  * (262144); larger n returns SA_ERR_TOO_LARGE.
- * The workspace is a 12 MiB array in the library's own device memory, held
+ * The workspace is a 16 MiB array in the library's own device memory, held
  * on every GPU that loads the library until the process exits. The first
  * call on a device looks up that array's device address (a CUDA runtime
  * query, once per device); make that first call before any stream capture

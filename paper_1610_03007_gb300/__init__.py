@@ -45,7 +45,7 @@ class Options(ctypes.Structure):
 
 
 KERNEL_CLASSES = ("byte_hist", "pack", "digit_hist", "plan", "onesweep", "rename", "gather",
-                  "output")
+                  "output", "refine", "scatter", "classify")
 
 
 class Stats(ctypes.Structure):
@@ -58,9 +58,9 @@ class Stats(ctypes.Structure):
                 ("groups", ctypes.c_uint64 * SA_MAX_ROUNDS),
                 ("bytes_model", ctypes.c_uint64),
                 ("launches", ctypes.c_uint32),
-                ("kernel_ms", ctypes.c_double * 8),
-                ("kernel_launches", ctypes.c_uint64 * 8),
-                ("kernel_bytes", ctypes.c_uint64 * 8)]
+                ("kernel_ms", ctypes.c_double * 11),
+                ("kernel_launches", ctypes.c_uint64 * 11),
+                ("kernel_bytes", ctypes.c_uint64 * 11)]
 
     def to_dict(self) -> dict:
         r = self.rounds

@@ -29,17 +29,29 @@ constexpr int TILE_COUNTERS = 1024;
 
 enum DevError : uint32_t { ERR_NONE = 0, ERR_TIMEOUT = 1, ERR_INTERNAL = 2 };
 
+// Counters of one doubling round (cleared when the round starts). The next
+// active list is written by two producers: the small-group refine first
+// (survivors [0, m_s), groups [0, g_s)), then the rename of round 0 or of
+// the large groups (survivors [m_s, m_s + m_l), groups [g_s, g_s + g_l)).
+struct RoundCounts {
+  uint32_t m_s, g_s;        // survivors / groups written by the refine
+  uint32_t m_l, g_l;        // survivors / groups written by the rename
+  uint32_t upd;             // deferred ISA updates queued by the refine
+  uint32_t pad;
+  unsigned long long large; // classify: (large groups << 32) | large items
+};
+
 // Device-resident control block of one build (cleared at build start).
 struct Ctrl {
   uint32_t error;      // first DevError raised by any kernel
   uint32_t err_where;  // kernel id that raised it
-  uint32_t m_next;     // active suffixes after the last rename
-  uint32_t g_next;     // groups among them
   uint32_t passes;     // radix passes the last plan kept
   uint32_t pass_mask;  // bit p set iff pass p of the last plan was kept
-  uint32_t pad[2];
+  RoundCounts rc;
+  uint32_t zero[4];    // constant zeros (output offsets of round 0)
   uint32_t tile_ctr[TILE_COUNTERS];  // one dynamic tile counter per launch
 };
+static_assert(sizeof(RoundCounts) == 32, "RoundCounts layout");
 
 // Where each radix pass reads and writes; written on the device by the plan
 // kernel after the digit histograms are known (constant digits are skipped).
@@ -100,6 +112,61 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
+// ---- TMA bulk copies (global -> shared) behind an mbarrier -----------------
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// One 1-D bulk copy; dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for phase `parity` of an mbarrier guarding this block's own
+// bulk copies. On expiry the error is recorded, and the wait continues (again
+// bounded) so the block never leaves while its copies may still land.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, Ctrl *ctrl,
+                                                  uint32_t spin_limit) {
+  for (uint32_t i = 0; i < spin_limit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (i > 64) __nanosleep(256);
+  }
+  raise_error(ctrl, ERR_TIMEOUT, 5);
+  for (uint32_t i = 0; i < spin_limit; ++i) {
+    if (mbar_try_wait(bar, parity)) return false;
+    __nanosleep(1024);
+  }
+  return false;
+}
+
 // Waits until status word `p` carries this launch's epoch and a non-zero
 // state; returns false if the wait gave up (bounded).
 __device__ __forceinline__ bool status_wait(const uint64_t *p, uint32_t epoch, uint64_t &w,
@@ -134,6 +201,51 @@ __device__ __forceinline__ bool look_back(const uint64_t *status, uint32_t strid
     carry = op(carry, (uint32_t)w);
     if (((uint32_t)(w >> 32) & 3u) == ST_INC) return true;
     --pred;
+  }
+  return true;
+}
+
+// Sum look-back that reads a window of 4 predecessors per round trip
+// (independent loads), so a chain of tiles that have only published their
+// aggregates costs a quarter of the dependent latencies. `stride`/`slot`
+// address the status word of this thread's digit in each tile.
+__device__ __forceinline__ bool look_back_sum4(const uint64_t *status, uint32_t stride,
+                                               uint32_t slot, uint32_t tile, uint32_t epoch,
+                                               uint32_t &carry, Ctrl *ctrl, uint32_t spin_limit) {
+  int64_t p = (int64_t)tile - 1;
+  uint32_t spins = 0, ns = 32;
+  const uint32_t ep = epoch & EPOCH_MASK;
+  while (p >= 0) {
+    uint64_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      w[k] = (p - k >= 0) ? status_load(status + (size_t)(p - k) * stride + slot) : 0ull;
+    int used = 0;
+    bool done = false, blocked = false;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (!done && !blocked && p - k >= 0) {
+        const uint32_t tag = (uint32_t)(w[k] >> 32);
+        if ((tag >> 2) != ep || (tag & 3u) == 0u) {
+          blocked = true;
+        } else {
+          carry += (uint32_t)w[k];
+          ++used;
+          if ((tag & 3u) == ST_INC) done = true;
+        }
+      }
+    }
+    if (done) return true;
+    p -= used;
+    if (used == 0) {
+      if (++spins > spin_limit) {
+        raise_error(ctrl, ERR_TIMEOUT, 1);
+        return false;
+      }
+      if ((spins & 15u) == 0u && has_error(ctrl)) return false;
+      __nanosleep(ns);
+      if (ns < 1024) ns <<= 1;
+    }
   }
   return true;
 }

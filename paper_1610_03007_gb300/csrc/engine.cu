@@ -5,20 +5,25 @@
 //   byte histogram -> alphabet (host) -> packed keys -> radix sort ->
 //   rename/unique/compact.
 // Round r >= 1 (one doubling step, h = c0 * 2^(r-1) characters resolved):
-//   partner-name gather -> radix sort of (group, partner) keys ->
-//   rename/unique/compact.
+//   large groups: partner-name gather -> radix sort of (group, partner)
+//   keys; small groups: tile-local refine (k_refine.cu); then the rename of
+//   the large groups, the queued ISA updates and the classification of the
+//   new groups.
 // The loop ends when no suffix is active (every name unique; the paper's
 // loop bound is one round short, so the count decides). SA is complete then:
 // each suffix wrote SA[name] = i when its name became unique.
 //
-// Host <-> device per round: one 32-byte read of the control block (active
-// count, group count, pass count, error word) after the rename.
+// Host <-> device per round: one 64-byte read of the control block (active
+// and group counts of both producers, large-group counts, pass count, error
+// word) at the end of the round.
 //
 // Data layout in HBM (N characters in S texts, gapped positions N + S):
-//   keys A/B u64[N], vals A/B u32[N], active list u64[N] (g << 32 | i'),
-//   ISA u32[N + S + 1] (end slots hold 0xFFFFFFFF), group bases u32[N/2+1]
-//   x2, look-back status u64[tiles * 256] (sort) and u64[tiles * 3]
-//   (rename), control block, plan, histograms: about 41 bytes per character.
+//   keys A/B u64[N], vals A/B u32[N] (radix sort of round 0 and of large
+//   groups), active lists u64[N] x2 (g << 32 | i', current and next), queued
+//   ISA updates u64[N], ISA u32[N + S + 1] (end slots hold 0xFFFFFFFF),
+//   group starts and names u32[N/2+1] x2 each, large-group lists, the
+//   refine tile map, look-back status, control block, plan, histograms:
+//   about 61 bytes per character.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -40,8 +45,10 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
   size_t ctrl, plan, hist, dbase, bytehist, code, segoff;
-  size_t ka, kb, va, vb, act, isa, base0, base1, st_sort, st_ren, total;
+  size_t ka, kb, va, vb, act0, act1, upd, isa, gs0, gs1, gn0, gn1, lg, loff, lbase, tfirst;
+  size_t st_sort, st_ren, total;
   size_t st_sort_bytes, st_ren_bytes;
+  uint32_t max_groups, max_large, max_tiles;
 };
 
 Layout make_layout(uint64_t N, uint32_t S) {
@@ -64,10 +71,21 @@ Layout make_layout(uint64_t N, uint32_t S) {
   L.kb = take(Nm * 8);
   L.va = take(Nm * 4);
   L.vb = take(Nm * 4);
-  L.act = take(Nm * 8);
+  L.act0 = take(Nm * 8);
+  L.act1 = take(Nm * 8);
+  L.upd = take(Nm * 8);
   L.isa = take((N + S + 1) * 4);
-  L.base0 = take((Nm / 2 + 1) * 4);
-  L.base1 = take((Nm / 2 + 1) * 4);
+  L.max_groups = (uint32_t)(Nm / 2 + 1);
+  L.gs0 = take(((size_t)L.max_groups + 1) * 4);
+  L.gs1 = take(((size_t)L.max_groups + 1) * 4);
+  L.gn0 = take((size_t)L.max_groups * 4);
+  L.gn1 = take((size_t)L.max_groups * 4);
+  L.max_large = (uint32_t)(Nm / (REFINE_SMALL_MAX + 1) + 1);
+  L.lg = take((size_t)L.max_large * 4);
+  L.loff = take((size_t)L.max_large * 4);
+  L.lbase = take((size_t)L.max_large * 4);
+  L.max_tiles = (uint32_t)((Nm + REFINE_NOMINAL - 1) / REFINE_NOMINAL);
+  L.tfirst = take(((size_t)L.max_tiles + 1) * 4);
   const uint64_t ts = std::max<uint64_t>(1, (N + SORT_TILE - 1) / SORT_TILE);
   L.st_sort_bytes = ts * RADIX * 8;
   L.st_sort = take(L.st_sort_bytes);
@@ -141,9 +159,18 @@ struct PoolBuf {
     if (e_ != cudaSuccess) return SA_ERR_CUDA; \
   } while (0)
 
+// Mirror of the first 64 bytes of Ctrl.
 struct HostCtrl {
-  uint32_t error, err_where, m_next, g_next, passes, pass_mask, pad[2];
+  uint32_t error, err_where, passes, pass_mask;
+  uint32_t m_s, g_s, m_l, g_l, upd, pad;
+  unsigned long long large;
+  uint32_t zero[4];
+  uint32_t m_next() const { return m_s + m_l; }
+  uint32_t g_next() const { return g_s + g_l; }
+  uint32_t m_large() const { return (uint32_t)large; }
+  uint32_t g_large() const { return (uint32_t)(large >> 32); }
 };
+static_assert(sizeof(HostCtrl) == 64, "HostCtrl mirrors the head of Ctrl");
 
 struct Build {
   // inputs
@@ -163,8 +190,11 @@ struct Build {
   SortPlan *plan = nullptr;
   uint32_t *hist = nullptr, *dbase = nullptr, *bytehist = nullptr, *segoff = nullptr;
   uint8_t *code = nullptr;
-  uint64_t *ka = nullptr, *kb = nullptr, *act = nullptr, *st_sort = nullptr, *st_ren = nullptr;
-  uint32_t *va = nullptr, *vb = nullptr, *isa = nullptr, *base[2] = {nullptr, nullptr};
+  uint64_t *ka = nullptr, *kb = nullptr, *act[2] = {nullptr, nullptr}, *upd = nullptr;
+  uint64_t *st_sort = nullptr, *st_ren = nullptr;
+  uint32_t *va = nullptr, *vb = nullptr, *isa = nullptr;
+  uint32_t *gstart[2] = {nullptr, nullptr}, *gname[2] = {nullptr, nullptr};
+  uint32_t *lg = nullptr, *loff = nullptr, *lbase = nullptr, *tfirst = nullptr;
   // launch bookkeeping
   uint32_t epoch = 0, slot = 0;
   uint32_t spin = DEFAULT_SPIN_LIMIT;
@@ -203,10 +233,18 @@ struct Build {
     kb = at<uint64_t>(L.kb);
     va = at<uint32_t>(L.va);
     vb = at<uint32_t>(L.vb);
-    act = at<uint64_t>(L.act);
+    act[0] = at<uint64_t>(L.act0);
+    act[1] = at<uint64_t>(L.act1);
+    upd = at<uint64_t>(L.upd);
     isa = at<uint32_t>(L.isa);
-    base[0] = at<uint32_t>(L.base0);
-    base[1] = at<uint32_t>(L.base1);
+    gstart[0] = at<uint32_t>(L.gs0);
+    gstart[1] = at<uint32_t>(L.gs1);
+    gname[0] = at<uint32_t>(L.gn0);
+    gname[1] = at<uint32_t>(L.gn1);
+    lg = at<uint32_t>(L.lg);
+    loff = at<uint32_t>(L.loff);
+    lbase = at<uint32_t>(L.lbase);
+    tfirst = at<uint32_t>(L.tfirst);
     st_sort = at<uint64_t>(L.st_sort);
     st_ren = at<uint64_t>(L.st_ren);
   }
@@ -320,8 +358,10 @@ struct Build {
     return s;
   }
 
-  sa_status rename(uint32_t m, bool round0, uint32_t cb, uint32_t c0, uint32_t W, int bi,
-                   uint32_t g_in) {
+  // Rename of round 0 (all suffixes) or of the large groups of a later
+  // round; writes the next active list at the device-side offsets `off_in`.
+  sa_status rename(uint32_t m, bool round0, uint32_t cb, uint32_t c0, uint32_t W,
+                   const uint32_t *base_in, uint32_t g_in, int out, const uint32_t *off_in) {
     RenameArgs ra{};
     ra.plan = plan;
     ra.m = m;
@@ -331,14 +371,17 @@ struct Build {
     ra.seg_off = segoff;
     ra.S = S;
     ra.W = W;
-    ra.base_in = base[bi];
+    ra.base_in = base_in;
     ra.g_in = g_in;
     ra.isa = isa;
     ra.isa_len = N + S + 1;
     ra.N = (uint32_t)N;
     ra.sa = sa;
-    ra.act_out = act;
-    ra.base_out = base[bi ^ 1];
+    ra.act_out = act[out];
+    ra.gstart_out = gstart[out];
+    ra.gname_out = gname[out];
+    ra.off_in = off_in;
+    ra.cnt_out = &ctrl->rc.m_l;
     ra.status = st_ren;
     sa_status s = next_launch(ra.tile_ctr, ra.epoch);
     if (s != SA_OK) return s;
@@ -347,20 +390,45 @@ struct Build {
     return launch(SA_K_RENAME, 0, 0, [&] { return launch_rename(ra, st); });
   }
 
-  // Rename reads 12 bytes per item plus 4 per item for the ISA write, 4 per
-  // unique item (SA), 8 per survivor and 4 per surviving group.
-  static uint64_t rename_bytes(uint32_t m, const HostCtrl &hc) {
-    const uint64_t u = m - hc.m_next;
-    return 16ull * m + 4 * u + 8ull * hc.m_next + 4ull * hc.g_next;
+  // Large groups and the refine tile map of the list just written.
+  sa_status classify(int out, uint64_t cap_groups) {
+    ClassifyArgs ca{};
+    ca.gstart = gstart[out];
+    ca.gname = gname[out];
+    ca.lg = lg;
+    ca.loff = loff;
+    ca.lbase = lbase;
+    ca.tfirst = tfirst;
+    ca.max_groups = L.max_groups;
+    ca.max_tiles = L.max_tiles;
+    ca.ctrl = ctrl;
+    return launch(SA_K_CLASSIFY, 0, 8 * cap_groups, [&] { return launch_classify(ca, sm_count(), st); });
+  }
+
+  // Rename (round 0 or large groups) reads 12 bytes per item plus 4 per
+  // item for the ISA write, 4 per unique item (SA), 8 per survivor and 8
+  // per surviving group.
+  static uint64_t rename_bytes(uint32_t m, uint32_t surv, uint32_t groups) {
+    const uint64_t u = m - surv;
+    return 16ull * m + 4 * u + 8ull * surv + 8ull * groups;
+  }
+
+  // Refine: 8 bytes read and a 4-byte gather per item, 8 bytes of group
+  // table per input group, 8 per survivor and per new group, 4 (SA) per
+  // unique item, 8 per queued update.
+  static uint64_t refine_bytes(uint32_t m, uint32_t G, uint32_t surv, uint32_t groups,
+                               uint32_t upd_n) {
+    const uint64_t u = m - surv;
+    return 12ull * m + 8ull * G + 8ull * surv + 8ull * groups + 4 * u + 8ull * upd_n;
   }
 
   void record(uint32_t r, uint32_t m, const HostCtrl &hc, uint32_t kbits) {
     if (!stats || r >= SA_MAX_ROUNDS) return;
     stats->active[r] = m;
-    stats->unique[r] = m - hc.m_next;
-    stats->passes[r] = hc.passes;
+    stats->unique[r] = m - hc.m_next();
+    stats->passes[r] = kbits ? hc.passes : 0;
     stats->key_bits[r] = kbits;
-    stats->groups[r] = hc.g_next;
+    stats->groups[r] = hc.g_next();
   }
 
   sa_status run() {
@@ -424,7 +492,10 @@ struct Build {
     inject_pending = opt.inject_stall != 0;
     s = sort(N32, spec_for(bits0));
     if (s != SA_OK) return s;
-    s = rename(N32, true, cb, c0, 0, 1, 0);  // writes base[0]
+    int cur = 0;  // the active list, group starts and names of this round
+    s = rename(N32, true, cb, c0, 0, nullptr, 0, cur, ctrl->zero);
+    if (s != SA_OK) return s;
+    s = classify(cur, N / 2 + 1);
     if (s != SA_OK) return s;
     if (opt.trace_isa && opt.trace_cap > 0 && S == 1)
       CK(cudaMemcpyAsync(opt.trace_isa, isa, N * 4, cudaMemcpyDeviceToDevice, st));
@@ -432,40 +503,98 @@ struct Build {
     s = read_ctrl(hc);
     if (s != SA_OK) return s;
     uint32_t m = N32;
-    s = flush(hc.pass_mask, rename_bytes(m, hc));
+    const uint64_t rb0 = rename_bytes(m, hc.m_next(), hc.g_next());
+    s = flush(hc.pass_mask, rb0);
     if (s != SA_OK) return s;
     record(0, m, hc, bits0);
-    bytes += (uint64_t)hc.passes * 24 * m + rename_bytes(m, hc);
+    bytes += (uint64_t)hc.passes * 24 * m + rb0;
 
     // ---- rounds r >= 1: one doubling step each ----
     const uint32_t W = bits_for(N);  // r2 in [0, N]
     uint64_t h = c0;
-    int bi = 0;
     uint32_t round = 1;
-    while (hc.m_next > 0) {
+    while (hc.m_next() > 0) {
       if (round >= SA_MAX_ROUNDS || h > N) return SA_ERR_INTERNAL;
-      m = hc.m_next;
-      const uint32_t G = hc.g_next;
-      s = launch(SA_K_GATHER, 0, 24ull * m, [&] {
-        return launch_gather(act, m, (uint32_t)h, W, isa, N + S + 1, ka, va, st);
+      m = hc.m_next();
+      const uint32_t G = hc.g_next();
+      const uint32_t mL = hc.m_large(), GL = hc.g_large();
+      const int nxt = cur ^ 1;
+      CK(cudaMemsetAsync(&ctrl->rc, 0, sizeof(RoundCounts), st));
+      // Large groups: keys for the global radix sort (gathered before any
+      // name of this round changes).
+      uint32_t kbits = 0;
+      if (mL > 0) {
+        GatherLargeArgs ga{};
+        ga.act = act[cur];
+        ga.gstart = gstart[cur];
+        ga.lg = lg;
+        ga.loff = loff;
+        ga.mL = mL;
+        ga.GL = GL;
+        ga.h = (uint32_t)h;
+        ga.W = W;
+        ga.isa = isa;
+        ga.isa_len = N + S + 1;
+        ga.keys = ka;
+        ga.vals = va;
+        s = launch(SA_K_GATHER, 0, 24ull * mL, [&] { return launch_gather_large(ga, st); });
+        if (s != SA_OK) return s;
+        bytes += 24ull * mL;
+        kbits = W + (GL > 1 ? bits_for(GL - 1) : 0);
+        s = sort(mL, spec_for(kbits));
+        if (s != SA_OK) return s;
+      }
+      // Small groups: refined tile by tile; name changes are queued.
+      RefineArgs rf{};
+      rf.act = act[cur];
+      rf.gstart = gstart[cur];
+      rf.gname = gname[cur];
+      rf.tfirst = tfirst;
+      rf.m = m;
+      rf.G = G;
+      rf.tiles = (m + REFINE_NOMINAL - 1) / REFINE_NOMINAL;
+      rf.h = (uint32_t)h;
+      rf.W = W;
+      rf.isa = isa;
+      rf.isa_len = N + S + 1;
+      rf.N = N32;
+      rf.sa = sa;
+      rf.act_out = act[nxt];
+      rf.gstart_out = gstart[nxt];
+      rf.gname_out = gname[nxt];
+      rf.upd = upd;
+      rf.ctrl = ctrl;
+      s = launch(SA_K_REFINE, 0, 0, [&] { return launch_refine(rf, st); });
+      if (s != SA_OK) return s;
+      if (mL > 0) {
+        s = rename(mL, false, 0, 0, W, lbase, GL, nxt, &ctrl->rc.m_s);
+        if (s != SA_OK) return s;
+      }
+      s = launch(SA_K_SCATTER, 0, 0, [&] {
+        return launch_scatter_updates(upd, m, isa, N + S + 1, ctrl, sm_count(), st);
       });
       if (s != SA_OK) return s;
-      bytes += 24ull * m;
-      const uint32_t kbits = W + (G > 1 ? bits_for(G - 1) : 0);
-      s = sort(m, spec_for(kbits));
+      s = classify(nxt, G);
       if (s != SA_OK) return s;
-      s = rename(m, false, 0, 0, W, bi, G);
-      if (s != SA_OK) return s;
-      bi ^= 1;
       if (opt.trace_isa && round < opt.trace_cap && S == 1)
         CK(cudaMemcpyAsync(opt.trace_isa + (size_t)round * N, isa, N * 4,
                            cudaMemcpyDeviceToDevice, st));
       s = read_ctrl(hc);
       if (s != SA_OK) return s;
-      s = flush(hc.pass_mask, rename_bytes(m, hc));
+      // Settle the byte counts that depend on this round's results.
+      const uint64_t rbl = mL ? rename_bytes(mL, hc.m_l, hc.g_l) : 0;
+      const uint64_t rfb = refine_bytes(m - mL, G - GL, hc.m_s, hc.g_s, hc.upd);
+      if (prof && stats) {
+        for (Rec &r : recs) {
+          if (r.cls == SA_K_REFINE) r.bytes = rfb;
+          if (r.cls == SA_K_SCATTER) r.bytes = 12ull * hc.upd;
+        }
+      }
+      s = flush(hc.pass_mask, rbl);
       if (s != SA_OK) return s;
       record(round, m, hc, kbits);
-      bytes += (uint64_t)hc.passes * 24 * m + rename_bytes(m, hc);
+      bytes += (mL ? (uint64_t)hc.passes * 24 * mL : 0) + rbl + rfb + 12ull * hc.upd + 8ull * G;
+      cur = nxt;
       h *= 2;
       ++round;
     }

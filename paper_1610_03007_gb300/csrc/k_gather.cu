@@ -1,50 +1,13 @@
-// Step A5 — partner names through the inverse suffix array (Section 2.1,
-// Algorithm 4: the name of suffix i + 2^k, or the sentinel past the end).
+// Output fix-ups (step A7): the build works on gapped positions (text s
+// occupies [off_s + s, off_s + s + len_s), the slot after it is an end
+// sentinel of the ISA); these kernels turn them into per-text local indices.
 //
-// For every active item (g, i'): r2 = ISA[i' + h] + 1, where the slot after
-// each text holds 0xFFFFFFFF so the sentinel becomes 0 and sorts below every
-// real name (the paper's literal sentinel 0 would collide with the real name
-// 0). An active item always has i' + h <= the end slot of its text, because
-// a suffix with at most h characters already has a unique name. The sort key
-// is (g << W) | r2 with g the group ordinal (rounds keep groups in order)
-// and W = bits of the largest r2.
-//
-// Also the output fix-ups of the batched build (gapped positions -> local
-// indices).
-//
-// Bound: HBM; 8 bytes read + 4 bytes gathered (one 32-byte sector each when
-// the ISA exceeds L2) + 12 bytes written per item.
+// Bound: HBM; 8 bytes per character.
 #include "launch.h"
 
 namespace gbsa {
 
 constexpr int GA_BLOCK = 256;
-
-__global__ void __launch_bounds__(GA_BLOCK)
-k_gather(const uint64_t *__restrict__ act, uint32_t m, uint32_t h, uint32_t W,
-         const uint32_t *__restrict__ isa, uint64_t isa_last, uint64_t *__restrict__ keys,
-         uint32_t *__restrict__ vals) {
-  const uint64_t j = (uint64_t)blockIdx.x * GA_BLOCK + threadIdx.x;
-  if (j >= m) return;
-  const uint64_t a = act[j];
-  const uint32_t ip = (uint32_t)a;
-  const uint32_t g = (uint32_t)(a >> 32);
-  // ip + h never passes the end slot of its text; the clamp only keeps a
-  // logic error from reading outside the array.
-  const uint64_t at = min((uint64_t)ip + h, isa_last);
-  const uint32_t r2 = __ldg(isa + at) + 1u;
-  keys[j] = ((uint64_t)g << W) | r2;
-  vals[j] = ip;
-}
-
-cudaError_t launch_gather(const uint64_t *act, uint32_t m, uint32_t h, uint32_t W,
-                          const uint32_t *isa, uint64_t isa_len, uint64_t *keys, uint32_t *vals,
-                          cudaStream_t stream) {
-  if (m == 0) return cudaSuccess;
-  const uint64_t grid = ((uint64_t)m + GA_BLOCK - 1) / GA_BLOCK;
-  k_gather<<<(unsigned)grid, GA_BLOCK, 0, stream>>>(act, m, h, W, isa, isa_len - 1, keys, vals);
-  return cudaGetLastError();
-}
 
 __global__ void __launch_bounds__(GA_BLOCK)
 k_sa_to_local(uint32_t *sa, uint32_t N, const uint32_t *__restrict__ seg_off, uint32_t S) {

@@ -1,0 +1,490 @@
+// Rounds >= 1 of prefix doubling with discarding (Section 2.1, Algorithm 5)
+// when most active groups are small.
+//
+// After round 0 every active suffix belongs to a group of equal names, and
+// a group only ever splits into subgroups: the refinement of a round never
+// crosses group boundaries. So the sort of a round is a segmented sort, and
+// a group that fits one tile can be refined entirely inside one block:
+//
+//   k_refine (one tile = whole groups whose starts fall in a 2048-item
+//   window, at most 4096 items): load the tile's (g, i') from the active
+//   list, gather the partner names r2 = ISA[i' + h] + 1 (Algorithm 4), sort
+//   by (local group, r2) with a radix sort in shared memory, then rename
+//   (CmpName + max PrefixSum inside the tile; NameDiscarding's
+//   r + (subgroup start - group start)), write SA for suffixes that became
+//   unique, compact the survivors into the next active list and queue every
+//   changed name as an (i', new) update. Tiles share nothing but two atomic
+//   counters: the next list only needs each group contiguous, not in any
+//   particular group order (names are absolute ranks).
+//
+//   Partner names of a round must all be read before any name of that round
+//   changes (a mix of old and new names within one group would order
+//   suffixes wrongly), so the refine never writes the ISA itself:
+//   k_scatter_updates applies the queued updates after every gather of the
+//   round has finished.
+//
+// Groups larger than REFINE_SMALL_MAX take the global path: k_gather_large
+// builds (large-group ordinal, r2) keys, the one-sweep radix sort orders
+// them and k_rename renames them (after the refine, so its direct ISA
+// writes come after every gather).
+//
+// k_classify runs at the end of each round over the new group table: it
+// lists the large groups (one 64-bit atomic gives each its slot and its
+// item offset at once) and maps every refine tile to its first group.
+//
+// Bound: HBM. Refine per item: 8 bytes read, one 4-byte random gather,
+// 8 bytes per survivor, 4 bytes random SA write per unique item, 8 bytes
+// queued per changed name; the update scatter reads 8 and writes 4 random
+// bytes per changed name.
+#include "launch.h"
+
+namespace gbsa {
+
+// ---- classify -------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t *a, uint32_t n, uint32_t v) {
+  uint32_t lo = 0, hi = n;  // first index with a[i] >= v, or n
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (a[mid] < v)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256) k_classify(ClassifyArgs a) {
+  const uint32_t m = a.ctrl->rc.m_s + a.ctrl->rc.m_l;
+  const uint32_t G = a.ctrl->rc.g_s + a.ctrl->rc.g_l;
+  if (G > a.max_groups) {
+    raise_error(a.ctrl, ERR_INTERNAL, 6);
+    return;
+  }
+  const uint32_t tiles = (m + REFINE_NOMINAL - 1) / REFINE_NOMINAL;
+  if (tiles > a.max_tiles) {
+    raise_error(a.ctrl, ERR_INTERNAL, 7);
+    return;
+  }
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t total = (uint64_t)(G > tiles + 1 ? G : tiles + 1);
+  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += stride) {
+    if (x < G) {
+      const uint32_t s = a.gstart[x];
+      const uint32_t e = x + 1 < G ? a.gstart[x + 1] : m;
+      const uint32_t size = e - s;
+      if (size > REFINE_SMALL_MAX) {
+        const unsigned long long old =
+            atomicAdd(&a.ctrl->rc.large, (1ull << 32) | (unsigned long long)size);
+        const uint32_t k = (uint32_t)(old >> 32), off = (uint32_t)old;
+        a.lg[k] = (uint32_t)x;
+        a.loff[k] = off;
+        a.lbase[k] = a.gname[x] - off;
+      }
+    }
+    if (x <= tiles) a.tfirst[x] = lower_bound_u32(a.gstart, G, (uint32_t)x * REFINE_NOMINAL);
+    if (x == 0) a.gstart[G] = m;
+  }
+}
+
+cudaError_t launch_classify(const ClassifyArgs &a, int num_sms, cudaStream_t stream) {
+  k_classify<<<num_sms * 4, 256, 0, stream>>>(a);
+  return cudaGetLastError();
+}
+
+// ---- large groups: keys for the global radix sort ---------------------------
+
+__global__ void __launch_bounds__(256) k_gather_large(GatherLargeArgs a) {
+  const uint64_t j64 = (uint64_t)blockIdx.x * 256 + threadIdx.x;
+  if (j64 >= a.mL) return;
+  const uint32_t j = (uint32_t)j64;
+  // k = the large group holding item j: the last k with loff[k] <= j
+  uint32_t lo = 0, hi = a.GL - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (__ldg(a.loff + mid) <= j)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const uint32_t g = __ldg(a.lg + lo);
+  const uint64_t e = a.act[__ldg(a.gstart + g) + (j - __ldg(a.loff + lo))];
+  const uint32_t ip = (uint32_t)e;
+  const uint64_t at = min((uint64_t)ip + a.h, a.isa_len - 1);
+  const uint32_t r2 = __ldg(a.isa + at) + 1u;
+  a.keys[j] = ((uint64_t)lo << a.W) | r2;
+  a.vals[j] = ip;
+}
+
+cudaError_t launch_gather_large(const GatherLargeArgs &a, cudaStream_t stream) {
+  if (a.mL == 0) return cudaSuccess;
+  k_gather_large<<<(unsigned)(((uint64_t)a.mL + 255) / 256), 256, 0, stream>>>(a);
+  return cudaGetLastError();
+}
+
+// ---- small groups: one tile per block ---------------------------------------
+
+constexpr int RF_BLOCK = 256;
+constexpr int RF_ITEMS = REFINE_CAP / RF_BLOCK;  // 16
+constexpr int RF_WARPS = RF_BLOCK / 32;
+constexpr int RF_MAXG = REFINE_NOMINAL / 2 + 1;  // groups have >= 2 members
+constexpr int RF_GPT = (RF_MAXG + RF_BLOCK - 1) / RF_BLOCK;  // groups per thread in scans
+
+struct RfSmem {
+  uint64_t keys[REFINE_CAP + REFINE_CAP / 16];  // padded (e + e/16) after the last pass
+  uint32_t vals[REFINE_CAP + REFINE_CAP / 32];  // padded (e + e/32) after the last pass
+  uint32_t whist[RF_WARPS][RADIX];
+  uint32_t dstart[RADIX];
+  uint32_t gname[RF_MAXG];
+  uint32_t gsrc[RF_MAXG];      // first position of the local group in the active list
+  uint32_t goff[RF_MAXG + 1];  // start of the local group in the tile (large groups: empty)
+  uint32_t tmp[RF_WARPS + 1];
+  uint32_t nitems, all_small, upd_base, surv_base, grp_base;
+  unsigned long long orv;
+};
+
+__device__ __forceinline__ uint32_t rf_peers(uint32_t d) {
+  uint32_t peers = 0xffffffffu;
+#pragma unroll
+  for (int b = 0; b < RADIX_BITS; ++b) {
+    const uint32_t bit = (d >> b) & 1u;
+    const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+    peers &= bit ? bal : ~bal;
+  }
+  return peers;
+}
+
+// Stable LSD radix sort of S.keys/S.vals[0, cnt) in shared memory over the
+// 8-bit digits below `nbits` that vary inside the tile. Warp w ranks the
+// contiguous chunk [w*C, (w+1)*C) with C = 32 * ceil(cnt / 256), so every
+// warp does the same useful work and (warp, slot, lane) is the input order.
+// The last pass writes the padded layout read by the rename phase (at
+// least one pass always runs).
+__device__ void rf_tile_sort(RfSmem &S, uint32_t cnt, unsigned long long varying, uint32_t nbits) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t lt = lanemask_lt();
+  const uint32_t K = (cnt + RF_BLOCK - 1) / RF_BLOCK;  // slots per lane, <= RF_ITEMS
+  const uint32_t chunk = K * 32;
+  const uint32_t ndig = (nbits + RADIX_BITS - 1) / RADIX_BITS;
+  uint32_t last = 0;
+  for (uint32_t p = 0; p < ndig; ++p)
+    if ((varying >> (p * RADIX_BITS)) & 0xFFull) last = p;
+  for (uint32_t p = 0; p <= last; ++p) {
+    const bool kept = ((varying >> (p * RADIX_BITS)) & 0xFFull) != 0ull;
+    if (!kept && p != last) continue;
+    const uint32_t shift = p * RADIX_BITS;
+    const bool pad = p == last;
+    for (int x = tid; x < RF_WARPS * RADIX; x += RF_BLOCK) (&S.whist[0][0])[x] = 0;
+    __syncthreads();
+    uint64_t key[RF_ITEMS];
+    uint32_t val[RF_ITEMS], pos[RF_ITEMS];
+    uint32_t *wh = S.whist[warp];
+#pragma unroll
+    for (int k = 0; k < RF_ITEMS; ++k) {
+      if ((uint32_t)k < K) {
+        const uint32_t li = warp * chunk + k * 32 + lane;
+        const bool valid = li < cnt;
+        key[k] = valid ? S.keys[li] : ~0ull;
+        val[k] = valid ? S.vals[li] : 0u;
+        const uint32_t d = valid ? (uint32_t)(key[k] >> shift) & 0xFFu : 0xFFu;
+        const uint32_t peers = rf_peers(d);
+        const uint32_t before = wh[d];
+        __syncwarp();
+        const uint32_t lower = peers & lt;
+        if (lower == 0) wh[d] = before + __popc(peers);
+        __syncwarp();
+        pos[k] = before + __popc(lower);
+      }
+    }
+    __syncthreads();
+    {
+      const uint32_t d = tid;
+      uint32_t total = 0;
+#pragma unroll
+      for (int w = 0; w < RF_WARPS; ++w) {
+        const uint32_t c = S.whist[w][d];
+        S.whist[w][d] = total;
+        total += c;
+      }
+      uint32_t tt;
+      S.dstart[d] = block_exclusive<RF_BLOCK>(total, OpAdd(), 0u, S.tmp, tt);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < RF_ITEMS; ++k) {
+      const uint32_t li = warp * chunk + k * 32 + lane;
+      if ((uint32_t)k < K && li < cnt) {
+        const uint32_t d = (uint32_t)(key[k] >> shift) & 0xFFu;
+        const uint32_t q = S.dstart[d] + S.whist[warp][d] + pos[k];
+        S.keys[pad ? q + (q >> 4) : q] = key[k];
+        S.vals[pad ? q + (q >> 5) : q] = val[k];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(RF_BLOCK, 3) k_refine(RefineArgs a) {
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  RfSmem &S = *reinterpret_cast<RfSmem *>(smem_raw);
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    S.orv = 0ull;
+    S.nitems = has_error(a.ctrl) ? 1u : 0u;  // borrowed as the bail flag
+  }
+  __syncthreads();
+  if (S.nitems) return;
+  const uint32_t tile = blockIdx.x;
+  const uint32_t g0 = __ldg(a.tfirst + tile), g1 = __ldg(a.tfirst + tile + 1);
+  const uint32_t ng = g1 - g0;
+  if (ng > (uint32_t)RF_MAXG) {  // never taken unless a logic error
+    if (tid == 0) raise_error(a.ctrl, ERR_INTERNAL, 8);
+    return;
+  }
+  if (ng == 0) return;
+
+  // Local group table: name, source position, size (0 for a large group),
+  // then exclusive offsets inside the tile.
+  uint32_t sz[RF_GPT];
+  uint32_t mysum = 0, mybig = 0;
+#pragma unroll
+  for (int r = 0; r < RF_GPT; ++r) {
+    const uint32_t lg = tid * RF_GPT + r;
+    sz[r] = 0;
+    if (lg < ng) {
+      const uint32_t g = g0 + lg;
+      const uint32_t s = __ldg(a.gstart + g), e = __ldg(a.gstart + g + 1);
+      S.gsrc[lg] = s;
+      S.gname[lg] = __ldg(a.gname + g);
+      const uint32_t size = e - s;
+      if (size <= REFINE_SMALL_MAX)
+        sz[r] = size;
+      else
+        mybig = 1;
+      mysum += sz[r];
+    }
+  }
+  uint32_t nitems;
+  uint32_t run = block_exclusive<RF_BLOCK>(mysum, OpAdd(), 0u, S.tmp, nitems);
+#pragma unroll
+  for (int r = 0; r < RF_GPT; ++r) {
+    const uint32_t lg = tid * RF_GPT + r;
+    if (lg < ng) S.goff[lg] = run;
+    run += sz[r];
+  }
+  const int any_big = __syncthreads_or(mybig);
+  if (tid == 0) {
+    S.goff[ng] = nitems;
+    S.nitems = nitems;
+    S.all_small = any_big ? 0u : 1u;
+  }
+  __syncthreads();
+  if (nitems > REFINE_CAP) {  // never taken unless a logic error
+    if (tid == 0) raise_error(a.ctrl, ERR_INTERNAL, 9);
+    return;
+  }
+  const uint32_t cnt = nitems;
+  if (cnt == 0) return;
+  const uint32_t K = (cnt + RF_BLOCK - 1) / RF_BLOCK;
+
+  // Load (g, i') and gather the partner names; all loads of a thread are
+  // issued before their uses.
+  uint64_t ent[RF_ITEMS];
+#pragma unroll
+  for (int k = 0; k < RF_ITEMS; ++k) {
+    const uint32_t q = k * RF_BLOCK + tid;
+    ent[k] = 0ull;
+    if ((uint32_t)k < K && q < cnt) {
+      uint32_t src;
+      if (S.all_small) {
+        src = S.gsrc[0] + q;
+      } else {
+        uint32_t lo = 0, hi = ng - 1;  // last local group with goff <= q
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi + 1) >> 1;
+          if (S.goff[mid] <= q)
+            lo = mid;
+          else
+            hi = mid - 1;
+        }
+        src = S.gsrc[lo] + (q - S.goff[lo]);
+      }
+      ent[k] = a.act[src];
+    }
+  }
+  uint32_t r2v[RF_ITEMS];
+#pragma unroll
+  for (int k = 0; k < RF_ITEMS; ++k) {
+    const uint32_t q = k * RF_BLOCK + tid;
+    r2v[k] = 0;
+    if ((uint32_t)k < K && q < cnt) {
+      const uint64_t at = min((uint64_t)(uint32_t)ent[k] + a.h, a.isa_len - 1);
+      r2v[k] = __ldg(a.isa + at) + 1u;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < RF_ITEMS; ++k) {
+    const uint32_t q = k * RF_BLOCK + tid;
+    if ((uint32_t)k < K && q < cnt) {
+      const uint32_t lgq = (uint32_t)(ent[k] >> 32) - g0;
+      S.keys[q] = ((uint64_t)lgq << a.W) | r2v[k];
+      S.vals[q] = (uint32_t)ent[k];
+    }
+  }
+  __syncthreads();
+  {
+    const uint64_t key0 = S.keys[0];
+    unsigned long long orv = 0ull;
+#pragma unroll
+    for (int k = 0; k < RF_ITEMS; ++k) {
+      const uint32_t q = k * RF_BLOCK + tid;
+      if ((uint32_t)k < K && q < cnt) orv |= S.keys[q] ^ key0;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) orv |= __shfl_xor_sync(0xffffffffu, orv, d);
+    if ((tid & 31) == 0 && orv) atomicOr(&S.orv, orv);
+  }
+  __syncthreads();
+  const uint32_t gbits = ng > 1 ? 32u - __clz(ng - 1) : 0u;
+  rf_tile_sort(S, cnt, S.orv, a.W + gbits);
+
+  // Rename in blocked layout: items tid*K .. tid*K+K-1 of the sorted tile.
+  const uint32_t l0 = tid * K;
+  bool f[RF_ITEMS + 1];
+  {
+    uint64_t prev = 0ull;
+    if (l0 > 0 && l0 - 1 < cnt) {
+      const uint32_t e = l0 - 1;
+      prev = S.keys[e + (e >> 4)];
+    }
+#pragma unroll
+    for (int k = 0; k <= RF_ITEMS; ++k) {
+      const uint32_t j = l0 + k;
+      f[k] = true;
+      if ((uint32_t)k <= K && j < cnt) {
+        const uint64_t kcur = S.keys[j + (j >> 4)];
+        f[k] = (j == 0) || kcur != prev;
+        prev = kcur;
+      }
+    }
+  }
+  uint32_t th_head = 0, th_surv = 0, th_hs = 0;
+#pragma unroll
+  for (int k = 0; k < RF_ITEMS; ++k) {
+    const uint32_t j = l0 + k;
+    if ((uint32_t)k < K && j < cnt) {
+      const bool uniq = f[k] && f[k + 1];
+      if (f[k]) th_head = j;
+      if (!uniq) {
+        ++th_surv;
+        if (f[k]) ++th_hs;
+      }
+    }
+  }
+  uint32_t tot_head;
+  const uint32_t ex_head = block_exclusive<RF_BLOCK>(th_head, OpMax(), 0u, S.tmp, tot_head);
+  // Names change for every item outside its group's first subgroup.
+  uint32_t th_chg = 0;
+  {
+    uint32_t rh = ex_head;
+#pragma unroll
+    for (int k = 0; k < RF_ITEMS; ++k) {
+      const uint32_t j = l0 + k;
+      if ((uint32_t)k < K && j < cnt) {
+        if (f[k]) rh = j;
+        const uint32_t lgq = (uint32_t)(S.keys[j + (j >> 4)] >> a.W);
+        if (rh != S.goff[lgq]) ++th_chg;
+      }
+    }
+  }
+  uint32_t tot_surv, tot_hs, tot_chg;
+  const uint32_t ex_surv = block_exclusive<RF_BLOCK>(th_surv, OpAdd(), 0u, S.tmp, tot_surv);
+  const uint32_t ex_hs = block_exclusive<RF_BLOCK>(th_hs, OpAdd(), 0u, S.tmp, tot_hs);
+  const uint32_t ex_chg = block_exclusive<RF_BLOCK>(th_chg, OpAdd(), 0u, S.tmp, tot_chg);
+
+  // Output space: the next active list only needs each group contiguous, so
+  // one 64-bit atomic reserves this tile's survivors (low word) and groups
+  // (high word) together, keeping group starts increasing with the group
+  // ordinal. Queued updates take one more atomic.
+  if (tid == 0) {
+    const unsigned long long inc = ((unsigned long long)tot_hs << 32) | tot_surv;
+    const unsigned long long old =
+        (tot_surv | tot_hs) ? atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctrl->rc.m_s), inc)
+                            : 0ull;
+    S.surv_base = (uint32_t)old;
+    S.grp_base = (uint32_t)(old >> 32);
+    S.upd_base = tot_chg ? atomicAdd(&a.ctrl->rc.upd, tot_chg) : 0u;
+  }
+  __syncthreads();
+  uint32_t run_head = ex_head;
+  uint32_t run_surv = S.surv_base + ex_surv;
+  uint32_t run_hs = S.grp_base + ex_hs;
+  uint32_t run_chg = S.upd_base + ex_chg;
+#pragma unroll
+  for (int k = 0; k < RF_ITEMS; ++k) {
+    const uint32_t j = l0 + k;
+    if ((uint32_t)k < K && j < cnt) {
+      if (f[k]) run_head = j;
+      const uint64_t kk = S.keys[j + (j >> 4)];
+      const uint32_t ip = S.vals[j + (j >> 5)];
+      const uint32_t lgq = (uint32_t)(kk >> a.W);
+      const uint32_t gs = S.goff[lgq];
+      const uint32_t name = S.gname[lgq] + (run_head - gs);
+      if (name >= a.N || ip >= a.isa_len) {  // never taken unless a logic error
+        raise_error(a.ctrl, ERR_INTERNAL, 10);
+        continue;
+      }
+      if (run_head != gs) a.upd[run_chg++] = ((uint64_t)name << 32) | ip;
+      if (f[k] && f[k + 1]) {
+        a.sa[name] = ip;
+      } else {
+        if (f[k]) {
+          a.gstart_out[run_hs] = run_surv;
+          a.gname_out[run_hs] = name;
+          ++run_hs;
+        }
+        a.act_out[run_surv] = ((uint64_t)(run_hs - 1) << 32) | ip;
+        ++run_surv;
+      }
+    }
+  }
+}
+
+cudaError_t launch_refine(const RefineArgs &a, cudaStream_t stream) {
+  if (a.tiles == 0) return cudaSuccess;
+  static bool configured = false;
+  const int smem = (int)sizeof(RfSmem);
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_refine, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  k_refine<<<a.tiles, RF_BLOCK, smem, stream>>>(a);
+  return cudaGetLastError();
+}
+
+// ---- deferred ISA updates -----------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_scatter_updates(const uint64_t *__restrict__ upd,
+                                                        uint32_t max_upd, uint32_t *isa,
+                                                        uint64_t isa_len, Ctrl *ctrl) {
+  const uint32_t n = min(ctrl->rc.upd, max_upd);
+  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+       x += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t u = upd[x];
+    const uint32_t ip = (uint32_t)u;
+    if (ip < isa_len) isa[ip] = (uint32_t)(u >> 32);
+  }
+}
+
+cudaError_t launch_scatter_updates(const uint64_t *upd, uint32_t max_upd, uint32_t *isa,
+                                   uint64_t isa_len, Ctrl *ctrl, int num_sms,
+                                   cudaStream_t stream) {
+  k_scatter_updates<<<num_sms * 8, 256, 0, stream>>>(upd, max_upd, isa, isa_len, ctrl);
+  return cudaGetLastError();
+}
+
+}  // namespace gbsa

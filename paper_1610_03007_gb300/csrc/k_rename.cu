@@ -9,14 +9,18 @@
 //    (f_j' ? j' : 0), a device-wide max-scan with decoupled look-back.
 //  - New name (NameDiscarding, Algorithms 5/6, in head-rank form): round 0
 //    new_j = s_j; later rounds new_j = r + (s_j - group start), stored as
-//    base[g] + s_j with base[g] = r - group start of group g.
+//    base[g] + s_j with base[g] = r - group start of group g (this kernel
+//    renames the large groups after rounds >= 1; k_refine.cu renames the
+//    small ones).
 //  - Unique (Algorithm 6): new_j differs from both neighbours, i.e.
 //    f_j and f_{j+1} (f_m = 1).
 //  - Discarding (Algorithm 5): ISA[i] = new for every item; a unique item is
 //    final and writes SA[new] = i; the others are compacted, in order, into
 //    the next active list with their group ordinal g', and each group's head
-//    records base'[g'] = new - its position in that list. Offsets come from
-//    two device-wide sums (survivors, group heads) with decoupled look-back.
+//    records its start in that list and its name (gstart'[g'], gname'[g']).
+//    Offsets come from two device-wide sums (survivors, group heads) with
+//    decoupled look-back, added to output offsets read from the device (the
+//    small-group refine of the same round writes first).
 //
 // All partner names of a round were gathered by an earlier kernel, so the
 // ISA writes here never race with reads of the same round.
@@ -162,13 +166,14 @@ __global__ void __launch_bounds__(RN_BLOCK) k_rename(RenameArgs a) {
   __syncthreads();
   if (S.bail) return;
   if (tid == 0 && base + count == a.m) {
-    a.ctrl->m_next = S.carry[1] + tot_surv;
-    a.ctrl->g_next = S.carry[2] + tot_hs;
+    a.cnt_out[0] = S.carry[1] + tot_surv;
+    a.cnt_out[1] = S.carry[2] + tot_hs;
   }
+  const uint32_t m_off = __ldg(a.off_in), g_off = __ldg(a.off_in + 1);
 
   uint32_t run_head = S.carry[0] > ex_head ? S.carry[0] : ex_head;
-  uint32_t run_surv = S.carry[1] + ex_surv;
-  uint32_t run_hs = S.carry[2] + ex_hs;
+  uint32_t run_surv = m_off + S.carry[1] + ex_surv;
+  uint32_t run_hs = g_off + S.carry[2] + ex_hs;
 #pragma unroll
   for (int k = 0; k < RN_ITEMS; ++k) {
     if (l0 + k < count) {
@@ -192,7 +197,8 @@ __global__ void __launch_bounds__(RN_BLOCK) k_rename(RenameArgs a) {
       } else {
         if (f[k]) {
           ++run_hs;
-          a.base_out[run_hs - 1] = name - run_surv;
+          a.gstart_out[run_hs - 1] = run_surv;
+          a.gname_out[run_hs - 1] = name;
         }
         a.act_out[run_surv] = ((uint64_t)(run_hs - 1) << 32) | ip;
         ++run_surv;

@@ -134,7 +134,7 @@ static_assert(OS_TILE == SORT_TILE, "tile size mismatch");
 static_assert(OS_BLOCK == RADIX, "one thread per digit");
 
 struct OsSmem {
-  uint64_t keys[OS_TILE];
+  uint64_t keys[OS_TILE];           // tile in input order, then in digit order
   uint32_t vals[OS_TILE];
   uint32_t whist[OS_WARPS][RADIX];  // per-warp counts, then per-warp prefixes
   uint32_t start[RADIX];            // tile-local start of each digit run
@@ -142,6 +142,7 @@ struct OsSmem {
   uint32_t tmp[OS_WARPS + 1];
   uint32_t tile;
   uint32_t bail;
+  uint64_t bar;                     // completion of the tile's bulk copies
 };
 
 // Lanes of the warp holding the same digit (8 ballots, one per digit bit).
@@ -156,14 +157,17 @@ __device__ __forceinline__ uint32_t peers_of(uint32_t d) {
   return peers;
 }
 
-__global__ void __launch_bounds__(OS_BLOCK) k_onesweep(PassArgs a) {
-  extern __shared__ __align__(16) uint8_t smem_raw[];
+// Three blocks per SM: registers capped at 85 per thread, ~59 KB of
+// shared memory per block.
+__global__ void __launch_bounds__(OS_BLOCK, 3) k_onesweep(PassArgs a) {
+  extern __shared__ __align__(128) uint8_t smem_raw[];
   OsSmem &S = *reinterpret_cast<OsSmem *>(smem_raw);
   if (!a.plan->active[a.p]) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
     S.tile = atomicAdd(a.tile_ctr, 1u);
     S.bail = has_error(a.ctrl) ? 1u : 0u;
+    mbar_init(&S.bar, 1);
   }
   for (int x = tid; x < OS_WARPS * RADIX; x += OS_BLOCK) (&S.whist[0][0])[x] = 0;
   __syncthreads();
@@ -176,6 +180,26 @@ __global__ void __launch_bounds__(OS_BLOCK) k_onesweep(PassArgs a) {
   const uint64_t base = (uint64_t)tile * OS_TILE;
   const uint32_t count = (uint32_t)min((uint64_t)OS_TILE, (uint64_t)a.m - base);
 
+  // Load the tile: one bulk copy each for keys and values (TMA, 16-byte
+  // granules), plain loads for a ragged remainder or unaligned arrays.
+  const uint64_t *kp = ksrc + base;
+  const uint32_t *vp = vsrc + base;
+  const bool aligned = ((((uintptr_t)kp) | ((uintptr_t)vp)) & 15u) == 0;
+  const uint32_t kbytes = aligned ? (count * 8u) & ~15u : 0u;
+  const uint32_t vbytes = aligned ? (count * 4u) & ~15u : 0u;
+  if (tid == 0 && (kbytes | vbytes)) {
+    mbar_expect_tx(&S.bar, kbytes + vbytes);
+    if (kbytes) bulk_g2s(S.keys, kp, kbytes, &S.bar);
+    if (vbytes) bulk_g2s(S.vals, vp, vbytes, &S.bar);
+  }
+  for (uint32_t e = kbytes / 8u + tid; e < count; e += OS_BLOCK) S.keys[e] = kp[e];
+  for (uint32_t e = vbytes / 4u + tid; e < count; e += OS_BLOCK) S.vals[e] = vp[e];
+  if (kbytes | vbytes) {
+    if (!mbar_wait_bounded(&S.bar, 0, a.ctrl, a.spin_limit)) S.bail = 1;
+  }
+  __syncthreads();
+  if (S.bail) return;
+
   // Rank: warp-striped items, item k of lane l at warp*512 + k*32 + l, so
   // the order (warp, k, lane) is the input order inside the tile.
   uint64_t key[OS_ITEMS];
@@ -187,7 +211,7 @@ __global__ void __launch_bounds__(OS_BLOCK) k_onesweep(PassArgs a) {
   for (int k = 0; k < OS_ITEMS; ++k) {
     const uint32_t li = warp * (32 * OS_ITEMS) + k * 32 + lane;
     const bool valid = li < count;
-    key[k] = valid ? ksrc[base + li] : ~0ull;
+    key[k] = valid ? S.keys[li] : ~0ull;
     // Items past the end take the largest digit and come last in the tile.
     const uint32_t d = valid ? digit_of(key[k], a.shift, a.bits) : dmax;
     const uint32_t peers = peers_of(d);
@@ -226,7 +250,7 @@ __global__ void __launch_bounds__(OS_BLOCK) k_onesweep(PassArgs a) {
   } else {
     status_store(st, status_word(a.epoch, ST_AGG, mine));
     uint32_t excl = 0;
-    if (look_back(a.status, RADIX, d, tile, a.epoch, OpAdd(), excl, a.ctrl, a.spin_limit)) {
+    if (look_back_sum4(a.status, RADIX, d, tile, a.epoch, excl, a.ctrl, a.spin_limit)) {
       status_store(st, status_word(a.epoch, ST_INC, excl + mine));
       S.goff[d] = a.digit_base[d] + excl - start;
     } else {
@@ -236,7 +260,9 @@ __global__ void __launch_bounds__(OS_BLOCK) k_onesweep(PassArgs a) {
   __syncthreads();
   if (S.bail) return;
 
-  // Stage the tile in digit order, then write each digit run contiguously.
+  // Permute the tile into digit order in place (every read of the input
+  // order happened before the barrier above), then write each digit run
+  // with consecutive addresses.
 #pragma unroll
   for (int k = 0; k < OS_ITEMS; ++k) {
     const uint32_t li = warp * (32 * OS_ITEMS) + k * 32 + lane;
@@ -244,11 +270,15 @@ __global__ void __launch_bounds__(OS_BLOCK) k_onesweep(PassArgs a) {
     pos[k] += S.start[dk] + S.whist[warp][dk];
     S.keys[pos[k]] = key[k];
   }
+  uint32_t val[OS_ITEMS];
 #pragma unroll
   for (int k = 0; k < OS_ITEMS; ++k) {
     const uint32_t li = warp * (32 * OS_ITEMS) + k * 32 + lane;
-    S.vals[pos[k]] = li < count ? vsrc[base + li] : 0u;
+    val[k] = li < count ? S.vals[li] : 0u;
   }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < OS_ITEMS; ++k) S.vals[pos[k]] = val[k];
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < OS_ITEMS; ++k) {
@@ -272,6 +302,9 @@ cudaError_t launch_onesweep(const PassArgs &a, cudaStream_t stream) {
   const int smem = (int)sizeof(OsSmem);
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_onesweep, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     configured = true;
   }

@@ -75,7 +75,10 @@ struct RenameArgs {
   uint32_t N;                // total characters = entries of sa (bounds guard)
   uint32_t *sa;              // SA of gapped positions
   uint64_t *act_out;         // survivors: (g' << 32) | i'
-  uint32_t *base_out;        // name - start of each surviving group
+  uint32_t *gstart_out;      // start of each surviving group in act_out
+  uint32_t *gname_out;       // name of each surviving group
+  const uint32_t *off_in;    // device: [survivor offset, group offset] of the output
+  uint32_t *cnt_out;         // device: [survivors, groups] written by the last tile
   uint64_t *status;          // >= 3 * tiles words
   uint32_t epoch;
   uint32_t *tile_ctr;
@@ -85,13 +88,62 @@ struct RenameArgs {
 constexpr int RENAME_TILE = 256 * 16;
 cudaError_t launch_rename(const RenameArgs &a, cudaStream_t stream);
 
-// ---- step A5: partner names (k_gather.cu) -------------------------------
-// keys[j] = (g << W) | (ISA[i'+h] + 1 mod 2^32), vals[j] = i' for the
-// active list act[j] = (g << 32) | i'.
-// isa_len = entries of the ISA array (the gather index is clamped to it).
-cudaError_t launch_gather(const uint64_t *act, uint32_t m, uint32_t h, uint32_t W,
-                          const uint32_t *isa, uint64_t isa_len, uint64_t *keys, uint32_t *vals,
-                          cudaStream_t stream);
+// ---- rounds >= 1: small-group refine and large-group path (k_refine.cu) --
+// Groups of up to REFINE_SMALL_MAX members are refined inside one tile
+// (gather, shared-memory sort, rename, compaction); larger ones go through
+// the global radix sort and k_rename.
+constexpr uint32_t REFINE_NOMINAL = 2048;  // tile t owns groups starting in [t, t+1) * this
+constexpr uint32_t REFINE_CAP = 4096;      // items one tile can hold
+constexpr uint32_t REFINE_SMALL_MAX = REFINE_CAP - REFINE_NOMINAL;
+
+struct ClassifyArgs {
+  uint32_t *gstart;         // G entries written by this round; entry G set here
+  const uint32_t *gname;
+  uint32_t *lg, *loff, *lbase;  // large groups: index, start in the large list, name - start
+  uint32_t *tfirst;         // first group of each refine tile (tiles + 1 entries)
+  uint32_t max_groups;      // upper bound of G (buffer capacity)
+  uint32_t max_tiles;       // upper bound of tiles (buffer capacity - 1)
+  Ctrl *ctrl;               // reads rc.m_s + rc.m_l, rc.g_s + rc.g_l; adds to rc.large
+};
+cudaError_t launch_classify(const ClassifyArgs &a, int num_sms, cudaStream_t stream);
+
+// keys[j] = (k << W) | r2 for the j-th item of the large groups, k = large
+// group ordinal; vals[j] = gapped position.
+struct GatherLargeArgs {
+  const uint64_t *act;
+  const uint32_t *gstart;
+  const uint32_t *lg, *loff;
+  uint32_t mL, GL;
+  uint32_t h, W;
+  const uint32_t *isa;
+  uint64_t isa_len;
+  uint64_t *keys;
+  uint32_t *vals;
+};
+cudaError_t launch_gather_large(const GatherLargeArgs &a, cudaStream_t stream);
+
+struct RefineArgs {
+  const uint64_t *act;      // current active list (g << 32) | i'
+  const uint32_t *gstart;   // G + 1 entries
+  const uint32_t *gname;
+  const uint32_t *tfirst;   // tiles + 1 entries
+  uint32_t m, G, tiles;
+  uint32_t h, W;
+  const uint32_t *isa;      // read only (updates are deferred)
+  uint64_t isa_len;
+  uint32_t N;
+  uint32_t *sa;
+  uint64_t *act_out;
+  uint32_t *gstart_out, *gname_out;
+  uint64_t *upd;            // (new << 32) | i' for every changed name
+  Ctrl *ctrl;               // rc.m_s / rc.g_s / rc.upd reserve the outputs
+};
+cudaError_t launch_refine(const RefineArgs &a, cudaStream_t stream);
+
+// ISA[i'] = new for the ctrl->rc.upd queued updates.
+cudaError_t launch_scatter_updates(const uint64_t *upd, uint32_t max_upd, uint32_t *isa,
+                                   uint64_t isa_len, Ctrl *ctrl, int num_sms,
+                                   cudaStream_t stream);
 
 // ---- output (k_gather.cu) ------------------------------------------------
 // Batched: sa[r] -= gapped start of the text that rank r belongs to.
