@@ -76,6 +76,15 @@ typedef struct {
    * k < trace_cap (single text only). */
   uint32_t *trace_isa;
   uint32_t trace_cap;
+  /* Group names between rounds. 0 (default): a split group's name stays
+   * with the subgroup whose SA interval contains it and every other
+   * subgroup takes the middle of its interval, so a majority subgroup keeps
+   * its name and fewer ISA entries are rewritten. 1: the paper's names, the
+   * start of the interval (Algorithms 5/6, NameDiscarding), so that the
+   * per-round names in trace_isa equal the paper's. Both give the same SA
+   * and ISA; any rank inside a group's interval is a valid lexicographic
+   * name (Section 2). */
+  uint32_t paper_names;
   /* When 1, CUDA events are recorded on `stream` around every kernel launch
    * and the per-kernel-class times, launch counts and algorithmic bytes are
    * returned in sa_stats (adds a few microseconds per launch). */
@@ -95,7 +104,8 @@ enum {
   SA_K_REFINE = 8,    /* small-group refine (rounds >= 1)    */
   SA_K_SCATTER = 9,   /* deferred ISA updates                */
   SA_K_CLASSIFY = 10, /* group classification, tile map      */
-  SA_K_CLASSES = 11
+  SA_K_APPLY = 11,    /* ISA entries of renamed survivors    */
+  SA_K_CLASSES = 12
 };
 
 /* Per-build statistics (HOST struct filled by the _ex calls). */
@@ -127,7 +137,7 @@ typedef struct {
  * text   : DEVICE, n bytes, read only.
  * n      : length, 0 <= n <= SA_MAX_N.
  * sa_out : DEVICE, n uint32, written with SA.
- * The workspace (about 61 bytes per character) is allocated from a
+ * The workspace (about 67 bytes per character) is allocated from a
  * library-private stream-ordered pool on `stream` and returned to it.
  * n = 0 writes nothing; n = 1 writes sa_out[0] = 0. */
 sa_status sa_build(const uint8_t *text, uint64_t n, uint32_t *sa_out,
@@ -199,7 +209,7 @@ size_t sa_sort_workspace_bytes(uint64_t m);
  * The paper has no counterpart; this is a packaging of the same build.
  * text, n, sa_out, stream: as for sa_build. n may be at most 2^18
  * (262144); larger n returns SA_ERR_TOO_LARGE.
- * The workspace is a 16 MiB array in the library's own device memory, held
+ * The workspace is a 20 MiB array in the library's own device memory, held
  * on every GPU that loads the library until the process exits. The first
  * call on a device looks up that array's device address (a CUDA runtime
  * query, once per device); make that first call before any stream capture

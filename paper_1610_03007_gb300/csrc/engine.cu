@@ -21,9 +21,9 @@
 //   keys A/B u64[N], vals A/B u32[N] (radix sort of round 0 and of large
 //   groups), active lists u64[N] x2 (g << 32 | i', current and next), queued
 //   ISA updates u64[N], ISA u32[N + S + 1] (end slots hold 0xFFFFFFFF),
-//   group starts and names u32[N/2+1] x2 each, large-group lists, the
-//   refine tile map, look-back status, control block, plan, histograms:
-//   about 61 bytes per character.
+//   group starts, names and head ranks u32[N/2+1] x2 each, parent names
+//   u32[N/2+1], large-group lists, the refine tile map, look-back status,
+//   control block, plan, histograms: about 67 bytes per character.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -45,7 +45,8 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
   size_t ctrl, plan, hist, dbase, bytehist, code, segoff;
-  size_t ka, kb, va, vb, act0, act1, upd, isa, gs0, gs1, gn0, gn1, lg, loff, lbase, tfirst;
+  size_t ka, kb, va, vb, act0, act1, upd, isa, gs0, gs1, gn0, gn1, gh0, gh1, gold;
+  size_t lg, loff, lbase, lold, tfirst;
   size_t st_sort, st_ren, total;
   size_t st_sort_bytes, st_ren_bytes;
   uint32_t max_groups, max_large, max_tiles;
@@ -80,10 +81,14 @@ Layout make_layout(uint64_t N, uint32_t S) {
   L.gs1 = take(((size_t)L.max_groups + 1) * 4);
   L.gn0 = take((size_t)L.max_groups * 4);
   L.gn1 = take((size_t)L.max_groups * 4);
+  L.gh0 = take((size_t)L.max_groups * 4);
+  L.gh1 = take((size_t)L.max_groups * 4);
+  L.gold = take((size_t)L.max_groups * 4);
   L.max_large = (uint32_t)(Nm / (REFINE_SMALL_MAX + 1) + 1);
   L.lg = take((size_t)L.max_large * 4);
   L.loff = take((size_t)L.max_large * 4);
   L.lbase = take((size_t)L.max_large * 4);
+  L.lold = take((size_t)L.max_large * 4);
   L.max_tiles = (uint32_t)((Nm + REFINE_NOMINAL - 1) / REFINE_NOMINAL);
   L.tfirst = take(((size_t)L.max_tiles + 1) * 4);
   const uint64_t ts = std::max<uint64_t>(1, (N + SORT_TILE - 1) / SORT_TILE);
@@ -194,13 +199,15 @@ struct Build {
   uint64_t *st_sort = nullptr, *st_ren = nullptr;
   uint32_t *va = nullptr, *vb = nullptr, *isa = nullptr;
   uint32_t *gstart[2] = {nullptr, nullptr}, *gname[2] = {nullptr, nullptr};
-  uint32_t *lg = nullptr, *loff = nullptr, *lbase = nullptr, *tfirst = nullptr;
+  uint32_t *ghead[2] = {nullptr, nullptr}, *gold = nullptr;
+  uint32_t *lg = nullptr, *loff = nullptr, *lbase = nullptr, *lold = nullptr, *tfirst = nullptr;
   // launch bookkeeping
   uint32_t epoch = 0, slot = 0;
   uint32_t spin = DEFAULT_SPIN_LIMIT;
   bool inject_pending = false;
   uint64_t bytes = 0;
   uint32_t launches = 0;
+  uint32_t naming = NAMES_RETAIN;
   // per-kernel profiling (events on the build's stream)
   struct Rec {
     int cls, pass;
@@ -241,9 +248,13 @@ struct Build {
     gstart[1] = at<uint32_t>(L.gs1);
     gname[0] = at<uint32_t>(L.gn0);
     gname[1] = at<uint32_t>(L.gn1);
+    ghead[0] = at<uint32_t>(L.gh0);
+    ghead[1] = at<uint32_t>(L.gh1);
+    gold = at<uint32_t>(L.gold);
     lg = at<uint32_t>(L.lg);
     loff = at<uint32_t>(L.loff);
     lbase = at<uint32_t>(L.lbase);
+    lold = at<uint32_t>(L.lold);
     tfirst = at<uint32_t>(L.tfirst);
     st_sort = at<uint64_t>(L.st_sort);
     st_ren = at<uint64_t>(L.st_ren);
@@ -361,7 +372,8 @@ struct Build {
   // Rename of round 0 (all suffixes) or of the large groups of a later
   // round; writes the next active list at the device-side offsets `off_in`.
   sa_status rename(uint32_t m, bool round0, uint32_t cb, uint32_t c0, uint32_t W,
-                   const uint32_t *base_in, uint32_t g_in, int out, const uint32_t *off_in) {
+                   const uint32_t *base_in, const uint32_t *old_in, uint32_t g_in, int out,
+                   const uint32_t *off_in) {
     RenameArgs ra{};
     ra.plan = plan;
     ra.m = m;
@@ -372,6 +384,7 @@ struct Build {
     ra.S = S;
     ra.W = W;
     ra.base_in = base_in;
+    ra.old_in = old_in;
     ra.g_in = g_in;
     ra.isa = isa;
     ra.isa_len = N + S + 1;
@@ -379,7 +392,8 @@ struct Build {
     ra.sa = sa;
     ra.act_out = act[out];
     ra.gstart_out = gstart[out];
-    ra.gname_out = gname[out];
+    ra.ghead_out = ghead[out];
+    ra.gold_out = gold;
     ra.off_in = off_in;
     ra.cnt_out = &ctrl->rc.m_l;
     ra.status = st_ren;
@@ -395,14 +409,24 @@ struct Build {
     ClassifyArgs ca{};
     ca.gstart = gstart[out];
     ca.gname = gname[out];
+    ca.ghead = ghead[out];
+    ca.gold = gold;
+    ca.naming = naming;
     ca.lg = lg;
     ca.loff = loff;
     ca.lbase = lbase;
+    ca.lold = lold;
     ca.tfirst = tfirst;
     ca.max_groups = L.max_groups;
     ca.max_tiles = L.max_tiles;
     ca.ctrl = ctrl;
-    return launch(SA_K_CLASSIFY, 0, 8 * cap_groups, [&] { return launch_classify(ca, sm_count(), st); });
+    sa_status s = launch(SA_K_CLASSIFY, 0, 16 * cap_groups,
+                         [&] { return launch_classify(ca, sm_count(), st); });
+    if (s != SA_OK) return s;
+    // ISA entries of the rename's survivors whose name changed.
+    return launch(SA_K_APPLY, 0, 0, [&] {
+      return launch_apply_names(act[out], gname[out], gold, isa, N + S + 1, ctrl, sm_count(), st);
+    });
   }
 
   // Rename (round 0 or large groups) reads 12 bytes per item plus 4 per
@@ -435,6 +459,7 @@ struct Build {
     const uint32_t N32 = (uint32_t)N;
     carve();
     prof = opt.profile != 0 && stats != nullptr;
+    naming = opt.paper_names ? NAMES_HEAD : NAMES_RETAIN;
     // Clear what must start at zero; the ISA starts all-ones so every end
     // slot reads as the sentinel.
     CK(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
@@ -493,7 +518,7 @@ struct Build {
     s = sort(N32, spec_for(bits0));
     if (s != SA_OK) return s;
     int cur = 0;  // the active list, group starts and names of this round
-    s = rename(N32, true, cb, c0, 0, nullptr, 0, cur, ctrl->zero);
+    s = rename(N32, true, cb, c0, 0, nullptr, nullptr, 0, cur, ctrl->zero);
     if (s != SA_OK) return s;
     s = classify(cur, N / 2 + 1);
     if (s != SA_OK) return s;
@@ -549,6 +574,8 @@ struct Build {
       rf.act = act[cur];
       rf.gstart = gstart[cur];
       rf.gname = gname[cur];
+      rf.ghead = ghead[cur];
+      rf.naming = naming;
       rf.tfirst = tfirst;
       rf.m = m;
       rf.G = G;
@@ -562,12 +589,13 @@ struct Build {
       rf.act_out = act[nxt];
       rf.gstart_out = gstart[nxt];
       rf.gname_out = gname[nxt];
+      rf.ghead_out = ghead[nxt];
       rf.upd = upd;
       rf.ctrl = ctrl;
       s = launch(SA_K_REFINE, 0, 0, [&] { return launch_refine(rf, st); });
       if (s != SA_OK) return s;
       if (mL > 0) {
-        s = rename(mL, false, 0, 0, W, lbase, GL, nxt, &ctrl->rc.m_s);
+        s = rename(mL, false, 0, 0, W, lbase, lold, GL, nxt, &ctrl->rc.m_s);
         if (s != SA_OK) return s;
       }
       s = launch(SA_K_SCATTER, 0, 0, [&] {

@@ -56,7 +56,8 @@ __device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t *a, uint32_t 
 
 __global__ void __launch_bounds__(256) k_classify(ClassifyArgs a) {
   const uint32_t m = a.ctrl->rc.m_s + a.ctrl->rc.m_l;
-  const uint32_t G = a.ctrl->rc.g_s + a.ctrl->rc.g_l;
+  const uint32_t gs = a.ctrl->rc.g_s;
+  const uint32_t G = gs + a.ctrl->rc.g_l;
   if (G > a.max_groups) {
     raise_error(a.ctrl, ERR_INTERNAL, 6);
     return;
@@ -73,13 +74,27 @@ __global__ void __launch_bounds__(256) k_classify(ClassifyArgs a) {
       const uint32_t s = a.gstart[x];
       const uint32_t e = x + 1 < G ? a.gstart[x + 1] : m;
       const uint32_t size = e - s;
+      uint32_t name;
+      if (x >= gs) {
+        // A group written by the rename: its name is chosen now that its
+        // size (its SA interval [head, head + size)) is known.
+        const uint32_t head = a.ghead[x], old = a.gold[x];
+        if (a.naming == NAMES_RETAIN)
+          name = (old != NO_NAME && old - head < size) ? old : head + size / 2;
+        else
+          name = head;
+        a.gname[x] = name;
+      } else {
+        name = a.gname[x];
+      }
       if (size > REFINE_SMALL_MAX) {
         const unsigned long long old =
             atomicAdd(&a.ctrl->rc.large, (1ull << 32) | (unsigned long long)size);
         const uint32_t k = (uint32_t)(old >> 32), off = (uint32_t)old;
         a.lg[k] = (uint32_t)x;
         a.loff[k] = off;
-        a.lbase[k] = a.gname[x] - off;
+        a.lbase[k] = a.ghead[x] - off;
+        a.lold[k] = name;
       }
     }
     if (x <= tiles) a.tfirst[x] = lower_bound_u32(a.gstart, G, (uint32_t)x * REFINE_NOMINAL);
@@ -133,26 +148,19 @@ constexpr int RF_GPT = (RF_MAXG + RF_BLOCK - 1) / RF_BLOCK;  // groups per threa
 struct RfSmem {
   uint64_t keys[REFINE_CAP + REFINE_CAP / 16];  // padded (e + e/16) after the last pass
   uint32_t vals[REFINE_CAP + REFINE_CAP / 32];  // padded (e + e/32) after the last pass
-  uint32_t whist[RF_WARPS][RADIX];
+  union {
+    uint32_t gsrc[RF_MAXG];           // loading: first position of each local group
+    uint32_t match[RF_WARPS][RADIX];  // sorting: per-warp peer masks
+  };
+  uint16_t whist[RF_WARPS][RADIX];
   uint32_t dstart[RADIX];
   uint32_t gname[RF_MAXG];
-  uint32_t gsrc[RF_MAXG];      // first position of the local group in the active list
+  uint32_t ghead[RF_MAXG];     // head rank (SA interval start) of the local group
   uint32_t goff[RF_MAXG + 1];  // start of the local group in the tile (large groups: empty)
   uint32_t tmp[RF_WARPS + 1];
   uint32_t nitems, all_small, upd_base, surv_base, grp_base;
   unsigned long long orv;
 };
-
-__device__ __forceinline__ uint32_t rf_peers(uint32_t d) {
-  uint32_t peers = 0xffffffffu;
-#pragma unroll
-  for (int b = 0; b < RADIX_BITS; ++b) {
-    const uint32_t bit = (d >> b) & 1u;
-    const uint32_t bal = __ballot_sync(0xffffffffu, bit);
-    peers &= bit ? bal : ~bal;
-  }
-  return peers;
-}
 
 // Stable LSD radix sort of S.keys/S.vals[0, cnt) in shared memory over the
 // 8-bit digits below `nbits` that vary inside the tile. Warp w ranks the
@@ -166,6 +174,7 @@ __device__ void rf_tile_sort(RfSmem &S, uint32_t cnt, unsigned long long varying
   const uint32_t K = (cnt + RF_BLOCK - 1) / RF_BLOCK;  // slots per lane, <= RF_ITEMS
   const uint32_t chunk = K * 32;
   const uint32_t ndig = (nbits + RADIX_BITS - 1) / RADIX_BITS;
+  for (int x = tid; x < RF_WARPS * RADIX; x += RF_BLOCK) (&S.match[0][0])[x] = 0u;
   uint32_t last = 0;
   for (uint32_t p = 0; p < ndig; ++p)
     if ((varying >> (p * RADIX_BITS)) & 0xFFull) last = p;
@@ -178,7 +187,8 @@ __device__ void rf_tile_sort(RfSmem &S, uint32_t cnt, unsigned long long varying
     __syncthreads();
     uint64_t key[RF_ITEMS];
     uint32_t val[RF_ITEMS], pos[RF_ITEMS];
-    uint32_t *wh = S.whist[warp];
+    uint16_t *wh = S.whist[warp];
+    uint32_t *mt = S.match[warp];
 #pragma unroll
     for (int k = 0; k < RF_ITEMS; ++k) {
       if ((uint32_t)k < K) {
@@ -187,13 +197,7 @@ __device__ void rf_tile_sort(RfSmem &S, uint32_t cnt, unsigned long long varying
         key[k] = valid ? S.keys[li] : ~0ull;
         val[k] = valid ? S.vals[li] : 0u;
         const uint32_t d = valid ? (uint32_t)(key[k] >> shift) & 0xFFu : 0xFFu;
-        const uint32_t peers = rf_peers(d);
-        const uint32_t before = wh[d];
-        __syncwarp();
-        const uint32_t lower = peers & lt;
-        if (lower == 0) wh[d] = before + __popc(peers);
-        __syncwarp();
-        pos[k] = before + __popc(lower);
+        pos[k] = warp_rank_digit(d, mt, wh, lane, lt);
       }
     }
     __syncthreads();
@@ -203,7 +207,7 @@ __device__ void rf_tile_sort(RfSmem &S, uint32_t cnt, unsigned long long varying
 #pragma unroll
       for (int w = 0; w < RF_WARPS; ++w) {
         const uint32_t c = S.whist[w][d];
-        S.whist[w][d] = total;
+        S.whist[w][d] = (uint16_t)total;
         total += c;
       }
       uint32_t tt;
@@ -224,7 +228,7 @@ __device__ void rf_tile_sort(RfSmem &S, uint32_t cnt, unsigned long long varying
   }
 }
 
-__global__ void __launch_bounds__(RF_BLOCK, 3) k_refine(RefineArgs a) {
+__global__ void __launch_bounds__(RF_BLOCK, 4) k_refine(RefineArgs a) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   RfSmem &S = *reinterpret_cast<RfSmem *>(smem_raw);
   const int tid = threadIdx.x;
@@ -256,6 +260,7 @@ __global__ void __launch_bounds__(RF_BLOCK, 3) k_refine(RefineArgs a) {
       const uint32_t s = __ldg(a.gstart + g), e = __ldg(a.gstart + g + 1);
       S.gsrc[lg] = s;
       S.gname[lg] = __ldg(a.gname + g);
+      S.ghead[lg] = __ldg(a.ghead + g);
       const uint32_t size = e - s;
       if (size <= REFINE_SMALL_MAX)
         sz[r] = size;
@@ -368,13 +373,19 @@ __global__ void __launch_bounds__(RF_BLOCK, 3) k_refine(RefineArgs a) {
       }
     }
   }
-  uint32_t th_head = 0, th_surv = 0, th_hs = 0;
+  // Subgroup bounds: start = last head at or before j (max-scan), end =
+  // first head after j (suffix min-scan); both inside the tile, since tiles
+  // hold whole groups.
+  uint32_t th_head = 0, th_first = 0xFFFFFFFFu, th_surv = 0, th_hs = 0;
 #pragma unroll
   for (int k = 0; k < RF_ITEMS; ++k) {
     const uint32_t j = l0 + k;
     if ((uint32_t)k < K && j < cnt) {
       const bool uniq = f[k] && f[k + 1];
-      if (f[k]) th_head = j;
+      if (f[k]) {
+        th_head = j;
+        if (th_first == 0xFFFFFFFFu) th_first = j;
+      }
       if (!uniq) {
         ++th_surv;
         if (f[k]) ++th_hs;
@@ -383,7 +394,26 @@ __global__ void __launch_bounds__(RF_BLOCK, 3) k_refine(RefineArgs a) {
   }
   uint32_t tot_head;
   const uint32_t ex_head = block_exclusive<RF_BLOCK>(th_head, OpMax(), 0u, S.tmp, tot_head);
-  // Names change for every item outside its group's first subgroup.
+  uint32_t next_head = block_suffix_min_exclusive<RF_BLOCK>(th_first, S.tmp);
+  if (next_head > cnt) next_head = cnt;
+  uint32_t rend[RF_ITEMS];
+  {
+    uint32_t e = next_head;
+#pragma unroll
+    for (int k = RF_ITEMS - 1; k >= 0; --k) {
+      const uint32_t j = l0 + k;
+      rend[k] = e;
+      if ((uint32_t)k < K && j < cnt && f[k]) e = j;
+    }
+  }
+  // New name of item j (see NamingRule): its subgroup's SA interval is
+  // [ghead + (start - goff), ghead + (end - goff)).
+  auto name_of = [&](uint32_t lgq, uint32_t start, uint32_t end) -> uint32_t {
+    const uint32_t lo = S.ghead[lgq] + (start - S.goff[lgq]);
+    if (a.naming != NAMES_RETAIN) return lo;
+    const uint32_t len = end - start, old = S.gname[lgq];
+    return old - lo < len ? old : lo + len / 2;
+  };
   uint32_t th_chg = 0;
   {
     uint32_t rh = ex_head;
@@ -393,7 +423,7 @@ __global__ void __launch_bounds__(RF_BLOCK, 3) k_refine(RefineArgs a) {
       if ((uint32_t)k < K && j < cnt) {
         if (f[k]) rh = j;
         const uint32_t lgq = (uint32_t)(S.keys[j + (j >> 4)] >> a.W);
-        if (rh != S.goff[lgq]) ++th_chg;
+        if (name_of(lgq, rh, rend[k]) != S.gname[lgq]) ++th_chg;
       }
     }
   }
@@ -428,19 +458,19 @@ __global__ void __launch_bounds__(RF_BLOCK, 3) k_refine(RefineArgs a) {
       const uint64_t kk = S.keys[j + (j >> 4)];
       const uint32_t ip = S.vals[j + (j >> 5)];
       const uint32_t lgq = (uint32_t)(kk >> a.W);
-      const uint32_t gs = S.goff[lgq];
-      const uint32_t name = S.gname[lgq] + (run_head - gs);
+      const uint32_t name = name_of(lgq, run_head, rend[k]);
       if (name >= a.N || ip >= a.isa_len) {  // never taken unless a logic error
         raise_error(a.ctrl, ERR_INTERNAL, 10);
         continue;
       }
-      if (run_head != gs) a.upd[run_chg++] = ((uint64_t)name << 32) | ip;
+      if (name != S.gname[lgq]) a.upd[run_chg++] = ((uint64_t)name << 32) | ip;
       if (f[k] && f[k + 1]) {
         a.sa[name] = ip;
       } else {
         if (f[k]) {
           a.gstart_out[run_hs] = run_surv;
           a.gname_out[run_hs] = name;
+          a.ghead_out[run_hs] = S.ghead[lgq] + (run_head - S.goff[lgq]);
           ++run_hs;
         }
         a.act_out[run_surv] = ((uint64_t)(run_hs - 1) << 32) | ip;
@@ -463,6 +493,29 @@ cudaError_t launch_refine(const RefineArgs &a, cudaStream_t stream) {
     configured = true;
   }
   k_refine<<<a.tiles, RF_BLOCK, smem, stream>>>(a);
+  return cudaGetLastError();
+}
+
+// ---- names of the rename's survivors ------------------------------------------
+
+__global__ void __launch_bounds__(256) k_apply_names(const uint64_t *__restrict__ act,
+                                                    const uint32_t *__restrict__ gname,
+                                                    const uint32_t *__restrict__ gold,
+                                                    uint32_t *isa, uint64_t isa_len, Ctrl *ctrl) {
+  const uint32_t lo = ctrl->rc.m_s, hi = lo + ctrl->rc.m_l;
+  for (uint64_t x = lo + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < hi;
+       x += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t e = act[x];
+    const uint32_t g = (uint32_t)(e >> 32), ip = (uint32_t)e;
+    const uint32_t name = __ldg(gname + g);
+    if (name != __ldg(gold + g) && ip < isa_len) isa[ip] = name;
+  }
+}
+
+cudaError_t launch_apply_names(const uint64_t *act, const uint32_t *gname, const uint32_t *gold,
+                               uint32_t *isa, uint64_t isa_len, Ctrl *ctrl, int num_sms,
+                               cudaStream_t stream) {
+  k_apply_names<<<num_sms * 8, 256, 0, stream>>>(act, gname, gold, isa, isa_len, ctrl);
   return cudaGetLastError();
 }
 

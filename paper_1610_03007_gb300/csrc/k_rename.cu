@@ -14,10 +14,12 @@
 //    small ones).
 //  - Unique (Algorithm 6): new_j differs from both neighbours, i.e.
 //    f_j and f_{j+1} (f_m = 1).
-//  - Discarding (Algorithm 5): ISA[i] = new for every item; a unique item is
-//    final and writes SA[new] = i; the others are compacted, in order, into
+//  - Discarding (Algorithm 5): a unique item is final and writes ISA[i] =
+//    SA position and SA[pos] = i; the others are compacted, in order, into
 //    the next active list with their group ordinal g', and each group's head
-//    records its start in that list and its name (gstart'[g'], gname'[g']).
+//    records its start in that list, its head rank and its parent's name
+//    (the group's own name and the ISA entries of its members follow in
+//    k_classify / k_apply_names, once group sizes are known).
 //    Offsets come from two device-wide sums (survivors, group heads) with
 //    decoupled look-back, added to output offsets read from the device (the
 //    small-group refine of the same round writes first).
@@ -25,8 +27,8 @@
 // All partner names of a round were gathered by an earlier kernel, so the
 // ISA writes here never race with reads of the same round.
 //
-// Bound: HBM. 12 bytes read per item; 4 bytes random ISA write per item,
-// 4 bytes random SA write per unique item, 8 bytes per survivor.
+// Bound: HBM. 12 bytes read per item; 4 bytes random ISA and SA writes per
+// unique item, 8 bytes per survivor.
 #include "launch.h"
 
 namespace gbsa {
@@ -186,19 +188,24 @@ __global__ void __launch_bounds__(RN_BLOCK) k_rename(RenameArgs a) {
         raise_error(a.ctrl, ERR_INTERNAL, 4);
         continue;
       }
-      const uint32_t name = a.round0 ? run_head : __ldg(a.base_in + g) + run_head;
-      if (name >= a.N || ip >= a.isa_len) {  // never taken unless a logic error
+      // Head rank of the item's new group (the start of its SA interval).
+      const uint32_t head = a.round0 ? run_head : __ldg(a.base_in + g) + run_head;
+      if (head >= a.N || ip >= a.isa_len) {  // never taken unless a logic error
         raise_error(a.ctrl, ERR_INTERNAL, 3);
         continue;
       }
-      a.isa[ip] = name;
       if (f[k] && f[k + 1]) {
-        a.sa[name] = ip;
+        // Unique: its name is its rank, final (Algorithm 5 discards it).
+        a.isa[ip] = head;
+        a.sa[head] = ip;
       } else {
+        // Survivors get their names, and their ISA entries, once the group
+        // sizes are known (k_classify, k_apply_names).
         if (f[k]) {
           ++run_hs;
           a.gstart_out[run_hs - 1] = run_surv;
-          a.gname_out[run_hs - 1] = name;
+          a.ghead_out[run_hs - 1] = head;
+          a.gold_out[run_hs - 1] = a.round0 ? NO_NAME : __ldg(a.old_in + g);
         }
         a.act_out[run_surv] = ((uint64_t)(run_hs - 1) << 32) | ip;
         ++run_surv;

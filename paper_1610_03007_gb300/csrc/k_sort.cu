@@ -136,7 +136,8 @@ static_assert(OS_BLOCK == RADIX, "one thread per digit");
 struct OsSmem {
   uint64_t keys[OS_TILE];           // tile in input order, then in digit order
   uint32_t vals[OS_TILE];
-  uint32_t whist[OS_WARPS][RADIX];  // per-warp counts, then per-warp prefixes
+  uint32_t match[OS_WARPS][RADIX];  // per-warp peer masks (zero between uses)
+  uint16_t whist[OS_WARPS][RADIX];  // per-warp counts, then per-warp prefixes
   uint32_t start[RADIX];            // tile-local start of each digit run
   uint32_t goff[RADIX];             // global index of a run = goff + local index
   uint32_t tmp[OS_WARPS + 1];
@@ -144,18 +145,6 @@ struct OsSmem {
   uint32_t bail;
   uint64_t bar;                     // completion of the tile's bulk copies
 };
-
-// Lanes of the warp holding the same digit (8 ballots, one per digit bit).
-__device__ __forceinline__ uint32_t peers_of(uint32_t d) {
-  uint32_t peers = 0xffffffffu;
-#pragma unroll
-  for (int b = 0; b < RADIX_BITS; ++b) {
-    const uint32_t bit = (d >> b) & 1u;
-    const uint32_t bal = __ballot_sync(0xffffffffu, bit);
-    peers &= bit ? bal : ~bal;
-  }
-  return peers;
-}
 
 // Three blocks per SM: registers capped at 85 per thread, ~59 KB of
 // shared memory per block.
@@ -169,7 +158,10 @@ __global__ void __launch_bounds__(OS_BLOCK, 3) k_onesweep(PassArgs a) {
     S.bail = has_error(a.ctrl) ? 1u : 0u;
     mbar_init(&S.bar, 1);
   }
-  for (int x = tid; x < OS_WARPS * RADIX; x += OS_BLOCK) (&S.whist[0][0])[x] = 0;
+  for (int x = tid; x < OS_WARPS * RADIX; x += OS_BLOCK) {
+    (&S.whist[0][0])[x] = 0;
+    (&S.match[0][0])[x] = 0u;
+  }
   __syncthreads();
   if (S.bail) return;
   const uint32_t tile = S.tile;
@@ -204,7 +196,8 @@ __global__ void __launch_bounds__(OS_BLOCK, 3) k_onesweep(PassArgs a) {
   // the order (warp, k, lane) is the input order inside the tile.
   uint64_t key[OS_ITEMS];
   uint32_t pos[OS_ITEMS];
-  uint32_t *wh = S.whist[warp];
+  uint16_t *wh = S.whist[warp];
+  uint32_t *mt = S.match[warp];
   const uint32_t lt = lanemask_lt();
   const uint32_t dmax = (1u << a.bits) - 1u;
 #pragma unroll
@@ -214,13 +207,7 @@ __global__ void __launch_bounds__(OS_BLOCK, 3) k_onesweep(PassArgs a) {
     key[k] = valid ? S.keys[li] : ~0ull;
     // Items past the end take the largest digit and come last in the tile.
     const uint32_t d = valid ? digit_of(key[k], a.shift, a.bits) : dmax;
-    const uint32_t peers = peers_of(d);
-    const uint32_t before = wh[d];
-    __syncwarp();
-    const uint32_t lower = peers & lt;
-    if (lower == 0) wh[d] = before + __popc(peers);
-    __syncwarp();
-    pos[k] = before + __popc(lower);
+    pos[k] = warp_rank_digit(d, mt, wh, lane, lt);
   }
   __syncthreads();
 
@@ -230,7 +217,7 @@ __global__ void __launch_bounds__(OS_BLOCK, 3) k_onesweep(PassArgs a) {
 #pragma unroll
   for (int w = 0; w < OS_WARPS; ++w) {
     const uint32_t c = S.whist[w][d];
-    S.whist[w][d] = total;
+    S.whist[w][d] = (uint16_t)total;
     total += c;
   }
   const uint32_t invalid = OS_TILE - count;

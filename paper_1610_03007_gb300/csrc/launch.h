@@ -68,15 +68,17 @@ struct RenameArgs {
   const uint32_t *seg_off;   // S+1 ungapped offsets
   uint32_t S;
   uint32_t W;                // later rounds: group ordinal g = key >> W
-  const uint32_t *base_in;   // later rounds: name - start of group g
+  const uint32_t *base_in;   // later rounds: head rank - start of group g
+  const uint32_t *old_in;    // later rounds: name of group g (round 0: NULL)
   uint32_t g_in;             // later rounds: groups in base_in (bounds guard)
-  uint32_t *isa;             // gapped ISA
+  uint32_t *isa;             // gapped ISA (written for new unique suffixes only)
   uint64_t isa_len;          // entries of isa (bounds guard)
   uint32_t N;                // total characters = entries of sa (bounds guard)
   uint32_t *sa;              // SA of gapped positions
   uint64_t *act_out;         // survivors: (g' << 32) | i'
   uint32_t *gstart_out;      // start of each surviving group in act_out
-  uint32_t *gname_out;       // name of each surviving group
+  uint32_t *ghead_out;       // head rank (SA interval start) of each surviving group
+  uint32_t *gold_out;        // name of its parent group (NO_NAME in round 0)
   const uint32_t *off_in;    // device: [survivor offset, group offset] of the output
   uint32_t *cnt_out;         // device: [survivors, groups] written by the last tile
   uint64_t *status;          // >= 3 * tiles words
@@ -92,14 +94,29 @@ cudaError_t launch_rename(const RenameArgs &a, cudaStream_t stream);
 // Groups of up to REFINE_SMALL_MAX members are refined inside one tile
 // (gather, shared-memory sort, rename, compaction); larger ones go through
 // the global radix sort and k_rename.
-constexpr uint32_t REFINE_NOMINAL = 2048;  // tile t owns groups starting in [t, t+1) * this
-constexpr uint32_t REFINE_CAP = 4096;      // items one tile can hold
+constexpr uint32_t REFINE_NOMINAL = 1024;  // tile t owns groups starting in [t, t+1) * this
+constexpr uint32_t REFINE_CAP = 2048;      // items one tile can hold
 constexpr uint32_t REFINE_SMALL_MAX = REFINE_CAP - REFINE_NOMINAL;
+
+// Names of groups. A name may be any rank inside the group's SA interval:
+// intervals are disjoint and ordered, so such names respect the order of
+// the suffixes, and a singleton's only choice is its rank. NAMES_HEAD is the
+// paper's rule (Algorithm 5/6: the interval start, r + (subgroup start -
+// group start)); NAMES_RETAIN keeps a parent's name in the subgroup whose
+// interval contains it and gives every other subgroup the middle of its
+// interval, so a majority subgroup keeps its name and fewer ISA entries
+// change per round.
+enum NamingRule : uint32_t { NAMES_HEAD = 0, NAMES_RETAIN = 1 };
+constexpr uint32_t NO_NAME = 0xFFFFFFFFu;
 
 struct ClassifyArgs {
   uint32_t *gstart;         // G entries written by this round; entry G set here
-  const uint32_t *gname;
-  uint32_t *lg, *loff, *lbase;  // large groups: index, start in the large list, name - start
+  uint32_t *gname;          // names: final for refine groups, set here for rename groups
+  const uint32_t *ghead;    // head rank of every group
+  const uint32_t *gold;     // parent names of the rename groups
+  uint32_t naming;          // NamingRule
+  uint32_t *lg, *loff, *lbase, *lold;  // large groups: index, start in the large
+                                       // list, head - start, name
   uint32_t *tfirst;         // first group of each refine tile (tiles + 1 entries)
   uint32_t max_groups;      // upper bound of G (buffer capacity)
   uint32_t max_tiles;       // upper bound of tiles (buffer capacity - 1)
@@ -126,6 +143,8 @@ struct RefineArgs {
   const uint64_t *act;      // current active list (g << 32) | i'
   const uint32_t *gstart;   // G + 1 entries
   const uint32_t *gname;
+  const uint32_t *ghead;    // head rank of each group
+  uint32_t naming;          // NamingRule
   const uint32_t *tfirst;   // tiles + 1 entries
   uint32_t m, G, tiles;
   uint32_t h, W;
@@ -134,11 +153,17 @@ struct RefineArgs {
   uint32_t N;
   uint32_t *sa;
   uint64_t *act_out;
-  uint32_t *gstart_out, *gname_out;
+  uint32_t *gstart_out, *gname_out, *ghead_out;
   uint64_t *upd;            // (new << 32) | i' for every changed name
   Ctrl *ctrl;               // rc.m_s / rc.g_s / rc.upd reserve the outputs
 };
 cudaError_t launch_refine(const RefineArgs &a, cudaStream_t stream);
+
+// ISA[i'] = gname[g] for the rename's survivors (act[rc.m_s, rc.m_s +
+// rc.m_l)) whose group name differs from their parent's.
+cudaError_t launch_apply_names(const uint64_t *act, const uint32_t *gname, const uint32_t *gold,
+                               uint32_t *isa, uint64_t isa_len, Ctrl *ctrl, int num_sms,
+                               cudaStream_t stream);
 
 // ISA[i'] = new for the ctrl->rc.upd queued updates.
 cudaError_t launch_scatter_updates(const uint64_t *upd, uint32_t max_upd, uint32_t *isa,

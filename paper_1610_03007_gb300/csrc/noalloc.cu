@@ -31,9 +31,9 @@
 
 #define GBSA_API extern "C" __attribute__((visibility("default")))
 
-// Largest text accepted: 2^18 bytes; its workspace is about 15.2 MiB.
+// Largest text accepted: 2^18 bytes; its workspace is about 16.7 MiB.
 constexpr uint64_t NOALLOC_MAX_N = 1ull << 18;
-constexpr size_t NOALLOC_SCRATCH_BYTES = 16ull << 20;  // 16 MiB
+constexpr size_t NOALLOC_SCRATCH_BYTES = 20ull << 20;  // 20 MiB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 

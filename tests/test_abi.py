@@ -63,9 +63,9 @@ def test_host_side_argument_checks(lib):
 
 
 def test_workspace_model(lib):
-    # About 61 bytes per character: keys A/B (16), values A/B (8), two
-    # active lists (16), the update list (8), ISA (4), group starts and names
-    # x2 (8) and look-back status.
+    # About 67 bytes per character: keys A/B (16), values A/B (8), two
+    # active lists (16), the update list (8), ISA (4), group starts, names
+    # and head ranks x2 plus parent names (14) and look-back status.
     for n in (1 << 20, 1 << 28, 1 << 31):
         b = lib.sa_workspace_bytes(n)
-        assert 60 * n < b < 62 * n
+        assert 66 * n < b < 67 * n

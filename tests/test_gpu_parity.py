@@ -43,7 +43,8 @@ def test_paper_example_1_and_2(gb, orc):
     assert list(gpu_sa(gb, t)) == ints(g["sa"])
     # Example 2's names after every round, with the paper's 2-character
     # initial names.
-    sa, isa, stats, trace = gb.sa_build_ex(dev_text(t), isa=True, h0_chars=2, trace_cap=8)
+    sa, isa, stats, trace = gb.sa_build_ex(dev_text(t), isa=True, h0_chars=2, trace_cap=8,
+                                           paper_names=True)
     rows = [list(r) for r in trace[: stats["rounds"]].cpu().numpy()]
     assert rows == [ints(g[f"names_{k}"]) for k in range(3)]
     assert list(isa.cpu().numpy()) == ints(g["names_2"])
@@ -92,16 +93,50 @@ def test_random_inputs(gb, orc, recipe, n):
 @pytest.mark.parametrize("recipe,n", [("dna", 1 << 20), ("zipf_repeats", 1 << 20),
                                       ("markov", 1 << 20), ("zipf_repeats", (1 << 21) + 12345)])
 def test_every_round_matches_the_oracle(gb, orc, recipe, n):
-    """Names after every round equal the oracle's with the same initial
-    prefix length (the key's c0 characters); SA and ISA equal at the end."""
+    """With the paper's naming rule, the names after every round equal the
+    oracle's with the same initial prefix length (the key's c0 characters);
+    SA and ISA equal at the end."""
     t = gen.text(recipe, 31337, n)
-    sa, isa, stats, trace = gb.sa_build_ex(dev_text(t), isa=True, trace_cap=24)
+    sa, isa, stats, trace = gb.sa_build_ex(dev_text(t), isa=True, trace_cap=24, paper_names=True)
     c0 = stats["chars_per_key"]
     osa, oisa, orounds, otrace = orc.pd_sa(t, h0=c0, trace_cap=24)
     assert stats["rounds"] == orounds + 1
     g = trace[: stats["rounds"]].cpu().numpy().view(np.uint32)
     for k in range(stats["rounds"]):
         assert np.array_equal(g[k], otrace[k]), f"round {k}"
+    assert np.array_equal(sa.cpu().numpy().view(np.uint32), osa)
+    assert np.array_equal(isa.cpu().numpy().view(np.uint32), oisa)
+
+
+def names_agree(gpu_names, oracle_names):
+    """The GPU names induce the oracle's groups in the oracle's order, and
+    every GPU name lies in its group's SA interval [head, head + size)."""
+    o = oracle_names.astype(np.int64)
+    g = gpu_names.astype(np.int64)
+    order = np.argsort(o, kind="stable")
+    os_, gs_ = o[order], g[order]
+    same_o = np.diff(os_) == 0
+    if not np.array_equal(same_o, np.diff(gs_) == 0):
+        return False
+    if np.any(np.diff(gs_) < 0):
+        return False
+    size = np.bincount(o, minlength=o.size)[o]
+    return bool(np.all((g >= o) & (g < o + size)))
+
+
+@pytest.mark.parametrize("recipe,n", [("zipf_repeats", 1 << 20), ("markov", 1 << 20),
+                                      ("zipf_repeats", (1 << 21) + 777)])
+def test_every_round_default_names_are_valid(gb, orc, recipe, n):
+    """With the default interval-retaining names, every round has exactly the
+    oracle's groups, in its order, each name inside its group's interval."""
+    t = gen.text(recipe, 4242, n)
+    sa, isa, stats, trace = gb.sa_build_ex(dev_text(t), isa=True, trace_cap=24)
+    c0 = stats["chars_per_key"]
+    osa, oisa, orounds, otrace = orc.pd_sa(t, h0=c0, trace_cap=24)
+    assert stats["rounds"] == orounds + 1
+    g = trace[: stats["rounds"]].cpu().numpy().view(np.uint32)
+    for k in range(stats["rounds"]):
+        assert names_agree(g[k], otrace[k]), f"round {k}"
     assert np.array_equal(sa.cpu().numpy().view(np.uint32), osa)
     assert np.array_equal(isa.cpu().numpy().view(np.uint32), oisa)
 
