@@ -85,6 +85,11 @@ typedef struct {
    * and ISA; any rank inside a group's interval is a valid lexicographic
    * name (Section 2). */
   uint32_t paper_names;
+  /* Tile shape of the small-group refine of rounds >= 1 (threads per block
+   * x items per tile): 0 = automatic, 1 = 128 x 1024, 2 = 256 x 2048,
+   * 3 = 256 x 4096, 4 = 256 x 1024. Groups of up to half a tile are refined
+   * inside one tile; larger ones take the global radix sort. */
+  uint32_t refine_shape;
   /* When 1, CUDA events are recorded on `stream` around every kernel launch
    * and the per-kernel-class times, launch counts and algorithmic bytes are
    * returned in sa_stats (adds a few microseconds per launch). */

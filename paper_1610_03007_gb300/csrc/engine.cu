@@ -84,12 +84,12 @@ Layout make_layout(uint64_t N, uint32_t S) {
   L.gh0 = take((size_t)L.max_groups * 4);
   L.gh1 = take((size_t)L.max_groups * 4);
   L.gold = take((size_t)L.max_groups * 4);
-  L.max_large = (uint32_t)(Nm / (REFINE_SMALL_MAX + 1) + 1);
+  L.max_large = (uint32_t)(Nm / (REFINE_MIN_NOMINAL + 1) + 1);
   L.lg = take((size_t)L.max_large * 4);
   L.loff = take((size_t)L.max_large * 4);
   L.lbase = take((size_t)L.max_large * 4);
   L.lold = take((size_t)L.max_large * 4);
-  L.max_tiles = (uint32_t)((Nm + REFINE_NOMINAL - 1) / REFINE_NOMINAL);
+  L.max_tiles = (uint32_t)((Nm + REFINE_MIN_NOMINAL - 1) / REFINE_MIN_NOMINAL);
   L.tfirst = take(((size_t)L.max_tiles + 1) * 4);
   const uint64_t ts = std::max<uint64_t>(1, (N + SORT_TILE - 1) / SORT_TILE);
   L.st_sort_bytes = ts * RADIX * 8;
@@ -208,6 +208,7 @@ struct Build {
   uint64_t bytes = 0;
   uint32_t launches = 0;
   uint32_t naming = NAMES_RETAIN;
+  uint32_t shape = 0, nominal = 512;  // refine tile shape and window
   // per-kernel profiling (events on the build's stream)
   struct Rec {
     int cls, pass;
@@ -417,6 +418,7 @@ struct Build {
     ca.lbase = lbase;
     ca.lold = lold;
     ca.tfirst = tfirst;
+    ca.nominal = nominal;
     ca.max_groups = L.max_groups;
     ca.max_tiles = L.max_tiles;
     ca.ctrl = ctrl;
@@ -460,6 +462,12 @@ struct Build {
     carve();
     prof = opt.profile != 0 && stats != nullptr;
     naming = opt.paper_names ? NAMES_HEAD : NAMES_RETAIN;
+    // Default: 128 threads x 1024 items (8 blocks per SM), the fastest shape
+    // measured on the repeated-text workloads.
+    shape = (opt.refine_shape >= 1 && opt.refine_shape <= (uint32_t)REFINE_SHAPES)
+                ? opt.refine_shape - 1
+                : 0;
+    nominal = REFINE_SHAPE[shape].cap / 2;
     // Clear what must start at zero; the ISA starts all-ones so every end
     // slot reads as the sentinel.
     CK(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
@@ -579,7 +587,8 @@ struct Build {
       rf.tfirst = tfirst;
       rf.m = m;
       rf.G = G;
-      rf.tiles = (m + REFINE_NOMINAL - 1) / REFINE_NOMINAL;
+      rf.shape = shape;
+      rf.tiles = (m + nominal - 1) / nominal;
       rf.h = (uint32_t)h;
       rf.W = W;
       rf.isa = isa;

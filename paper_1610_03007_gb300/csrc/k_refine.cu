@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(256) k_classify(ClassifyArgs a) {
     raise_error(a.ctrl, ERR_INTERNAL, 6);
     return;
   }
-  const uint32_t tiles = (m + REFINE_NOMINAL - 1) / REFINE_NOMINAL;
+  const uint32_t tiles = (m + a.nominal - 1) / a.nominal;
   if (tiles > a.max_tiles) {
     raise_error(a.ctrl, ERR_INTERNAL, 7);
     return;
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(256) k_classify(ClassifyArgs a) {
       } else {
         name = a.gname[x];
       }
-      if (size > REFINE_SMALL_MAX) {
+      if (size > a.nominal) {
         const unsigned long long old =
             atomicAdd(&a.ctrl->rc.large, (1ull << 32) | (unsigned long long)size);
         const uint32_t k = (uint32_t)(old >> 32), off = (uint32_t)old;
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256) k_classify(ClassifyArgs a) {
         a.lold[k] = name;
       }
     }
-    if (x <= tiles) a.tfirst[x] = lower_bound_u32(a.gstart, G, (uint32_t)x * REFINE_NOMINAL);
+    if (x <= tiles) a.tfirst[x] = lower_bound_u32(a.gstart, G, (uint32_t)x * a.nominal);
     if (x == 0) a.gstart[G] = m;
   }
 }
@@ -139,58 +139,153 @@ cudaError_t launch_gather_large(const GatherLargeArgs &a, cudaStream_t stream) {
 
 // ---- small groups: one tile per block ---------------------------------------
 
-constexpr int RF_BLOCK = 256;
-constexpr int RF_ITEMS = REFINE_CAP / RF_BLOCK;  // 16
-constexpr int RF_WARPS = RF_BLOCK / 32;
-constexpr int RF_MAXG = REFINE_NOMINAL / 2 + 1;  // groups have >= 2 members
-constexpr int RF_GPT = (RF_MAXG + RF_BLOCK - 1) / RF_BLOCK;  // groups per thread in scans
+template <int BLOCK, int CAP>
+struct RfCfg {
+  static constexpr int WARPS = BLOCK / 32;
+  static constexpr int ITEMS = CAP / BLOCK;       // slots per thread
+  static constexpr int NOMINAL = CAP / 2;         // tile window and largest small group
+  static constexpr int MAXG = NOMINAL / 2 + 1;    // groups have >= 2 members
+  static constexpr int GPT = (MAXG + BLOCK - 1) / BLOCK;  // groups per thread
+  static constexpr int DPT = RADIX / BLOCK;       // digits per thread in the digit scan
+  static_assert(ITEMS >= 1 && ITEMS <= 16, "slots per thread");
+  static_assert(DPT >= 1 && RADIX % BLOCK == 0, "digits per thread");
+};
 
+template <int BLOCK, int CAP>
 struct RfSmem {
-  uint64_t keys[REFINE_CAP + REFINE_CAP / 16];  // padded (e + e/16) after the last pass
-  uint32_t vals[REFINE_CAP + REFINE_CAP / 32];  // padded (e + e/32) after the last pass
+  using C = RfCfg<BLOCK, CAP>;
+  uint64_t keys[CAP + CAP / 16];  // padded (e + e/16) after the last pass
+  uint32_t vals[CAP + CAP / 32];  // padded (e + e/32) after the last pass
   union {
-    uint32_t gsrc[RF_MAXG];           // loading: first position of each local group
-    uint32_t match[RF_WARPS][RADIX];  // sorting: per-warp peer masks
+    uint32_t gsrc[C::MAXG];             // loading: first position of each local group
+    uint32_t match[C::WARPS][RADIX];    // sorting: per-warp peer masks
   };
-  uint16_t whist[RF_WARPS][RADIX];
+  uint16_t whist[2][C::WARPS][RADIX];   // per pass (double-buffered): counts, then prefixes
   uint32_t dstart[RADIX];
-  uint32_t gname[RF_MAXG];
-  uint32_t ghead[RF_MAXG];     // head rank (SA interval start) of the local group
-  uint32_t goff[RF_MAXG + 1];  // start of the local group in the tile (large groups: empty)
-  uint32_t tmp[RF_WARPS + 1];
-  uint32_t nitems, all_small, upd_base, surv_base, grp_base;
+  uint32_t gname[C::MAXG];
+  uint32_t ghead[C::MAXG];              // head rank (SA interval start) of the local group
+  uint32_t goff[C::MAXG + 1];           // start of the local group in the tile
+  uint32_t tmp[2][4 * C::WARPS];        // scan scratch (double-buffered)
+  uint32_t flag, all_small, upd_local, upd_base, surv_base, grp_base;
   unsigned long long orv;
 };
 
+// One-barrier exclusive sum over the block: warp scans, warp totals in
+// `tmp`, then every thread adds the totals of the warps before it. `tmp`
+// must not be rewritten before the next barrier.
+template <int BLOCK>
+__device__ __forceinline__ uint32_t rf_block_excl_sum(uint32_t v, uint32_t *tmp, uint32_t &total) {
+  constexpr int WARPS = BLOCK / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t incl = warp_inclusive(v, OpAdd());
+  if (lane == 31) tmp[warp] = incl;
+  __syncthreads();
+  uint32_t before = 0, all = 0;
+#pragma unroll
+  for (int w = 0; w < WARPS; ++w) {
+    const uint32_t t = tmp[w];
+    before += w < warp ? t : 0u;
+    all += t;
+  }
+  total = all;
+  return before + incl - v;
+}
+
+// One-barrier fused scans of the rename phase: exclusive max (mx), two
+// exclusive sums (s1, s2) and the exclusive suffix minimum (mn, over the
+// threads after this one).
+template <int BLOCK>
+__device__ __forceinline__ void rf_block_scan4(uint32_t mx, uint32_t s1, uint32_t s2, uint32_t mn,
+                                               uint32_t *tmp, uint32_t &ex_mx, uint32_t &ex_s1,
+                                               uint32_t &ex_s2, uint32_t &sf_mn, uint32_t &tot_s1,
+                                               uint32_t &tot_s2) {
+  constexpr int WARPS = BLOCK / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t imx = mx, is1 = s1, is2 = s2, imn = mn;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t omx = __shfl_up_sync(0xffffffffu, imx, d);
+    const uint32_t os1 = __shfl_up_sync(0xffffffffu, is1, d);
+    const uint32_t os2 = __shfl_up_sync(0xffffffffu, is2, d);
+    const uint32_t omn = __shfl_down_sync(0xffffffffu, imn, d);
+    if (lane >= d) {
+      imx = omx > imx ? omx : imx;
+      is1 += os1;
+      is2 += os2;
+    }
+    if (lane + d < 32) imn = omn < imn ? omn : imn;
+  }
+  if (lane == 31) {
+    tmp[warp] = imx;
+    tmp[WARPS + warp] = is1;
+    tmp[2 * WARPS + warp] = is2;
+  }
+  if (lane == 0) tmp[3 * WARPS + warp] = imn;
+  __syncthreads();
+  uint32_t pmx = 0, ps1 = 0, ps2 = 0, pmn = 0xFFFFFFFFu, t1 = 0, t2 = 0;
+#pragma unroll
+  for (int w = 0; w < WARPS; ++w) {
+    const uint32_t a1 = tmp[WARPS + w], a2 = tmp[2 * WARPS + w];
+    t1 += a1;
+    t2 += a2;
+    if (w < warp) {
+      const uint32_t a0 = tmp[w];
+      pmx = a0 > pmx ? a0 : pmx;
+      ps1 += a1;
+      ps2 += a2;
+    }
+    if (w > warp) {
+      const uint32_t a3 = tmp[3 * WARPS + w];
+      pmn = a3 < pmn ? a3 : pmn;
+    }
+  }
+  uint32_t emx = __shfl_up_sync(0xffffffffu, imx, 1);
+  if (lane == 0) emx = 0;
+  uint32_t nmn = __shfl_down_sync(0xffffffffu, imn, 1);
+  if (lane == 31) nmn = 0xFFFFFFFFu;
+  ex_mx = emx > pmx ? emx : pmx;
+  ex_s1 = ps1 + is1 - s1;
+  ex_s2 = ps2 + is2 - s2;
+  sf_mn = nmn < pmn ? nmn : pmn;
+  tot_s1 = t1;
+  tot_s2 = t2;
+}
+
 // Stable LSD radix sort of S.keys/S.vals[0, cnt) in shared memory over the
 // 8-bit digits below `nbits` that vary inside the tile. Warp w ranks the
-// contiguous chunk [w*C, (w+1)*C) with C = 32 * ceil(cnt / 256), so every
+// contiguous chunk [w*C, (w+1)*C) with C = 32 * ceil(cnt / BLOCK), so every
 // warp does the same useful work and (warp, slot, lane) is the input order.
 // The last pass writes the padded layout read by the rename phase (at
-// least one pass always runs).
-__device__ void rf_tile_sort(RfSmem &S, uint32_t cnt, unsigned long long varying, uint32_t nbits) {
+// least one pass always runs). Four barriers per pass.
+template <int BLOCK, int CAP>
+__device__ void rf_tile_sort(RfSmem<BLOCK, CAP> &S, uint32_t cnt, unsigned long long varying,
+                             uint32_t nbits) {
+  using C = RfCfg<BLOCK, CAP>;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t lt = lanemask_lt();
-  const uint32_t K = (cnt + RF_BLOCK - 1) / RF_BLOCK;  // slots per lane, <= RF_ITEMS
+  const uint32_t K = (cnt + BLOCK - 1) / BLOCK;  // slots per lane, <= ITEMS
   const uint32_t chunk = K * 32;
   const uint32_t ndig = (nbits + RADIX_BITS - 1) / RADIX_BITS;
-  for (int x = tid; x < RF_WARPS * RADIX; x += RF_BLOCK) (&S.match[0][0])[x] = 0u;
+  for (int x = tid; x < C::WARPS * RADIX; x += BLOCK) {
+    (&S.match[0][0])[x] = 0u;
+    (&S.whist[0][0][0])[x] = 0;
+  }
+  __syncthreads();
   uint32_t last = 0;
   for (uint32_t p = 0; p < ndig; ++p)
     if ((varying >> (p * RADIX_BITS)) & 0xFFull) last = p;
+  uint32_t buf = 0;
   for (uint32_t p = 0; p <= last; ++p) {
     const bool kept = ((varying >> (p * RADIX_BITS)) & 0xFFull) != 0ull;
     if (!kept && p != last) continue;
     const uint32_t shift = p * RADIX_BITS;
     const bool pad = p == last;
-    for (int x = tid; x < RF_WARPS * RADIX; x += RF_BLOCK) (&S.whist[0][0])[x] = 0;
-    __syncthreads();
-    uint64_t key[RF_ITEMS];
-    uint32_t val[RF_ITEMS], pos[RF_ITEMS];
-    uint16_t *wh = S.whist[warp];
+    uint64_t key[C::ITEMS];
+    uint32_t val[C::ITEMS], pos[C::ITEMS];
+    uint16_t *wh = S.whist[buf][warp];
     uint32_t *mt = S.match[warp];
 #pragma unroll
-    for (int k = 0; k < RF_ITEMS; ++k) {
+    for (int k = 0; k < C::ITEMS; ++k) {
       if ((uint32_t)k < K) {
         const uint32_t li = warp * chunk + k * 32 + lane;
         const bool valid = li < cnt;
@@ -201,59 +296,80 @@ __device__ void rf_tile_sort(RfSmem &S, uint32_t cnt, unsigned long long varying
       }
     }
     __syncthreads();
-    {
-      const uint32_t d = tid;
+    // Thread t owns digits [t*DPT, (t+1)*DPT): per-warp prefixes, then the
+    // block scan of the digit totals gives each digit's start in the tile.
+    uint32_t dsum = 0, dtot[C::DPT];
+#pragma unroll
+    for (int i = 0; i < C::DPT; ++i) {
+      const uint32_t d = tid * C::DPT + i;
       uint32_t total = 0;
 #pragma unroll
-      for (int w = 0; w < RF_WARPS; ++w) {
-        const uint32_t c = S.whist[w][d];
-        S.whist[w][d] = (uint16_t)total;
+      for (int w = 0; w < C::WARPS; ++w) {
+        const uint32_t c = S.whist[buf][w][d];
+        S.whist[buf][w][d] = (uint16_t)total;
         total += c;
       }
-      uint32_t tt;
-      S.dstart[d] = block_exclusive<RF_BLOCK>(total, OpAdd(), 0u, S.tmp, tt);
+      dtot[i] = total;
+      dsum += total;
+    }
+    uint32_t all;
+    uint32_t run = rf_block_excl_sum<BLOCK>(dsum, S.tmp[buf], all);
+#pragma unroll
+    for (int i = 0; i < C::DPT; ++i) {
+      S.dstart[tid * C::DPT + i] = run;
+      run += dtot[i];
     }
     __syncthreads();
+    uint16_t *nxt = &S.whist[buf ^ 1][0][0];
+    for (int x = tid; x < C::WARPS * RADIX; x += BLOCK) nxt[x] = 0;
 #pragma unroll
-    for (int k = 0; k < RF_ITEMS; ++k) {
+    for (int k = 0; k < C::ITEMS; ++k) {
       const uint32_t li = warp * chunk + k * 32 + lane;
       if ((uint32_t)k < K && li < cnt) {
         const uint32_t d = (uint32_t)(key[k] >> shift) & 0xFFu;
-        const uint32_t q = S.dstart[d] + S.whist[warp][d] + pos[k];
+        const uint32_t q = S.dstart[d] + S.whist[buf][warp][d] + pos[k];
         S.keys[pad ? q + (q >> 4) : q] = key[k];
         S.vals[pad ? q + (q >> 5) : q] = val[k];
       }
     }
     __syncthreads();
+    buf ^= 1;
   }
 }
 
-__global__ void __launch_bounds__(RF_BLOCK, 4) k_refine(RefineArgs a) {
+// Up to 8 slots per thread: 64 registers (4 blocks of 256 or 8 of 128 per
+// SM); 16 slots: 128 registers (such tiles fit 2 blocks per SM anyway).
+template <int BLOCK, int CAP>
+__global__ void __launch_bounds__(BLOCK, (CAP / BLOCK > 8 ? 512 : 1024) / BLOCK)
+    k_refine(RefineArgs a) {
+  using C = RfCfg<BLOCK, CAP>;
+  using Sm = RfSmem<BLOCK, CAP>;
   extern __shared__ __align__(128) uint8_t smem_raw[];
-  RfSmem &S = *reinterpret_cast<RfSmem *>(smem_raw);
+  Sm &S = *reinterpret_cast<Sm *>(smem_raw);
   const int tid = threadIdx.x;
   if (tid == 0) {
     S.orv = 0ull;
-    S.nitems = has_error(a.ctrl) ? 1u : 0u;  // borrowed as the bail flag
+    S.upd_local = 0u;
+    S.flag = has_error(a.ctrl) ? 1u : 0u;
   }
   __syncthreads();
-  if (S.nitems) return;
+  if (S.flag) return;
   const uint32_t tile = blockIdx.x;
   const uint32_t g0 = __ldg(a.tfirst + tile), g1 = __ldg(a.tfirst + tile + 1);
   const uint32_t ng = g1 - g0;
-  if (ng > (uint32_t)RF_MAXG) {  // never taken unless a logic error
+  if (ng > (uint32_t)C::MAXG) {  // never taken unless a logic error
     if (tid == 0) raise_error(a.ctrl, ERR_INTERNAL, 8);
     return;
   }
   if (ng == 0) return;
 
-  // Local group table: name, source position, size (0 for a large group),
-  // then exclusive offsets inside the tile.
-  uint32_t sz[RF_GPT];
+  // Local group table: source position, name, head rank, size (0 for a
+  // large group), then exclusive offsets inside the tile.
+  uint32_t sz[C::GPT];
   uint32_t mysum = 0, mybig = 0;
 #pragma unroll
-  for (int r = 0; r < RF_GPT; ++r) {
-    const uint32_t lg = tid * RF_GPT + r;
+  for (int r = 0; r < C::GPT; ++r) {
+    const uint32_t lg = tid * C::GPT + r;
     sz[r] = 0;
     if (lg < ng) {
       const uint32_t g = g0 + lg;
@@ -262,7 +378,7 @@ __global__ void __launch_bounds__(RF_BLOCK, 4) k_refine(RefineArgs a) {
       S.gname[lg] = __ldg(a.gname + g);
       S.ghead[lg] = __ldg(a.ghead + g);
       const uint32_t size = e - s;
-      if (size <= REFINE_SMALL_MAX)
+      if (size <= (uint32_t)C::NOMINAL)
         sz[r] = size;
       else
         mybig = 1;
@@ -270,34 +386,33 @@ __global__ void __launch_bounds__(RF_BLOCK, 4) k_refine(RefineArgs a) {
     }
   }
   uint32_t nitems;
-  uint32_t run = block_exclusive<RF_BLOCK>(mysum, OpAdd(), 0u, S.tmp, nitems);
+  uint32_t run = rf_block_excl_sum<BLOCK>(mysum, S.tmp[0], nitems);
 #pragma unroll
-  for (int r = 0; r < RF_GPT; ++r) {
-    const uint32_t lg = tid * RF_GPT + r;
+  for (int r = 0; r < C::GPT; ++r) {
+    const uint32_t lg = tid * C::GPT + r;
     if (lg < ng) S.goff[lg] = run;
     run += sz[r];
   }
   const int any_big = __syncthreads_or(mybig);
   if (tid == 0) {
     S.goff[ng] = nitems;
-    S.nitems = nitems;
     S.all_small = any_big ? 0u : 1u;
   }
   __syncthreads();
-  if (nitems > REFINE_CAP) {  // never taken unless a logic error
+  if (nitems > (uint32_t)CAP) {  // never taken unless a logic error
     if (tid == 0) raise_error(a.ctrl, ERR_INTERNAL, 9);
     return;
   }
   const uint32_t cnt = nitems;
   if (cnt == 0) return;
-  const uint32_t K = (cnt + RF_BLOCK - 1) / RF_BLOCK;
+  const uint32_t K = (cnt + BLOCK - 1) / BLOCK;
 
   // Load (g, i') and gather the partner names; all loads of a thread are
   // issued before their uses.
-  uint64_t ent[RF_ITEMS];
+  uint64_t ent[C::ITEMS];
 #pragma unroll
-  for (int k = 0; k < RF_ITEMS; ++k) {
-    const uint32_t q = k * RF_BLOCK + tid;
+  for (int k = 0; k < C::ITEMS; ++k) {
+    const uint32_t q = k * BLOCK + tid;
     ent[k] = 0ull;
     if ((uint32_t)k < K && q < cnt) {
       uint32_t src;
@@ -317,45 +432,49 @@ __global__ void __launch_bounds__(RF_BLOCK, 4) k_refine(RefineArgs a) {
       ent[k] = a.act[src];
     }
   }
-  uint32_t r2v[RF_ITEMS];
+  uint32_t r2v[C::ITEMS];
 #pragma unroll
-  for (int k = 0; k < RF_ITEMS; ++k) {
-    const uint32_t q = k * RF_BLOCK + tid;
+  for (int k = 0; k < C::ITEMS; ++k) {
+    const uint32_t q = k * BLOCK + tid;
     r2v[k] = 0;
     if ((uint32_t)k < K && q < cnt) {
       const uint64_t at = min((uint64_t)(uint32_t)ent[k] + a.h, a.isa_len - 1);
       r2v[k] = __ldg(a.isa + at) + 1u;
     }
   }
+  unsigned long long orv = 0ull;
+  uint64_t key0 = 0ull;
 #pragma unroll
-  for (int k = 0; k < RF_ITEMS; ++k) {
-    const uint32_t q = k * RF_BLOCK + tid;
+  for (int k = 0; k < C::ITEMS; ++k) {
+    const uint32_t q = k * BLOCK + tid;
     if ((uint32_t)k < K && q < cnt) {
       const uint32_t lgq = (uint32_t)(ent[k] >> 32) - g0;
-      S.keys[q] = ((uint64_t)lgq << a.W) | r2v[k];
+      const uint64_t key = ((uint64_t)lgq << a.W) | r2v[k];
+      S.keys[q] = key;
       S.vals[q] = (uint32_t)ent[k];
+      if (q == 0) key0 = key;
     }
   }
+  // Bits that vary inside the tile: OR of (key ^ first key). Every key
+  // shares the first key's local group 0 bits only when ng == 1, so the
+  // reference key is the tile's first key, read after the barrier.
   __syncthreads();
-  {
-    const uint64_t key0 = S.keys[0];
-    unsigned long long orv = 0ull;
+  key0 = S.keys[0];
 #pragma unroll
-    for (int k = 0; k < RF_ITEMS; ++k) {
-      const uint32_t q = k * RF_BLOCK + tid;
-      if ((uint32_t)k < K && q < cnt) orv |= S.keys[q] ^ key0;
-    }
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) orv |= __shfl_xor_sync(0xffffffffu, orv, d);
-    if ((tid & 31) == 0 && orv) atomicOr(&S.orv, orv);
+  for (int k = 0; k < C::ITEMS; ++k) {
+    const uint32_t q = k * BLOCK + tid;
+    if ((uint32_t)k < K && q < cnt) orv |= S.keys[q] ^ key0;
   }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) orv |= __shfl_xor_sync(0xffffffffu, orv, d);
+  if ((tid & 31) == 0 && orv) atomicOr(&S.orv, orv);
   __syncthreads();
   const uint32_t gbits = ng > 1 ? 32u - __clz(ng - 1) : 0u;
-  rf_tile_sort(S, cnt, S.orv, a.W + gbits);
+  rf_tile_sort<BLOCK, CAP>(S, cnt, S.orv, a.W + gbits);
 
   // Rename in blocked layout: items tid*K .. tid*K+K-1 of the sorted tile.
   const uint32_t l0 = tid * K;
-  bool f[RF_ITEMS + 1];
+  bool f[C::ITEMS + 1];
   {
     uint64_t prev = 0ull;
     if (l0 > 0 && l0 - 1 < cnt) {
@@ -363,7 +482,7 @@ __global__ void __launch_bounds__(RF_BLOCK, 4) k_refine(RefineArgs a) {
       prev = S.keys[e + (e >> 4)];
     }
 #pragma unroll
-    for (int k = 0; k <= RF_ITEMS; ++k) {
+    for (int k = 0; k <= C::ITEMS; ++k) {
       const uint32_t j = l0 + k;
       f[k] = true;
       if ((uint32_t)k <= K && j < cnt) {
@@ -378,7 +497,7 @@ __global__ void __launch_bounds__(RF_BLOCK, 4) k_refine(RefineArgs a) {
   // hold whole groups.
   uint32_t th_head = 0, th_first = 0xFFFFFFFFu, th_surv = 0, th_hs = 0;
 #pragma unroll
-  for (int k = 0; k < RF_ITEMS; ++k) {
+  for (int k = 0; k < C::ITEMS; ++k) {
     const uint32_t j = l0 + k;
     if ((uint32_t)k < K && j < cnt) {
       const bool uniq = f[k] && f[k + 1];
@@ -392,15 +511,15 @@ __global__ void __launch_bounds__(RF_BLOCK, 4) k_refine(RefineArgs a) {
       }
     }
   }
-  uint32_t tot_head;
-  const uint32_t ex_head = block_exclusive<RF_BLOCK>(th_head, OpMax(), 0u, S.tmp, tot_head);
-  uint32_t next_head = block_suffix_min_exclusive<RF_BLOCK>(th_first, S.tmp);
+  uint32_t ex_head, ex_surv, ex_hs, next_head, tot_surv, tot_hs;
+  rf_block_scan4<BLOCK>(th_head, th_surv, th_hs, th_first, S.tmp[1], ex_head, ex_surv, ex_hs,
+                        next_head, tot_surv, tot_hs);
   if (next_head > cnt) next_head = cnt;
-  uint32_t rend[RF_ITEMS];
+  uint32_t rend[C::ITEMS];
   {
     uint32_t e = next_head;
 #pragma unroll
-    for (int k = RF_ITEMS - 1; k >= 0; --k) {
+    for (int k = C::ITEMS - 1; k >= 0; --k) {
       const uint32_t j = l0 + k;
       rend[k] = e;
       if ((uint32_t)k < K && j < cnt && f[k]) e = j;
@@ -414,11 +533,13 @@ __global__ void __launch_bounds__(RF_BLOCK, 4) k_refine(RefineArgs a) {
     const uint32_t len = end - start, old = S.gname[lgq];
     return old - lo < len ? old : lo + len / 2;
   };
+  // Changed names are queued in any order: a shared-memory atomic gives
+  // each thread its slots, one global atomic the tile's.
   uint32_t th_chg = 0;
   {
     uint32_t rh = ex_head;
 #pragma unroll
-    for (int k = 0; k < RF_ITEMS; ++k) {
+    for (int k = 0; k < C::ITEMS; ++k) {
       const uint32_t j = l0 + k;
       if ((uint32_t)k < K && j < cnt) {
         if (f[k]) rh = j;
@@ -427,10 +548,8 @@ __global__ void __launch_bounds__(RF_BLOCK, 4) k_refine(RefineArgs a) {
       }
     }
   }
-  uint32_t tot_surv, tot_hs, tot_chg;
-  const uint32_t ex_surv = block_exclusive<RF_BLOCK>(th_surv, OpAdd(), 0u, S.tmp, tot_surv);
-  const uint32_t ex_hs = block_exclusive<RF_BLOCK>(th_hs, OpAdd(), 0u, S.tmp, tot_hs);
-  const uint32_t ex_chg = block_exclusive<RF_BLOCK>(th_chg, OpAdd(), 0u, S.tmp, tot_chg);
+  const uint32_t my_chg = th_chg ? atomicAdd(&S.upd_local, th_chg) : 0u;
+  __syncthreads();
 
   // Output space: the next active list only needs each group contiguous, so
   // one 64-bit atomic reserves this tile's survivors (low word) and groups
@@ -443,15 +562,15 @@ __global__ void __launch_bounds__(RF_BLOCK, 4) k_refine(RefineArgs a) {
                             : 0ull;
     S.surv_base = (uint32_t)old;
     S.grp_base = (uint32_t)(old >> 32);
-    S.upd_base = tot_chg ? atomicAdd(&a.ctrl->rc.upd, tot_chg) : 0u;
+    S.upd_base = S.upd_local ? atomicAdd(&a.ctrl->rc.upd, S.upd_local) : 0u;
   }
   __syncthreads();
   uint32_t run_head = ex_head;
   uint32_t run_surv = S.surv_base + ex_surv;
   uint32_t run_hs = S.grp_base + ex_hs;
-  uint32_t run_chg = S.upd_base + ex_chg;
+  uint32_t run_chg = S.upd_base + my_chg;
 #pragma unroll
-  for (int k = 0; k < RF_ITEMS; ++k) {
+  for (int k = 0; k < C::ITEMS; ++k) {
     const uint32_t j = l0 + k;
     if ((uint32_t)k < K && j < cnt) {
       if (f[k]) run_head = j;
@@ -480,20 +599,32 @@ __global__ void __launch_bounds__(RF_BLOCK, 4) k_refine(RefineArgs a) {
   }
 }
 
-cudaError_t launch_refine(const RefineArgs &a, cudaStream_t stream) {
-  if (a.tiles == 0) return cudaSuccess;
+template <int BLOCK, int CAP>
+cudaError_t launch_refine_t(const RefineArgs &a, cudaStream_t stream) {
   static bool configured = false;
-  const int smem = (int)sizeof(RfSmem);
+  const int smem = (int)sizeof(RfSmem<BLOCK, CAP>);
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(k_refine<BLOCK, CAP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_refine, cudaFuncAttributePreferredSharedMemoryCarveout,
+    e = cudaFuncSetAttribute(k_refine<BLOCK, CAP>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  k_refine<<<a.tiles, RF_BLOCK, smem, stream>>>(a);
+  k_refine<BLOCK, CAP><<<a.tiles, BLOCK, smem, stream>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_refine(const RefineArgs &a, cudaStream_t stream) {
+  if (a.tiles == 0) return cudaSuccess;
+  switch (a.shape) {
+    case 0: return launch_refine_t<128, 1024>(a, stream);
+    case 1: return launch_refine_t<256, 2048>(a, stream);
+    case 2: return launch_refine_t<256, 4096>(a, stream);
+    case 3: return launch_refine_t<256, 1024>(a, stream);
+  }
+  return cudaErrorInvalidValue;
 }
 
 // ---- names of the rename's survivors ------------------------------------------

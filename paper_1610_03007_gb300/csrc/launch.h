@@ -94,9 +94,16 @@ cudaError_t launch_rename(const RenameArgs &a, cudaStream_t stream);
 // Groups of up to REFINE_SMALL_MAX members are refined inside one tile
 // (gather, shared-memory sort, rename, compaction); larger ones go through
 // the global radix sort and k_rename.
-constexpr uint32_t REFINE_NOMINAL = 1024;  // tile t owns groups starting in [t, t+1) * this
-constexpr uint32_t REFINE_CAP = 2048;      // items one tile can hold
-constexpr uint32_t REFINE_SMALL_MAX = REFINE_CAP - REFINE_NOMINAL;
+// Tile shapes of the refine (threads per block, items one tile can hold).
+// Tile t owns the groups whose starts fall in [t, t+1) * cap/2 of the
+// active list, so groups of up to cap/2 members are "small".
+struct RefineShape {
+  uint32_t block, cap;
+};
+constexpr int REFINE_SHAPES = 4;
+constexpr RefineShape REFINE_SHAPE[REFINE_SHAPES] = {{128, 1024}, {256, 2048}, {256, 4096},
+                                                     {256, 1024}};
+constexpr uint32_t REFINE_MIN_NOMINAL = 512;  // smallest cap/2 (buffer sizing)
 
 // Names of groups. A name may be any rank inside the group's SA interval:
 // intervals are disjoint and ordered, so such names respect the order of
@@ -118,6 +125,7 @@ struct ClassifyArgs {
   uint32_t *lg, *loff, *lbase, *lold;  // large groups: index, start in the large
                                        // list, head - start, name
   uint32_t *tfirst;         // first group of each refine tile (tiles + 1 entries)
+  uint32_t nominal;         // refine tile window (cap / 2); also the largest small group
   uint32_t max_groups;      // upper bound of G (buffer capacity)
   uint32_t max_tiles;       // upper bound of tiles (buffer capacity - 1)
   Ctrl *ctrl;               // reads rc.m_s + rc.m_l, rc.g_s + rc.g_l; adds to rc.large
@@ -146,6 +154,7 @@ struct RefineArgs {
   const uint32_t *ghead;    // head rank of each group
   uint32_t naming;          // NamingRule
   const uint32_t *tfirst;   // tiles + 1 entries
+  uint32_t shape;           // index into REFINE_SHAPE
   uint32_t m, G, tiles;
   uint32_t h, W;
   const uint32_t *isa;      // read only (updates are deferred)

@@ -200,3 +200,15 @@ def test_repeated_builds_reuse_workspace(gb, orc):
             t = gen.text(recipe, seed, 1 << 18)
             sa, _, _, _ = gb.sa_build_ex(dev_text(t), workspace=ws)
             assert np.array_equal(sa.cpu().numpy().view(np.uint32), orc.pd_sa(t)[0])
+
+
+@pytest.mark.parametrize("shape", [1, 2, 3, 4])
+@pytest.mark.parametrize("recipe", ["zipf_repeats", "markov", "bytes"])
+def test_every_refine_tile_shape(gb, orc, shape, recipe):
+    """Each refine tile shape (which also moves the small/large group
+    threshold) gives the oracle's SA and ISA."""
+    t = gen.text(recipe, 90 + shape, (1 << 20) + 3 * shape)
+    sa, isa, _, _ = gb.sa_build_ex(dev_text(t), isa=True, refine_shape=shape)
+    osa, oisa, _, _ = orc.pd_sa(t)
+    assert np.array_equal(sa.cpu().numpy().view(np.uint32), osa)
+    assert np.array_equal(isa.cpu().numpy().view(np.uint32), oisa)
