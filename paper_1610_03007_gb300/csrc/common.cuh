@@ -205,6 +205,50 @@ __device__ __forceinline__ bool look_back(const uint64_t *status, uint32_t strid
   return true;
 }
 
+// Look-back with an associative operator reading a window of 4
+// predecessors per round trip (see look_back_sum4).
+template <class Op>
+__device__ __forceinline__ bool look_back4(const uint64_t *status, uint32_t stride, uint32_t slot,
+                                           uint32_t tile, uint32_t epoch, Op op, uint32_t &carry,
+                                           Ctrl *ctrl, uint32_t spin_limit) {
+  int64_t p = (int64_t)tile - 1;
+  uint32_t spins = 0, ns = 32;
+  const uint32_t ep = epoch & EPOCH_MASK;
+  while (p >= 0) {
+    uint64_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      w[k] = (p - k >= 0) ? status_load(status + (size_t)(p - k) * stride + slot) : 0ull;
+    int used = 0;
+    bool done = false, blocked = false;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (!done && !blocked && p - k >= 0) {
+        const uint32_t tag = (uint32_t)(w[k] >> 32);
+        if ((tag >> 2) != ep || (tag & 3u) == 0u) {
+          blocked = true;
+        } else {
+          carry = op(carry, (uint32_t)w[k]);
+          ++used;
+          if ((tag & 3u) == ST_INC) done = true;
+        }
+      }
+    }
+    if (done) return true;
+    p -= used;
+    if (used == 0) {
+      if (++spins > spin_limit) {
+        raise_error(ctrl, ERR_TIMEOUT, 1);
+        return false;
+      }
+      if ((spins & 15u) == 0u && has_error(ctrl)) return false;
+      __nanosleep(ns);
+      if (ns < 1024) ns <<= 1;
+    }
+  }
+  return true;
+}
+
 // Sum look-back that reads a window of 4 predecessors per round trip
 // (independent loads), so a chain of tiles that have only published their
 // aggregates costs a quarter of the dependent latencies. `stride`/`slot`
@@ -291,6 +335,22 @@ __device__ __forceinline__ uint32_t warp_rank_digit(uint32_t d, uint32_t *match,
   }
   __syncwarp();
   return before + __popc(lower);
+}
+
+// Local index of gapped position ip: text s occupies the gapped positions
+// [seg_off[s] + s, seg_off[s+1] + s) (the slot after it is its end
+// sentinel), so gapped starts increase strictly even across empty texts.
+__device__ __forceinline__ uint32_t local_index(uint32_t ip, const uint32_t *seg_off, uint32_t S) {
+  if (S <= 1) return ip;
+  uint32_t lo = 0, hi = S - 1;  // the last s with seg_off[s] + s <= ip
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (__ldg(seg_off + mid) + mid <= ip)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return ip - (__ldg(seg_off + lo) + lo);
 }
 
 // Inclusive warp scan.

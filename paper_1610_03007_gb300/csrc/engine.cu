@@ -328,12 +328,16 @@ struct Build {
 
   // Radix sort of (ka, va)[0, m) by the digits of spec; result where the
   // device plan says (plan->kfinal / vfinal).
-  sa_status sort(uint32_t m, const DigitSpec &spec) {
-    CK(cudaMemsetAsync(hist, 0, (size_t)spec.P * RADIX * 4, st));
-    sa_status s = launch(SA_K_DIGIT_HIST, 0, 8ull * m, [&] {
-      return launch_digit_histogram(ka, m, spec, hist, sm_count(), st);
-    });
-    if (s != SA_OK) return s;
+  sa_status sort(uint32_t m, const DigitSpec &spec, bool hist_ready = false) {
+    sa_status s = SA_OK;
+    if (!hist_ready) {
+      CK(cudaMemsetAsync(hist, 0, (size_t)spec.P * RADIX * 4, st));
+      s = launch(SA_K_DIGIT_HIST, 0, 8ull * m, [&] {
+        return launch_digit_histogram(ka, m, spec, hist, sm_count(), st);
+      });
+      if (s != SA_OK) return s;
+      bytes += 8ull * m;  // histogram read
+    }
     s = launch(SA_K_PLAN, 0, (uint64_t)spec.P * RADIX * 8, [&] {
       return launch_sort_plan(hist, dbase, spec, m, ka, kb, va, vb, plan, ctrl, st);
     });
@@ -356,7 +360,6 @@ struct Build {
       if (s != SA_OK) return s;
     }
     inject_pending = false;
-    bytes += 8ull * m;  // histogram read
     return SA_OK;
   }
 
@@ -388,6 +391,7 @@ struct Build {
     ra.old_in = old_in;
     ra.g_in = g_in;
     ra.isa = isa;
+    ra.upd = upd;
     ra.isa_len = N + S + 1;
     ra.N = (uint32_t)N;
     ra.sa = sa;
@@ -431,12 +435,12 @@ struct Build {
     });
   }
 
-  // Rename (round 0 or large groups) reads 12 bytes per item plus 4 per
-  // item for the ISA write, 4 per unique item (SA), 8 per survivor and 8
-  // per surviving group.
+  // Rename (round 0 or large groups) reads 12 bytes per item; writes 4
+  // (SA) + 8 (queued ISA entry) per unique item, 8 per survivor and 12 per
+  // surviving group (start, head rank, parent name).
   static uint64_t rename_bytes(uint32_t m, uint32_t surv, uint32_t groups) {
     const uint64_t u = m - surv;
-    return 16ull * m + 4 * u + 8ull * surv + 8ull * groups;
+    return 12ull * m + 12 * u + 8ull * surv + 12ull * groups;
   }
 
   // Refine: 8 bytes read and a 4-byte gather per item, 8 bytes of group
@@ -518,20 +522,21 @@ struct Build {
     pk.cb = cb;
     pk.keys = ka;
     pk.vals = va;
+    const uint32_t bits0 = cb + segbits;
+    pk.spec = spec_for(bits0);
+    pk.hist = hist;
+    CK(cudaMemsetAsync(hist, 0, (size_t)pk.spec.P * RADIX * 4, st));
     s = launch(SA_K_PACK, 0, 13ull * N, [&] { return launch_pack(pk, st); });
     if (s != SA_OK) return s;
     bytes += 13ull * N;
-    const uint32_t bits0 = cb + segbits;
     inject_pending = opt.inject_stall != 0;
-    s = sort(N32, spec_for(bits0));
+    s = sort(N32, pk.spec, true);
     if (s != SA_OK) return s;
     int cur = 0;  // the active list, group starts and names of this round
     s = rename(N32, true, cb, c0, 0, nullptr, nullptr, 0, cur, ctrl->zero);
     if (s != SA_OK) return s;
     s = classify(cur, N / 2 + 1);
     if (s != SA_OK) return s;
-    if (opt.trace_isa && opt.trace_cap > 0 && S == 1)
-      CK(cudaMemcpyAsync(opt.trace_isa, isa, N * 4, cudaMemcpyDeviceToDevice, st));
     HostCtrl hc{};
     s = read_ctrl(hc);
     if (s != SA_OK) return s;
@@ -541,6 +546,17 @@ struct Build {
     if (s != SA_OK) return s;
     record(0, m, hc, bits0);
     bytes += (uint64_t)hc.passes * 24 * m + rb0;
+    // The unique suffixes' ISA entries are needed only by a later round, the
+    // ISA output or the trace; a text resolved in round 0 skips them.
+    const bool want_trace = opt.trace_isa && opt.trace_cap > 0 && S == 1;
+    if (hc.m_next() > 0 || isa_out || want_trace) {
+      s = launch(SA_K_SCATTER, 0, 12ull * hc.upd, [&] {
+        return launch_scatter_updates(upd, N32, isa, N + S + 1, ctrl, sm_count(), st);
+      });
+      if (s != SA_OK) return s;
+      bytes += 12ull * hc.upd;
+    }
+    if (want_trace) CK(cudaMemcpyAsync(opt.trace_isa, isa, N * 4, cudaMemcpyDeviceToDevice, st));
 
     // ---- rounds r >= 1: one doubling step each ----
     const uint32_t W = bits_for(N);  // r2 in [0, N]
@@ -595,6 +611,8 @@ struct Build {
       rf.isa_len = N + S + 1;
       rf.N = N32;
       rf.sa = sa;
+      rf.seg_off = segoff;
+      rf.S = S;
       rf.act_out = act[nxt];
       rf.gstart_out = gstart[nxt];
       rf.gname_out = gname[nxt];
@@ -636,11 +654,6 @@ struct Build {
       ++round;
     }
     // ---- output ----
-    if (S > 1) {
-      s = launch(SA_K_OUTPUT, 0, 8ull * N, [&] { return launch_sa_to_local(sa, N32, segoff, S, st); });
-      if (s != SA_OK) return s;
-      bytes += 8ull * N;
-    }
     if (isa_out) {
       s = launch(SA_K_OUTPUT, 0, 8ull * N, [&] {
         return launch_isa_to_local(isa, isa_out, N32, segoff, S, st);

@@ -17,40 +17,90 @@
 // and the slot right after it is an end sentinel of the ISA.
 //
 // Bound: HBM, N bytes read (+ L1-cached overlap of c0-1 bytes per key),
-// 12 N bytes written.
+// 12 N bytes written; the digit histograms of the following sort are
+// accumulated in shared memory on the way.
 #include "launch.h"
 
 namespace gbsa {
 
 constexpr int PACK_BLOCK = 256;
+constexpr int PACK_ITEMS = 8;
+constexpr int PACK_SPAN = PACK_BLOCK * PACK_ITEMS;
 
+// One block packs PACK_SPAN consecutive keys. The text of the block's first
+// and last key is found once; keys in between search only that range. The
+// 256-bin histograms of every radix digit of the keys (the one-sweep
+// sort's upfront histogram) are accumulated here as well, so the sort needs
+// no separate read of the keys.
 __global__ void __launch_bounds__(PACK_BLOCK) k_pack(PackArgs a) {
   __shared__ uint8_t s_code[RADIX];
-  s_code[threadIdx.x] = a.code[threadIdx.x];
+  __shared__ uint32_t s_hist[MAX_PASSES][RADIX];
+  __shared__ uint32_t s_seg[2];
+  const int tid = threadIdx.x, lane = tid & 31;
+  s_code[tid] = a.code[tid];
+  for (int x = tid; x < MAX_PASSES * RADIX; x += PACK_BLOCK) (&s_hist[0][0])[x] = 0;
+  const uint64_t j0 = (uint64_t)blockIdx.x * PACK_SPAN;
+  if (tid < 2 && a.S > 1) {
+    const uint64_t jl = min(j0 + PACK_SPAN, (uint64_t)a.N) - 1;
+    s_seg[tid] = segment_of(a.seg_off, a.S, (uint32_t)(tid == 0 ? j0 : jl));
+  }
   __syncthreads();
-  const uint64_t j64 = (uint64_t)blockIdx.x * PACK_BLOCK + threadIdx.x;
-  if (j64 >= a.N) return;
-  const uint32_t j = (uint32_t)j64;
-  const uint32_t s = a.S > 1 ? segment_of(a.seg_off, a.S, j) : 0u;
-  const uint32_t off = __ldg(a.seg_off + s);
-  const uint32_t len = __ldg(a.seg_off + s + 1) - off;
-  const uint32_t rel = j - off;
-  const uint32_t t = len < a.c0 - 1 ? len : a.c0 - 1;  // tail positions of this text
-  const uint32_t irel = rel < t ? len - 1 - rel : rel - t;
-  const uint32_t avail = len - irel;
-  const uint32_t take = avail < a.c0 ? avail : a.c0;
-  const uint8_t *p = a.text + off + irel;
-  uint64_t key = 0;
-  for (uint32_t q = 0; q < take; ++q)
-    key |= (uint64_t)s_code[__ldg(p + q)] << (a.cb - a.b * (q + 1));
-  if (a.S > 1) key |= (uint64_t)s << a.cb;
-  a.keys[j] = key;
-  a.vals[j] = off + irel + s;
+  const uint32_t s_lo = a.S > 1 ? s_seg[0] : 0u, s_hi = a.S > 1 ? s_seg[1] : 0u;
+#pragma unroll
+  for (int k = 0; k < PACK_ITEMS; ++k) {
+    const uint64_t j64 = j0 + (uint64_t)k * PACK_BLOCK + tid;
+    const bool valid = j64 < a.N;
+    uint64_t key = 0;
+    if (valid) {
+      const uint32_t j = (uint32_t)j64;
+      uint32_t s = s_lo;
+      if (s_hi != s_lo) {  // the last s in [s_lo, s_hi] with seg_off[s] <= j
+        uint32_t lo = s_lo, hi = s_hi;
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi + 1) >> 1;
+          if (__ldg(a.seg_off + mid) <= j)
+            lo = mid;
+          else
+            hi = mid - 1;
+        }
+        s = lo;
+      }
+      const uint32_t off = __ldg(a.seg_off + s);
+      const uint32_t len = __ldg(a.seg_off + s + 1) - off;
+      const uint32_t rel = j - off;
+      const uint32_t t = len < a.c0 - 1 ? len : a.c0 - 1;  // tail positions of this text
+      const uint32_t irel = rel < t ? len - 1 - rel : rel - t;
+      const uint32_t avail = len - irel;
+      const uint32_t take = avail < a.c0 ? avail : a.c0;
+      const uint8_t *p = a.text + off + irel;
+      for (uint32_t q = 0; q < take; ++q)
+        key |= (uint64_t)s_code[__ldg(p + q)] << (a.cb - a.b * (q + 1));
+      if (a.S > 1) key |= (uint64_t)s << a.cb;
+      a.keys[j] = key;
+      a.vals[j] = off + irel + s;
+    }
+    // Digit histograms (warp-aggregated when a warp shares a digit).
+    const uint32_t nvalid = __popc(__ballot_sync(0xffffffffu, valid));
+    for (uint32_t p = 0; p < a.spec.P; ++p) {
+      const uint32_t d = digit_of(key, a.spec.shift[p], a.spec.bits[p]);
+      const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
+      if (__all_sync(0xffffffffu, !valid || d == d0)) {
+        if (lane == 0 && nvalid) atomicAdd(&s_hist[p][d0], nvalid);
+      } else if (valid) {
+        atomicAdd(&s_hist[p][d], 1u);
+      }
+    }
+  }
+  __syncthreads();
+  for (uint32_t x = tid; x < a.spec.P * RADIX; x += PACK_BLOCK) {
+    const uint32_t v = (&s_hist[0][0])[x];
+    if (v) atomicAdd(&a.hist[x], v);
+  }
 }
 
 cudaError_t launch_pack(const PackArgs &a, cudaStream_t stream) {
   if (a.N == 0) return cudaSuccess;
-  uint64_t grid = ((uint64_t)a.N + PACK_BLOCK - 1) / PACK_BLOCK;
+  const uint64_t grid = ((uint64_t)a.N + PACK_SPAN - 1) / PACK_SPAN;
   k_pack<<<(unsigned)grid, PACK_BLOCK, 0, stream>>>(a);
   return cudaGetLastError();
 }

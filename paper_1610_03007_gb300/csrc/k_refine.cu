@@ -584,7 +584,7 @@ __global__ void __launch_bounds__(BLOCK, (CAP / BLOCK > 8 ? 512 : 1024) / BLOCK)
       }
       if (name != S.gname[lgq]) a.upd[run_chg++] = ((uint64_t)name << 32) | ip;
       if (f[k] && f[k + 1]) {
-        a.sa[name] = ip;
+        a.sa[name] = local_index(ip, a.seg_off, a.S);
       } else {
         if (f[k]) {
           a.gstart_out[run_hs] = run_surv;

@@ -14,8 +14,9 @@
 //    small ones).
 //  - Unique (Algorithm 6): new_j differs from both neighbours, i.e.
 //    f_j and f_{j+1} (f_m = 1).
-//  - Discarding (Algorithm 5): a unique item is final and writes ISA[i] =
-//    SA position and SA[pos] = i; the others are compacted, in order, into
+//  - Discarding (Algorithm 5): a unique item is final: it writes SA[pos] = i
+//    and queues ISA[i] = pos (applied by k_scatter_updates when a later
+//    round or an output reads the ISA); the others are compacted, in order, into
 //    the next active list with their group ordinal g', and each group's head
 //    records its start in that list, its head rank and its parent's name
 //    (the group's own name and the ISA entries of its members follow in
@@ -27,14 +28,15 @@
 // All partner names of a round were gathered by an earlier kernel, so the
 // ISA writes here never race with reads of the same round.
 //
-// Bound: HBM. 12 bytes read per item; 4 bytes random ISA and SA writes per
-// unique item, 8 bytes per survivor.
+// Bound: HBM. 12 bytes read per item; per unique item 4 bytes of SA (in
+// rank order: sequential in round 0) and 8 queued bytes; 8 bytes per
+// survivor.
 #include "launch.h"
 
 namespace gbsa {
 
 constexpr int RN_BLOCK = 256;
-constexpr int RN_ITEMS = 16;
+constexpr int RN_ITEMS = 8;
 constexpr int RN_TILE = RN_BLOCK * RN_ITEMS;
 constexpr int RN_WARPS = RN_BLOCK / 32;
 static_assert(RN_TILE == RENAME_TILE, "tile size mismatch");
@@ -46,19 +48,21 @@ struct RnSmem {
   uint32_t prev_val, next_val;
   uint32_t tmp[RN_WARPS + 1];
   uint32_t carry[3];
-  uint32_t tile, bail;
+  uint32_t tile, bail, upd_local, upd_base;
 };
 
 __device__ __forceinline__ uint32_t kidx(uint32_t e) { return e + (e >> 4); }
 __device__ __forceinline__ uint32_t vidx(uint32_t e) { return e + (e >> 5); }
 
-__global__ void __launch_bounds__(RN_BLOCK) k_rename(RenameArgs a) {
+// 64 registers: 4 blocks of 256 threads per SM (26 KB of shared memory each).
+__global__ void __launch_bounds__(RN_BLOCK, 4) k_rename(RenameArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   RnSmem &S = *reinterpret_cast<RnSmem *>(smem_raw);
   const int tid = threadIdx.x;
   if (tid == 0) {
     S.tile = atomicAdd(a.tile_ctr, 1u);
     S.bail = has_error(a.ctrl) ? 1u : 0u;
+    S.upd_local = 0u;
   }
   __syncthreads();
   if (S.bail) return;
@@ -106,7 +110,8 @@ __global__ void __launch_bounds__(RN_BLOCK) k_rename(RenameArgs a) {
   // Round 0: does the suffix at gapped position v (key k) have fewer than
   // c0 characters left in its text?
   auto tail = [&](uint64_t k, uint32_t v) -> bool {
-    const uint32_t s = a.S > 1 ? (uint32_t)(k >> a.cb) : 0u;
+    if (a.S <= 1) return a.N - v < a.c0;  // one text: gapped = plain positions
+    const uint32_t s = (uint32_t)(k >> a.cb);
     const uint32_t off = __ldg(a.seg_off + s);
     const uint32_t len = __ldg(a.seg_off + s + 1) - off;
     return len - (v - (off + s)) < a.c0;
@@ -125,7 +130,7 @@ __global__ void __launch_bounds__(RN_BLOCK) k_rename(RenameArgs a) {
     if (a.round0 && j > 0 && j < a.m) b = b || is_tail[k + 1] || is_tail[k];
     f[k] = b;
   }
-  uint32_t th_head = 0, th_surv = 0, th_hs = 0;
+  uint32_t th_head = 0, th_surv = 0, th_hs = 0, th_uniq = 0;
 #pragma unroll
   for (int k = 0; k < RN_ITEMS; ++k) {
     if (l0 + k < count) {
@@ -134,9 +139,14 @@ __global__ void __launch_bounds__(RN_BLOCK) k_rename(RenameArgs a) {
       if (!uniq) {
         ++th_surv;
         if (f[k]) ++th_hs;
+      } else {
+        ++th_uniq;
       }
     }
   }
+  // ISA entries of new unique suffixes are queued (in any order) and applied
+  // only when a later round, the ISA output or the trace reads them.
+  const uint32_t my_upd = th_uniq ? atomicAdd(&S.upd_local, th_uniq) : 0u;
   uint32_t tot_head, tot_surv, tot_hs;
   const uint32_t ex_head = block_exclusive<RN_BLOCK>(th_head, OpMax(), 0u, S.tmp, tot_head);
   const uint32_t ex_surv = block_exclusive<RN_BLOCK>(th_surv, OpAdd(), 0u, S.tmp, tot_surv);
@@ -154,9 +164,9 @@ __global__ void __launch_bounds__(RN_BLOCK) k_rename(RenameArgs a) {
     } else {
       status_store(st, status_word(a.epoch, ST_AGG, agg));
       if (which == 0)
-        ok = look_back(a.status, 3, which, tile, a.epoch, OpMax(), carry, a.ctrl, a.spin_limit);
+        ok = look_back4(a.status, 3, which, tile, a.epoch, OpMax(), carry, a.ctrl, a.spin_limit);
       else
-        ok = look_back(a.status, 3, which, tile, a.epoch, OpAdd(), carry, a.ctrl, a.spin_limit);
+        ok = look_back4(a.status, 3, which, tile, a.epoch, OpAdd(), carry, a.ctrl, a.spin_limit);
       if (ok) {
         const uint32_t inc = which == 0 ? (carry > agg ? carry : agg) : carry + agg;
         status_store(st, status_word(a.epoch, ST_INC, inc));
@@ -167,10 +177,15 @@ __global__ void __launch_bounds__(RN_BLOCK) k_rename(RenameArgs a) {
   }
   __syncthreads();
   if (S.bail) return;
-  if (tid == 0 && base + count == a.m) {
-    a.cnt_out[0] = S.carry[1] + tot_surv;
-    a.cnt_out[1] = S.carry[2] + tot_hs;
+  if (tid == 0) {
+    if (base + count == a.m) {
+      a.cnt_out[0] = S.carry[1] + tot_surv;
+      a.cnt_out[1] = S.carry[2] + tot_hs;
+    }
+    S.upd_base = S.upd_local ? atomicAdd(&a.ctrl->rc.upd, S.upd_local) : 0u;
   }
+  __syncthreads();
+  uint32_t run_upd = S.upd_base + my_upd;
   const uint32_t m_off = __ldg(a.off_in), g_off = __ldg(a.off_in + 1);
 
   uint32_t run_head = S.carry[0] > ex_head ? S.carry[0] : ex_head;
@@ -195,9 +210,19 @@ __global__ void __launch_bounds__(RN_BLOCK) k_rename(RenameArgs a) {
         continue;
       }
       if (f[k] && f[k + 1]) {
-        // Unique: its name is its rank, final (Algorithm 5 discards it).
-        a.isa[ip] = head;
-        a.sa[head] = ip;
+        // Unique: its name is its rank, final (Algorithm 5 discards it). SA
+        // holds the index local to the suffix's own text.
+        a.upd[run_upd++] = ((uint64_t)head << 32) | ip;
+        uint32_t local = ip;
+        if (a.S > 1) {
+          if (a.round0) {
+            const uint32_t s = (uint32_t)(kk >> a.cb);
+            local = ip - (__ldg(a.seg_off + s) + s);
+          } else {
+            local = local_index(ip, a.seg_off, a.S);
+          }
+        }
+        a.sa[head] = local;
       } else {
         // Survivors get their names, and their ISA entries, once the group
         // sizes are known (k_classify, k_apply_names).

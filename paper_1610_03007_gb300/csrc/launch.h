@@ -27,6 +27,8 @@ struct PackArgs {
   uint32_t cb;             // c0 * b (segment id sits above these bits)
   uint64_t *keys;          // out: N keys, tail-first order per text
   uint32_t *vals;          // out: N gapped positions
+  DigitSpec spec;          // digits of the following radix sort
+  uint32_t *hist;          // out: += their histograms (P * 256, zeroed by the caller)
 };
 cudaError_t launch_pack(const PackArgs &a, cudaStream_t stream);
 
@@ -71,10 +73,11 @@ struct RenameArgs {
   const uint32_t *base_in;   // later rounds: head rank - start of group g
   const uint32_t *old_in;    // later rounds: name of group g (round 0: NULL)
   uint32_t g_in;             // later rounds: groups in base_in (bounds guard)
-  uint32_t *isa;             // gapped ISA (written for new unique suffixes only)
+  uint64_t *upd;             // queued ISA entries (head << 32 | i') of new unique suffixes
+  uint32_t *isa;             // gapped ISA (not written; bounds of gapped positions)
   uint64_t isa_len;          // entries of isa (bounds guard)
   uint32_t N;                // total characters = entries of sa (bounds guard)
-  uint32_t *sa;              // SA of gapped positions
+  uint32_t *sa;              // SA, written with indices local to each text
   uint64_t *act_out;         // survivors: (g' << 32) | i'
   uint32_t *gstart_out;      // start of each surviving group in act_out
   uint32_t *ghead_out;       // head rank (SA interval start) of each surviving group
@@ -87,7 +90,7 @@ struct RenameArgs {
   Ctrl *ctrl;
   uint32_t spin_limit;
 };
-constexpr int RENAME_TILE = 256 * 16;
+constexpr int RENAME_TILE = 256 * 8;
 cudaError_t launch_rename(const RenameArgs &a, cudaStream_t stream);
 
 // ---- rounds >= 1: small-group refine and large-group path (k_refine.cu) --
@@ -160,7 +163,9 @@ struct RefineArgs {
   const uint32_t *isa;      // read only (updates are deferred)
   uint64_t isa_len;
   uint32_t N;
-  uint32_t *sa;
+  uint32_t *sa;             // written with indices local to each text
+  const uint32_t *seg_off;  // S + 1 ungapped offsets
+  uint32_t S;
   uint64_t *act_out;
   uint32_t *gstart_out, *gname_out, *ghead_out;
   uint64_t *upd;            // (new << 32) | i' for every changed name
@@ -180,9 +185,6 @@ cudaError_t launch_scatter_updates(const uint64_t *upd, uint32_t max_upd, uint32
                                    cudaStream_t stream);
 
 // ---- output (k_gather.cu) ------------------------------------------------
-// Batched: sa[r] -= gapped start of the text that rank r belongs to.
-cudaError_t launch_sa_to_local(uint32_t *sa, uint32_t N, const uint32_t *seg_off, uint32_t S,
-                               cudaStream_t stream);
 // isa_out[p] = isa[p + s] - off_s for text s (single text: a copy).
 cudaError_t launch_isa_to_local(const uint32_t *isa, uint32_t *isa_out, uint32_t N,
                                 const uint32_t *seg_off, uint32_t S, cudaStream_t stream);

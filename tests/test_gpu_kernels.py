@@ -137,3 +137,24 @@ def test_argument_errors(gb):
     lib = gb.load()
     assert lib.sa_build(None, 5, None, None) == 1
     assert lib.sa_build(None, (1 << 31) + 1, None, None) == 2
+
+
+def test_workload_4_batched_full_size(gb, orc):
+    """4096 uniform-DNA texts, log-uniform lengths in [1 KiB, 4 MiB] (about
+    2 GB): every text's SA passes the linear-time checker; 48 sampled texts
+    equal the oracle element by element."""
+    import torch
+    flat, off = gen.batch(4001, 4096, 1 << 10, 4 << 20)
+    sa = gb.sa_build_batched(torch.from_numpy(flat).cuda(), off)
+    torch.cuda.synchronize()
+    s = sa.cpu().numpy().view(np.uint32)
+    del sa
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(9)
+    sample = set(rng.integers(0, 4096, 48).tolist()) | {0, 4095}
+    for k in range(4096):
+        a, b = int(off[k]), int(off[k + 1])
+        if k in sample:
+            assert np.array_equal(s[a:b], orc.pd_sa(flat[a:b])[0]), k
+        else:
+            assert orc.check_sa(flat[a:b], s[a:b])[0] == 0, k
