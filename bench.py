@@ -386,13 +386,83 @@ def run_batched(args, emit=True):
     return out
 
 
+SERVE_SEED = 5001
+SERVE_RATES = (10, 30, 100, 300, 1000, 2000)
+SERVE_LO, SERVE_HI = 10 << 10, 64 << 20
+
+
+def run_serving(args):
+    """Workload 5: Poisson arrivals of SA builds at each offered rate, sizes
+    log-uniform in [10 KiB, 64 MiB], a fair coin choosing uniform DNA or
+    i.i.d. Zipf(1.1) bytes; continuous batching under a 100 GB device budget
+    (sa_server_*). Each request's text is a slice of one of two 64 MiB
+    buffers drawn from those two distributions (same statistics as a fresh
+    draw, without generating ~1.5 GB of text per rate)."""
+    import torch
+
+    import gen
+    import paper_1610_03007_gb300 as gbsa
+    from paper_1610_03007_gb300 import _build
+
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    _build.build()
+    gbsa.load()
+    count = args.requests or 200
+    pools = [torch.from_numpy(gen.text("dna", SERVE_SEED, SERVE_HI)).pin_memory(),
+             torch.from_numpy(gen.text("zipf", SERVE_SEED + 1, SERVE_HI)).pin_memory()]
+    views = [p.numpy() for p in pools]
+    rates = [float(r) for r in (args.rates.split(",") if args.rates else SERVE_RATES)]
+    out_rates = []
+    with gbsa.Server(budget_bytes=100 * 10**9, slots=args.slots) as srv:
+        for t in [srv.submit(views[k % 2][: 1 << 20]) for k in range(8)]:
+            srv.wait(t)  # warm-up: pool, module, streams
+        for lam in rates:
+            arr, sizes, kinds = gen.request_stream(SERVE_SEED + int(lam), count, lam,
+                                                   SERVE_LO, SERVE_HI)
+            tickets = []
+            t0 = time.perf_counter()
+            for k in range(count):
+                delay = t0 + float(arr[k]) - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                n = int(sizes[k])
+                start = (k * 2654435761) % (SERVE_HI - n + 1)
+                tickets.append(srv.submit(views[int(kinds[k])][start:start + n]))
+            infos = [srv.wait(t)[1] for t in tickets]
+            lat = np.array([i["latency_s"] for i in infos]) * 1e3
+            span = max(i["done_s"] for i in infos) - min(i["submit_s"] for i in infos)
+            total = float(np.sum(sizes))
+            st = srv.stats()
+            out_rates.append({"offered_rps": lam, "requests": count,
+                              "p50_ms": float(np.percentile(lat, 50)),
+                              "p99_ms": float(np.percentile(lat, 99)),
+                              "mean_ms": float(lat.mean()),
+                              "throughput_MBps": total / span / 1e6,
+                              "achieved_rps": count / span,
+                              "input_MB": total / 1e6,
+                              "peak_in_flight": st["peak_in_flight"],
+                              "peak_GB_in_use": st["peak_bytes_in_use"] / 1e9})
+    line = {"metric": "serving latency p50/p99 (ms) and input MB/s per offered rate",
+            "unit": "ms", "higher_is_better": False, "data": "synthetic",
+            "config": {"workload": "Poisson arrivals, sizes log-uniform [10 KiB, 64 MiB], "
+                                   "50/50 uniform DNA / Zipf(1.1) bytes, 100 GB budget",
+                       "slots": args.slots, "requests_per_rate": count, "seed": SERVE_SEED},
+            "rates": out_rates}
+    print(json.dumps(line), flush=True)
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="plain", choices=["plain", "batched"])
+    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving"])
+    ap.add_argument("--requests", type=int, default=0, help="requests per rate (serving)")
+    ap.add_argument("--rates", default="", help="comma-separated offered rates (serving)")
+    ap.add_argument("--slots", type=int, default=16, help="server slots (serving)")
     ap.add_argument("--batch-count", type=int, default=0, help="texts in the batched workload")
     ap.add_argument("--n", type=int, default=0, help="override the text length (testing)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
@@ -401,6 +471,8 @@ def main():
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_plain(args)
 

@@ -225,6 +225,69 @@ size_t sa_sort_workspace_bytes(uint64_t m);
 sa_status sa_build_noalloc(const uint8_t *text, uint64_t n, uint32_t *sa_out,
                            gbsa_stream_t stream);
 
+/* ---- Serving: continuous batching of SA builds --------------------------
+ * A server owns `slots` worker threads, each with its own CUDA stream.
+ * Requests (a HOST text and a HOST output buffer) queue in arrival order;
+ * the request at the head of the queue starts as soon as a slot is free
+ * and its device footprint (sa_request_footprint) fits in what is left of
+ * `budget_bytes`. Each running request keeps its text, SA and workspace
+ * (rank and ISA state) resident on the device for all its rounds and frees
+ * them when it completes, so requests that arrive while others run are
+ * admitted as slots and memory free up, and the builds in flight overlap
+ * on the device. Every request's result is exactly sa_build's. */
+typedef struct sa_server sa_server;
+
+typedef struct {
+  uint64_t budget_bytes;      /* device bytes in use at once; 0 = 100 GB        */
+  uint32_t slots;             /* builds in flight at once; 0 = 8, at most 64    */
+  int32_t device;             /* CUDA device of the workers (-1 = current)      */
+  /* Test hook: when non-zero no GPU work is done; a request "runs" for
+   * n * simulate_ns_per_byte nanoseconds and its SA buffer is untouched. */
+  uint32_t simulate;
+  double simulate_ns_per_byte;
+} sa_server_config;
+
+typedef struct {
+  sa_status status;           /* result of the build (SA_OK when done well)     */
+  uint64_t n;                 /* text length                                     */
+  uint32_t slot;              /* worker that ran it                              */
+  double submit_s, start_s, done_s; /* seconds since the server was created     */
+} sa_request_info;
+
+typedef struct {
+  uint64_t submitted, completed;
+  uint64_t bytes_in_use, peak_bytes_in_use;
+  uint32_t in_flight, peak_in_flight, queued;
+} sa_server_stats;
+
+/* Device bytes a request of n characters holds while it runs (text, SA and
+ * build workspace). */
+size_t sa_request_footprint(uint64_t n);
+
+/* Creates a server (cfg HOST, may be NULL for the defaults). */
+sa_status sa_server_create(const sa_server_config *cfg, sa_server **out);
+
+/* Queues a request. host_text (n bytes) and host_sa (n uint32) are HOST
+ * buffers owned by the caller that must stay valid until the request is
+ * done. *ticket identifies it. A request whose footprint exceeds the whole
+ * budget is refused with SA_ERR_OOM; n > SA_MAX_N with SA_ERR_TOO_LARGE. */
+sa_status sa_server_submit(sa_server *s, const uint8_t *host_text, uint64_t n,
+                           uint32_t *host_sa, uint64_t *ticket);
+
+/* 1 if the request is done (info filled), 0 if pending, -1 if the ticket
+ * is unknown. Non-blocking. */
+int sa_server_poll(sa_server *s, uint64_t ticket, sa_request_info *info);
+
+/* Blocks until the request is done; returns its status (info may be NULL). */
+sa_status sa_server_wait(sa_server *s, uint64_t ticket, sa_request_info *info);
+
+/* Current counters (HOST struct). */
+void sa_server_get_stats(sa_server *s, sa_server_stats *out);
+
+/* Finishes every queued and running request, stops the workers and frees
+ * the server. */
+void sa_server_destroy(sa_server *s);
+
 /* Human-readable name of a status code (static string). */
 const char *sa_status_string(sa_status s);
 

@@ -29,7 +29,8 @@ SA_MAX_ROUNDS = 64
 EXPORTED = ("sa_build", "sa_workspace_bytes", "sa_build_ex", "sa_build_batched",
             "sa_batched_workspace_bytes", "sa_build_batched_ex", "sa_build_host",
             "sa_sort_pairs", "sa_sort_workspace_bytes", "sa_status_string",
-            "sa_build_noalloc")
+            "sa_build_noalloc", "sa_request_footprint", "sa_server_create", "sa_server_submit",
+            "sa_server_poll", "sa_server_wait", "sa_server_get_stats", "sa_server_destroy")
 
 
 class SAError(RuntimeError):
@@ -76,6 +77,30 @@ class Stats(ctypes.Structure):
                             for k, name in enumerate(KERNEL_CLASSES)}}
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_uint64), ("slots", ctypes.c_uint32),
+                ("device", ctypes.c_int32), ("simulate", ctypes.c_uint32),
+                ("simulate_ns_per_byte", ctypes.c_double)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("n", ctypes.c_uint64), ("slot", ctypes.c_uint32),
+                ("submit_s", ctypes.c_double), ("start_s", ctypes.c_double),
+                ("done_s", ctypes.c_double)]
+
+    def to_dict(self) -> dict:
+        return {"status": self.status, "n": self.n, "slot": self.slot,
+                "submit_s": self.submit_s, "start_s": self.start_s, "done_s": self.done_s,
+                "latency_s": self.done_s - self.submit_s}
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("bytes_in_use", ctypes.c_uint64), ("peak_bytes_in_use", ctypes.c_uint64),
+                ("in_flight", ctypes.c_uint32), ("peak_in_flight", ctypes.c_uint32),
+                ("queued", ctypes.c_uint32)]
+
+
 _lib = None
 
 
@@ -108,6 +133,20 @@ def load(path: str | None = None):
     lib.sa_sort_pairs.argtypes = [vp, vp, u64, u32, u32, vp, sz, vp]
     lib.sa_sort_workspace_bytes.argtypes = [u64]
     lib.sa_sort_workspace_bytes.restype = sz
+    lib.sa_request_footprint.argtypes = [u64]
+    lib.sa_request_footprint.restype = sz
+    lib.sa_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+    lib.sa_server_create.restype = ctypes.c_int
+    lib.sa_server_submit.argtypes = [vp, vp, u64, vp, ctypes.POINTER(u64)]
+    lib.sa_server_submit.restype = ctypes.c_int
+    lib.sa_server_poll.argtypes = [vp, u64, ctypes.POINTER(RequestInfo)]
+    lib.sa_server_poll.restype = ctypes.c_int
+    lib.sa_server_wait.argtypes = [vp, u64, ctypes.POINTER(RequestInfo)]
+    lib.sa_server_wait.restype = ctypes.c_int
+    lib.sa_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+    lib.sa_server_get_stats.restype = None
+    lib.sa_server_destroy.argtypes = [vp]
+    lib.sa_server_destroy.restype = None
     lib.sa_status_string.argtypes = [ctypes.c_int]
     lib.sa_status_string.restype = ctypes.c_char_p
     for f in ("sa_build", "sa_build_ex", "sa_build_batched", "sa_build_batched_ex",
@@ -252,3 +291,67 @@ def sa_sort_pairs(keys, vals, begin_bit=0, end_bit=64, workspace=None, stream=No
 
 def status_string(s: int) -> str:
     return load().sa_status_string(s).decode()
+
+
+class Server:
+    """Continuous-batching SA server (sa_server_* in include/gbsa.h).
+
+    submit() takes a host numpy uint8 text and returns a ticket; the output
+    buffer (numpy uint32) is kept alive here until the request is waited on.
+    """
+
+    def __init__(self, budget_bytes: int = 0, slots: int = 0, device: int = -1,
+                 simulate_ns_per_byte: float = 0.0):
+        self._lib = load()
+        cfg = ServerConfig(budget_bytes, slots, device, 1 if simulate_ns_per_byte > 0 else 0,
+                           simulate_ns_per_byte)
+        h = ctypes.c_void_p()
+        _check(self._lib.sa_server_create(ctypes.byref(cfg), ctypes.byref(h)), "sa_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, text: np.ndarray, out: np.ndarray | None = None) -> int:
+        a = np.ascontiguousarray(text, dtype=np.uint8)
+        if out is None:
+            out = np.empty(a.size, dtype=np.uint32)
+        t = ctypes.c_uint64()
+        _check(self._lib.sa_server_submit(self._h, a.ctypes.data, a.size, out.ctypes.data,
+                                          ctypes.byref(t)), "sa_server_submit")
+        self._keep[t.value] = (a, out)
+        return t.value
+
+    def poll(self, ticket: int):
+        info = RequestInfo()
+        r = self._lib.sa_server_poll(self._h, ticket, ctypes.byref(info))
+        return info.to_dict() if r == 1 else None
+
+    def wait(self, ticket: int):
+        """(SA as numpy uint32, info dict); raises SAError if the build failed."""
+        info = RequestInfo()
+        st = self._lib.sa_server_wait(self._h, ticket, ctypes.byref(info))
+        _, out = self._keep.pop(ticket)
+        _check(st, "sa_server request")
+        return out, info.to_dict()
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        self._lib.sa_server_get_stats(self._h, ctypes.byref(s))
+        return {f: getattr(s, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            self._lib.sa_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

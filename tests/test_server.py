@@ -1,0 +1,90 @@
+"""Serving loop admission logic, on the host: the server in simulate mode
+does no GPU work (a request of n bytes "runs" for n * ns_per_byte), so
+these run without a GPU and check FIFO admission, the byte budget, the slot
+limit and that requests arriving during others' runs are admitted."""
+import time
+
+import numpy as np
+import pytest
+
+
+@pytest.fixture(scope="module")
+def gbsa():
+    from paper_1610_03007_gb300 import _build
+    _build.build()
+    import paper_1610_03007_gb300 as g
+    g.load()
+    return g
+
+
+def foot(g, n):
+    return int(g.load().sa_request_footprint(n))
+
+
+def run_all(srv, sizes):
+    texts = [np.zeros(n, np.uint8) for n in sizes]
+    tickets = [srv.submit(t) for t in texts]
+    infos = [srv.wait(t)[1] for t in tickets]
+    return infos
+
+
+def test_footprint_model(gbsa):
+    for n in (1, 1000, 1 << 20):
+        f = foot(gbsa, n)
+        assert f >= n + 4 * n + gbsa.workspace_bytes(n)
+
+
+def test_fifo_order_and_slot_limit(gbsa):
+    with gbsa.Server(budget_bytes=1 << 40, slots=3, simulate_ns_per_byte=20.0) as srv:
+        infos = run_all(srv, [100_000] * 12)
+        st = srv.stats()
+    starts = [i["start_s"] for i in infos]
+    assert starts == sorted(starts)
+    assert st["peak_in_flight"] == 3
+    assert st["completed"] == 12
+    for i in infos:
+        assert i["submit_s"] <= i["start_s"] <= i["done_s"]
+
+
+def test_budget_limits_concurrency(gbsa):
+    n = 200_000
+    budget = 2 * foot(gbsa, n) + 1000  # room for two requests at a time
+    with gbsa.Server(budget_bytes=budget, slots=8, simulate_ns_per_byte=20.0) as srv:
+        run_all(srv, [n] * 10)
+        st = srv.stats()
+    assert st["peak_in_flight"] == 2
+    assert st["peak_bytes_in_use"] <= budget
+    assert st["bytes_in_use"] == 0
+
+
+def test_head_of_line_waits_for_memory(gbsa):
+    small, big = 50_000, 400_000
+    budget = foot(gbsa, big) + foot(gbsa, small)
+    with gbsa.Server(budget_bytes=budget, slots=8, simulate_ns_per_byte=20.0) as srv:
+        infos = run_all(srv, [small, small, big, small])
+    # the big request waits until it fits; the small one behind it does not
+    # overtake it (strict FIFO)
+    assert infos[3]["start_s"] >= infos[2]["start_s"]
+    assert infos[2]["start_s"] >= min(infos[0]["done_s"], infos[1]["done_s"])
+
+
+def test_arrivals_during_runs_are_admitted(gbsa):
+    with gbsa.Server(budget_bytes=1 << 40, slots=4, simulate_ns_per_byte=100.0) as srv:
+        first = srv.submit(np.zeros(2_000_000, np.uint8))  # runs ~0.2 s
+        time.sleep(0.02)
+        later = srv.submit(np.zeros(1000, np.uint8))
+        _, a = srv.wait(first)
+        _, b = srv.wait(later)
+    # continuous batching: the later request started and finished while the
+    # first was still running
+    assert b["start_s"] < a["done_s"]
+    assert b["done_s"] < a["done_s"]
+
+
+def test_refusals(gbsa):
+    with gbsa.Server(budget_bytes=foot(gbsa, 1000), slots=2, simulate_ns_per_byte=1.0) as srv:
+        with pytest.raises(gbsa.SAError) as e:
+            srv.submit(np.zeros(100_000, np.uint8))
+        assert e.value.status == 3  # SA_ERR_OOM: footprint above the whole budget
+        t = srv.submit(np.zeros(1000, np.uint8))
+        srv.wait(t)
