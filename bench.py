@@ -192,9 +192,15 @@ def run_plain(args):
     text = torch.from_numpy(t_host).to(dev)
     ws = torch.empty(gbsa.workspace_bytes(n), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
+    # Tile parameters picked by the project's autotuner on this input
+    # (outside the timed region).
+    from paper_1610_03007_gb300 import autotune
+    tuned = autotune.tune(text, ws, reps=2) if not args.no_tune else {
+        "params": dict(autotune.DEFAULTS), "ms": None, "tried": {}}
+    params = tuned["params"]
 
     def step(profile=False):
-        return gbsa.sa_build_ex(text, workspace=ws, profile=profile)
+        return gbsa.sa_build_ex(text, workspace=ws, profile=profile, **params)
 
     for _ in range(max(args.warmup, 0)):
         step()
@@ -268,6 +274,8 @@ def run_plain(args):
         "config": {"workload": "single text n=2^28 bytes: 1 MiB Zipf(1.1) base over bytes 1..255 "
                                "x256 copies, 0.1% substitutions per copy; uint32 SA",
                    "n": n, "seed": PLAIN_SEED, "rounds": stats["rounds"],
+                   "tuned": {"params": params,
+                             "candidates_ms": {k: round(v, 3) for k, v in tuned["tried"].items()}},
                    "l2": "inputs larger than L2 (256 MiB text, ~10 GiB working set); no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm,
@@ -322,10 +330,21 @@ def run_batched(args, emit=True):
                      dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(profile=False):
+    def step(profile=False, items=0):
         return gbsa.sa_build_batched(texts, off, sa_out=sa, workspace=ws, stats=True,
-                                     profile=profile)
+                                     profile=profile, sort_items=items or best_items)
 
+    # Radix tile picked by measurement (the batched build is sort-bound).
+    best_items, cand = 16, {}
+    for items in (16, 12, 8):
+        step(items=items)
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        step(items=items)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        cand[items] = c0.elapsed_time(c1)
+    best_items = min(cand, key=cand.get)
     for _ in range(max(args.warmup, 1)):
         step()
     torch.cuda.synchronize()
@@ -371,7 +390,9 @@ def run_batched(args, emit=True):
            "unit": "MB/s", "ms_per_step": ms, "steps": steps,
            "config": {"workload": f"{count} uniform-DNA texts, lengths log-uniform in "
                                   f"[1 KiB, 4 MiB], one SA per text", "total_bytes": N,
-                      "seed": BATCH_SEED, "rounds": st["rounds"]},
+                      "seed": BATCH_SEED, "rounds": st["rounds"],
+                      "tuned": {"sort_items": best_items,
+                                "candidates_ms": {str(k): round(v, 2) for k, v in cand.items()}}},
            "per_text_plain": {"value": N / (plain_ms * 1e-3) / 1e6, "unit": "MB/s",
                               "ms": plain_ms, "calls": count},
            "speedup_vs_per_text": plain_ms / ms,
@@ -466,6 +487,7 @@ def main():
     ap.add_argument("--batch-count", type=int, default=0, help="texts in the batched workload")
     ap.add_argument("--n", type=int, default=0, help="override the text length (testing)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    ap.add_argument("--no-tune", action="store_true", help="use the default tile parameters")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

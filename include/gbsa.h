@@ -90,6 +90,9 @@ typedef struct {
    * 3 = 256 x 4096, 4 = 256 x 1024. Groups of up to half a tile are refined
    * inside one tile; larger ones take the global radix sort. */
   uint32_t refine_shape;
+  /* Keys per thread of the one-sweep radix pass (tile = 256 x this):
+   * 8, 12 or 16; 0 = automatic (16). */
+  uint32_t sort_items;
   /* When 1, CUDA events are recorded on `stream` around every kernel launch
    * and the per-kernel-class times, launch counts and algorithmic bytes are
    * returned in sa_stats (adds a few microseconds per launch). */

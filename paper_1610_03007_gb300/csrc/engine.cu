@@ -91,7 +91,7 @@ Layout make_layout(uint64_t N, uint32_t S) {
   L.lold = take((size_t)L.max_large * 4);
   L.max_tiles = (uint32_t)((Nm + REFINE_MIN_NOMINAL - 1) / REFINE_MIN_NOMINAL);
   L.tfirst = take(((size_t)L.max_tiles + 1) * 4);
-  const uint64_t ts = std::max<uint64_t>(1, (N + SORT_TILE - 1) / SORT_TILE);
+  const uint64_t ts = std::max<uint64_t>(1, (N + SORT_TILE_MIN - 1) / SORT_TILE_MIN);
   L.st_sort_bytes = ts * RADIX * 8;
   L.st_sort = take(L.st_sort_bytes);
   const uint64_t tr = std::max<uint64_t>(1, (N + RENAME_TILE - 1) / RENAME_TILE);
@@ -209,6 +209,7 @@ struct Build {
   uint32_t launches = 0;
   uint32_t naming = NAMES_RETAIN;
   uint32_t shape = 0, nominal = 512;  // refine tile shape and window
+  uint32_t sort_items = SORT_ITEMS_DEFAULT;  // keys per thread of the radix pass
   // per-kernel profiling (events on the build's stream)
   struct Rec {
     int cls, pass;
@@ -356,6 +357,7 @@ struct Build {
       pa.ctrl = ctrl;
       pa.spin_limit = spin;
       pa.inject = inject_pending ? 1u : 0u;
+      pa.items = sort_items;
       s = launch(SA_K_ONESWEEP, (int)p, 24ull * m, [&] { return launch_onesweep(pa, st); });
       if (s != SA_OK) return s;
     }
@@ -472,6 +474,8 @@ struct Build {
                 ? opt.refine_shape - 1
                 : 0;
     nominal = REFINE_SHAPE[shape].cap / 2;
+    if (opt.sort_items == 8 || opt.sort_items == 12 || opt.sort_items == 16)
+      sort_items = opt.sort_items;
     // Clear what must start at zero; the ISA starts all-ones so every end
     // slot reads as the sentinel.
     CK(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
@@ -811,7 +815,7 @@ GBSA_API sa_status sa_build_host(const uint8_t *host_text, uint64_t n, uint32_t 
 
 GBSA_API size_t sa_sort_workspace_bytes(uint64_t m) {
   const uint64_t mm = m ? m : 1;
-  const uint64_t tiles = (mm + SORT_TILE - 1) / SORT_TILE;
+  const uint64_t tiles = (mm + SORT_TILE_MIN - 1) / SORT_TILE_MIN;
   return align256(sizeof(Ctrl)) + align256(sizeof(SortPlan)) + 2 * align256(MAX_PASSES * RADIX * 4) +
          align256(mm * 8) + align256(mm * 4) + align256(tiles * RADIX * 8);
 }
@@ -838,7 +842,7 @@ GBSA_API sa_status sa_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t m, uin
     }
     ws = (uint8_t *)own.p;
   }
-  const uint64_t tiles = (m + SORT_TILE - 1) / SORT_TILE;
+  const uint64_t tiles = (m + SORT_TILE_MIN - 1) / SORT_TILE_MIN;
   size_t o = 0;
   auto take = [&](size_t bytes) { uint8_t *r = ws + o; o += align256(bytes); return r; };
   Build B;

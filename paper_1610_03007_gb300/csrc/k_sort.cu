@@ -10,7 +10,7 @@
 //   2. k_sort_plan (one block): exclusive digit offsets per pass; a digit
 //      position whose keys all share one value is skipped; the source and
 //      destination buffers of the remaining passes ping-pong A <-> B.
-//   3. k_onesweep per kept pass: each tile of 4096 items ranks its items by
+//   3. k_onesweep per kept pass: each tile of 256 x 8..16 items ranks its items by
 //      digit (warp ballots give the peers of equal digit, so the local order
 //      is stable), publishes its per-digit counts, finds its per-digit
 //      global offsets by decoupled look-back over the preceding tiles, stages
@@ -127,13 +127,12 @@ cudaError_t launch_sort_plan(const uint32_t *hist, uint32_t *digit_base, const D
 // ---- 3. one-sweep pass -----------------------------------------------------
 
 constexpr int OS_BLOCK = 256;  // == RADIX: thread d owns digit d in the look-back
-constexpr int OS_ITEMS = 16;
-constexpr int OS_TILE = OS_BLOCK * OS_ITEMS;
 constexpr int OS_WARPS = OS_BLOCK / 32;
-static_assert(OS_TILE == SORT_TILE, "tile size mismatch");
 static_assert(OS_BLOCK == RADIX, "one thread per digit");
 
+template <int OS_ITEMS>
 struct OsSmem {
+  static constexpr int OS_TILE = OS_BLOCK * OS_ITEMS;
   uint64_t keys[OS_TILE];           // tile in input order, then in digit order
   uint32_t vals[OS_TILE];
   uint32_t match[OS_WARPS][RADIX];  // per-warp peer masks (zero between uses)
@@ -146,11 +145,15 @@ struct OsSmem {
   uint64_t bar;                     // completion of the tile's bulk copies
 };
 
-// Three blocks per SM: registers capped at 85 per thread, ~59 KB of
-// shared memory per block.
-__global__ void __launch_bounds__(OS_BLOCK, 3) k_onesweep(PassArgs a) {
+// OS_ITEMS keys per thread (8, 12 or 16; chosen per build): 16 fits three
+// blocks per SM (~62 KB of shared memory each), 12 four, 8 five; registers
+// are capped to match.
+template <int OS_ITEMS>
+__global__ void __launch_bounds__(OS_BLOCK, OS_ITEMS >= 16 ? 3 : (OS_ITEMS >= 12 ? 4 : 5))
+    k_onesweep(PassArgs a) {
+  constexpr int OS_TILE = OS_BLOCK * OS_ITEMS;
   extern __shared__ __align__(128) uint8_t smem_raw[];
-  OsSmem &S = *reinterpret_cast<OsSmem *>(smem_raw);
+  OsSmem<OS_ITEMS> &S = *reinterpret_cast<OsSmem<OS_ITEMS> *>(smem_raw);
   if (!a.plan->active[a.p]) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
@@ -283,21 +286,33 @@ __global__ void __launch_bounds__(OS_BLOCK, 3) k_onesweep(PassArgs a) {
   }
 }
 
-cudaError_t launch_onesweep(const PassArgs &a, cudaStream_t stream) {
-  if (a.m == 0) return cudaSuccess;
+template <int OS_ITEMS>
+cudaError_t launch_onesweep_t(const PassArgs &a, cudaStream_t stream) {
   static bool configured = false;  // per process; the attribute is per function
-  const int smem = (int)sizeof(OsSmem);
+  const int smem = (int)sizeof(OsSmem<OS_ITEMS>);
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(k_onesweep<OS_ITEMS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_onesweep, cudaFuncAttributePreferredSharedMemoryCarveout,
+    e = cudaFuncSetAttribute(k_onesweep<OS_ITEMS>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  const uint64_t tiles = ((uint64_t)a.m + OS_TILE - 1) / OS_TILE;
-  k_onesweep<<<(unsigned)tiles, OS_BLOCK, smem, stream>>>(a);
+  const uint64_t tile = (uint64_t)OS_BLOCK * OS_ITEMS;
+  const uint64_t tiles = ((uint64_t)a.m + tile - 1) / tile;
+  k_onesweep<OS_ITEMS><<<(unsigned)tiles, OS_BLOCK, smem, stream>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_onesweep(const PassArgs &a, cudaStream_t stream) {
+  if (a.m == 0) return cudaSuccess;
+  switch (a.items) {
+    case 8: return launch_onesweep_t<8>(a, stream);
+    case 12: return launch_onesweep_t<12>(a, stream);
+    case 16: return launch_onesweep_t<16>(a, stream);
+  }
+  return cudaErrorInvalidValue;
 }
 
 // ---- copy-back for the standalone sort ------------------------------------

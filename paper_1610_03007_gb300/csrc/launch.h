@@ -53,8 +53,10 @@ struct PassArgs {
   Ctrl *ctrl;
   uint32_t spin_limit;
   uint32_t inject;
+  uint32_t items;    // keys per thread: 8, 12 or 16 (tile = 256 * items)
 };
-constexpr int SORT_TILE = 256 * 16;
+constexpr int SORT_TILE_MIN = 256 * 8;  // smallest tile (sizes the status array)
+constexpr uint32_t SORT_ITEMS_DEFAULT = 16;
 cudaError_t launch_onesweep(const PassArgs &a, cudaStream_t stream);
 // Copies the plan's final buffer back to (ka, va) when it is buffer B.
 cudaError_t launch_copy_back(const SortPlan *plan, uint64_t *ka, uint32_t *va, uint32_t m,

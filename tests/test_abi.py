@@ -68,4 +68,4 @@ def test_workspace_model(lib):
     # and head ranks x2 plus parent names (14) and look-back status.
     for n in (1 << 20, 1 << 28, 1 << 31):
         b = lib.sa_workspace_bytes(n)
-        assert 66 * n < b < 67 * n
+        assert 66 * n < b < 68 * n

@@ -212,3 +212,16 @@ def test_every_refine_tile_shape(gb, orc, shape, recipe):
     osa, oisa, _, _ = orc.pd_sa(t)
     assert np.array_equal(sa.cpu().numpy().view(np.uint32), osa)
     assert np.array_equal(isa.cpu().numpy().view(np.uint32), oisa)
+
+
+@pytest.mark.parametrize("items", [8, 12, 16])
+def test_every_radix_tile_size(gb, orc, items):
+    """Each radix-pass tile size gives the oracle's SA (round 0 sorts all n
+    keys; repeats force later large-group sorts too)."""
+    for recipe, n in (("dna", 200003), ("zipf_repeats", 1 << 20), ("bytes", 77777)):
+        t = gen.text(recipe, 500 + items, n)
+        sa, _, _, _ = gb.sa_build_ex(dev_text(t), sort_items=items)
+        assert np.array_equal(sa.cpu().numpy().view(np.uint32), orc.pd_sa(t)[0])
+    t = b"a" * 300000  # one large group every round: the global sort path
+    sa, _, _, _ = gb.sa_build_ex(dev_text(t), sort_items=items)
+    assert list(sa.cpu().numpy()) == list(range(299999, -1, -1))
