@@ -55,6 +55,8 @@ class Oracle:
         lib.oracle_pd_sa.restype = i64
         lib.oracle_check_sa.argtypes = [p, i64, p, p]
         lib.oracle_check_sa.restype = ctypes.c_int
+        lib.oracle_check_permutation.argtypes = [p, i64, p]
+        lib.oracle_check_permutation.restype = ctypes.c_int
         lib.oracle_check_adjacent.argtypes = [p, i64, p, p, i64]
         lib.oracle_check_adjacent.restype = i64
         lib.oracle_suffix_rank.argtypes = [p, i64, i64]
@@ -108,6 +110,12 @@ class Oracle:
         code = self._lib.oracle_check_sa(T.ctypes.data, T.size, s.ctypes.data,
                                          ctypes.byref(bad))
         return int(code), int(bad.value)
+
+    def check_permutation(self, sa) -> int:
+        """0 if SA is a permutation of [0, len(SA)), else 1."""
+        s = np.ascontiguousarray(sa, dtype=np.uint32)
+        bad = ctypes.c_int64(-1)
+        return int(self._lib.oracle_check_permutation(s.ctypes.data, s.size, ctypes.byref(bad)))
 
     def check_adjacent(self, t, sa, idx) -> int:
         T = self._text(t)

@@ -238,6 +238,22 @@ int oracle_check_sa(const uint8_t *T, int64_t n, const uint32_t *sa, int64_t *ba
   return 0;
 }
 
+int oracle_check_permutation(const uint32_t *sa, int64_t n, int64_t *bad) {
+  if (n <= 0) return 0;
+  uint64_t *seen = (uint64_t *)calloc((size_t)(n + 63) / 64, sizeof(uint64_t));
+  for (int64_t j = 0; j < n; ++j) {
+    const uint64_t v = sa[j];
+    if ((int64_t)v >= n || (seen[v >> 6] >> (v & 63)) & 1u) {
+      if (bad) *bad = j;
+      free(seen);
+      return 1;
+    }
+    seen[v >> 6] |= 1ull << (v & 63);
+  }
+  free(seen);
+  return 0;
+}
+
 int64_t oracle_check_adjacent(const uint8_t *T, int64_t n, const uint32_t *sa,
                               const int64_t *idx, int64_t count) {
   int64_t bad = 0;

@@ -66,6 +66,11 @@ int64_t oracle_pd_sa(const uint8_t *T, int64_t n, int64_t h0, uint32_t *sa,
  * offending index. Linear time; any n. */
 int oracle_check_sa(const uint8_t *T, int64_t n, const uint32_t *sa, int64_t *bad);
 
+/* SA is a permutation of [0, n): every entry below n and none repeated
+ * (a bitmap of n bits). Returns 0 if so, else 1 + the first bad index in
+ * *bad. Linear time, n / 8 bytes of memory. */
+int oracle_check_permutation(const uint32_t *sa, int64_t n, int64_t *bad);
+
 /* Direct lexicographic check of sampled adjacent pairs:
  * T[SA[j],n) < T[SA[j+1],n) for j in idx[0..count). Returns the number of
  * violations. */

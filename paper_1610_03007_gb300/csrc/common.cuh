@@ -205,24 +205,26 @@ __device__ __forceinline__ bool look_back(const uint64_t *status, uint32_t strid
   return true;
 }
 
-// Look-back with an associative operator reading a window of 4
-// predecessors per round trip (see look_back_sum4).
-template <class Op>
-__device__ __forceinline__ bool look_back4(const uint64_t *status, uint32_t stride, uint32_t slot,
-                                           uint32_t tile, uint32_t epoch, Op op, uint32_t &carry,
-                                           Ctrl *ctrl, uint32_t spin_limit) {
+// Look-back with an associative operator that reads a window of W
+// predecessors per round trip (W independent loads): a chain of tiles that
+// have published only their aggregates costs 1/W of the dependent
+// latencies. Bounded like status_wait.
+template <int W, class Op>
+__device__ __forceinline__ bool look_back_w(const uint64_t *status, uint32_t stride, uint32_t slot,
+                                            uint32_t tile, uint32_t epoch, Op op, uint32_t &carry,
+                                            Ctrl *ctrl, uint32_t spin_limit) {
   int64_t p = (int64_t)tile - 1;
   uint32_t spins = 0, ns = 32;
   const uint32_t ep = epoch & EPOCH_MASK;
   while (p >= 0) {
-    uint64_t w[4];
+    uint64_t w[W];
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < W; ++k)
       w[k] = (p - k >= 0) ? status_load(status + (size_t)(p - k) * stride + slot) : 0ull;
     int used = 0;
     bool done = false, blocked = false;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < W; ++k) {
       if (!done && !blocked && p - k >= 0) {
         const uint32_t tag = (uint32_t)(w[k] >> 32);
         if ((tag >> 2) != ep || (tag & 3u) == 0u) {
@@ -247,6 +249,13 @@ __device__ __forceinline__ bool look_back4(const uint64_t *status, uint32_t stri
     }
   }
   return true;
+}
+
+template <class Op>
+__device__ __forceinline__ bool look_back4(const uint64_t *status, uint32_t stride, uint32_t slot,
+                                           uint32_t tile, uint32_t epoch, Op op, uint32_t &carry,
+                                           Ctrl *ctrl, uint32_t spin_limit) {
+  return look_back_w<4>(status, stride, slot, tile, epoch, op, carry, ctrl, spin_limit);
 }
 
 // Sum look-back that reads a window of 4 predecessors per round trip

@@ -129,6 +129,12 @@ cudaError_t launch_sort_plan(const uint32_t *hist, uint32_t *digit_base, const D
 constexpr int OS_BLOCK = 256;  // == RADIX: thread d owns digit d in the look-back
 constexpr int OS_WARPS = OS_BLOCK / 32;
 static_assert(OS_BLOCK == RADIX, "one thread per digit");
+#ifndef GBSA_LB_WINDOW
+#define GBSA_LB_WINDOW 4
+#endif
+// Predecessors read per look-back round trip (4 independent 8-byte loads
+// per digit thread).
+constexpr int LB_WINDOW = GBSA_LB_WINDOW;
 
 template <int OS_ITEMS>
 struct OsSmem {
@@ -240,7 +246,7 @@ __global__ void __launch_bounds__(OS_BLOCK, OS_ITEMS >= 16 ? 3 : (OS_ITEMS >= 12
   } else {
     status_store(st, status_word(a.epoch, ST_AGG, mine));
     uint32_t excl = 0;
-    if (look_back_sum4(a.status, RADIX, d, tile, a.epoch, excl, a.ctrl, a.spin_limit)) {
+    if (look_back_w<LB_WINDOW>(a.status, RADIX, d, tile, a.epoch, OpAdd(), excl, a.ctrl, a.spin_limit)) {
       status_store(st, status_word(a.epoch, ST_INC, excl + mine));
       S.goff[d] = a.digit_base[d] + excl - start;
     } else {

@@ -225,3 +225,27 @@ def test_every_radix_tile_size(gb, orc, items):
     t = b"a" * 300000  # one large group every round: the global sort path
     sa, _, _, _ = gb.sa_build_ex(dev_text(t), sort_items=items)
     assert list(sa.cpu().numpy()) == list(range(299999, -1, -1))
+
+
+def test_workload_3_full_size_properties(gb, orc):
+    """n = 2^31 order-3 Markov DNA with 5% copied segments (the largest
+    input, about 154 GB on the device): SA is a permutation (bitmap), 200000
+    sampled adjacent suffixes compare strictly increasing, and the oracle's
+    one-by-one rank of two sampled suffixes equals their SA positions."""
+    import torch
+    n = 1 << 31
+    t = gen.text("markov", 3001, n)
+    d = dev_text(t)
+    ws = torch.empty(gb.workspace_bytes(n), dtype=torch.uint8, device="cuda")
+    sa, _, stats, _ = gb.sa_build_ex(d, workspace=ws)
+    torch.cuda.synchronize()
+    del ws
+    s = sa.cpu().numpy().view(np.uint32)
+    del sa, d
+    torch.cuda.empty_cache()
+    assert stats["rounds"] > 3
+    assert orc.check_permutation(s) == 0
+    rng = np.random.default_rng(31)
+    assert orc.check_adjacent(t, s, rng.integers(0, n - 1, 200000)) == 0
+    for j in rng.integers(0, n, 2):
+        assert orc.suffix_rank(t, int(s[j])) == int(j)

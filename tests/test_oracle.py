@@ -130,6 +130,11 @@ def pin_checker(o):
         s[100], s[400] = s[400], s[100]
         if o.check_sa(t, s)[0] == 0:
             bad.append("accepts a far swap")
+    if o.check_permutation(np.array(py_sa(b"banana"), dtype=np.uint32)) != 0:
+        bad.append("permutation check rejects a permutation")
+    for wrong in ([0, 1, 1], [0, 3, 1], [2, 0]):
+        if o.check_permutation(np.array(wrong, dtype=np.uint32)) == 0:
+            bad.append(f"permutation check accepts {wrong}")
     t = b"aaaa"
     if o.check_sa(t, np.array([0, 1, 2, 3], dtype=np.uint32))[0] == 0:
         bad.append("accepts a^4 in text order")
