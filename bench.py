@@ -105,22 +105,37 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def ncu_traffic(kernel_file: str, kernel: str):
-    """DRAM bytes per item from the committed ncu summary of `kernel`, if the
-    kernel source is unchanged since it was captured (else None)."""
-    src = os.path.join(ROOT, "paper_1610_03007_gb300", "csrc", kernel_file)
-    with open(src, "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+KERNEL_SOURCES = {"onesweep": "k_sort.cu", "refine": "k_refine.cu", "rename": "k_rename.cu",
+                  "scatter": "k_refine.cu", "apply": "k_refine.cu", "pack": "k_pack.cu"}
+
+
+def kernel_source_hash(kernel: str):
+    """First 16 hex digits of the SHA-256 over the kernel's source file and
+    the two headers every kernel includes."""
+    csrc = os.path.join(ROOT, "paper_1610_03007_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in (KERNEL_SOURCES[kernel], "common.cuh", "launch.h"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """Measured DRAM bytes per algorithmic byte of `kernel`, from its committed
+    ncu summary, if the kernel's sources are unchanged since it was captured
+    (else None)."""
+    if kernel not in KERNEL_SOURCES:
+        return None
     path = os.path.join(ROOT, "profiles", f"ncu_{kernel}.md")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         text = f.read()
     m_sha = re.search(r"source_sha256_16:\s*([0-9a-f]{16})", text)
-    m_b = re.search(r"dram_bytes_per_item:\s*([0-9.]+)", text)
-    if not (m_sha and m_b) or m_sha.group(1) != sha:
+    m_r = re.search(r"dram_bytes_per_algorithmic_byte:\s*([0-9.]+)", text)
+    if not (m_sha and m_r) or m_sha.group(1) != kernel_source_hash(kernel):
         return None
-    return float(m_b.group(1))
+    return float(m_r.group(1))
 
 
 def cpu_baseline():
@@ -259,11 +274,9 @@ def run_plain(args):
     dom = max(kern.items(), key=lambda kv: kv[1]["ms"])
     dname, d = dom
     achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
-    traffic_per_item = ncu_traffic("k_sort.cu", "onesweep") if dname == "onesweep" else None
+    ratio = ncu_traffic(dname)
     avg_bytes = d["bytes"] / max(d["launches"], 1)
-    traffic = None
-    if traffic_per_item is not None:
-        traffic = traffic_per_item * (avg_bytes / 24.0)
+    traffic = ratio * avg_bytes if ratio is not None else None
     value = n * world / (ms * 1e-3) / 1e6
     path_gbs = bytes_model / args.steps / (ms * 1e-3) / 1e9
     line = {
@@ -287,6 +300,7 @@ def run_plain(args):
                           "frac_measured": path_gbs / hbm, "frac_8tbs": path_gbs / 8000.0},
         "kernels": {k: {"ms_per_step": v["ms"] / args.steps,
                         "launches_per_step": v["launches"] / args.steps,
+                        "bytes_per_step": v["bytes"] / args.steps,
                         "gbs": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
                     for k, v in kern.items() if v["launches"]},
         "e2e": {"value": n / (e2e_ms * 1e-3) / 1e6, "unit": "MB/s", "h2d_bytes_per_step": n,
@@ -397,7 +411,8 @@ def run_batched(args, emit=True):
                               "ms": plain_ms, "calls": count},
            "speedup_vs_per_text": plain_ms / ms,
            "roofline": {"bound": "hbm", "kernel": dom[0], "achieved": achieved, "peak": hbm,
-                        "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind},
+                        "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
+                        "traffic": None},
            "kernels": {k: {"ms_per_step": v["ms"] / steps,
                            "gbs": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
                        for k, v in kern.items() if v["launches"]},

@@ -113,7 +113,8 @@ enum {
   SA_K_SCATTER = 9,   /* deferred ISA updates                */
   SA_K_CLASSIFY = 10, /* group classification, tile map      */
   SA_K_APPLY = 11,    /* ISA entries of renamed survivors    */
-  SA_K_CLASSES = 12
+  SA_K_BUCKET = 12,   /* position bucketing of ISA writes    */
+  SA_K_CLASSES = 13
 };
 
 /* Per-build statistics (HOST struct filled by the _ex calls). */
@@ -145,7 +146,7 @@ typedef struct {
  * text   : DEVICE, n bytes, read only.
  * n      : length, 0 <= n <= SA_MAX_N.
  * sa_out : DEVICE, n uint32, written with SA.
- * The workspace (about 67 bytes per character) is allocated from a
+ * The workspace (about 67 bytes per character plus 1 MiB) is allocated from a
  * library-private stream-ordered pool on `stream` and returned to it.
  * n = 0 writes nothing; n = 1 writes sa_out[0] = 0. */
 sa_status sa_build(const uint8_t *text, uint64_t n, uint32_t *sa_out,

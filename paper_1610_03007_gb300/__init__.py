@@ -48,7 +48,7 @@ class Options(ctypes.Structure):
 
 
 KERNEL_CLASSES = ("byte_hist", "pack", "digit_hist", "plan", "onesweep", "rename", "gather",
-                  "output", "refine", "scatter", "classify", "apply")
+                  "output", "refine", "scatter", "classify", "apply", "bucket")
 
 
 class Stats(ctypes.Structure):
@@ -61,9 +61,9 @@ class Stats(ctypes.Structure):
                 ("groups", ctypes.c_uint64 * SA_MAX_ROUNDS),
                 ("bytes_model", ctypes.c_uint64),
                 ("launches", ctypes.c_uint32),
-                ("kernel_ms", ctypes.c_double * 12),
-                ("kernel_launches", ctypes.c_uint64 * 12),
-                ("kernel_bytes", ctypes.c_uint64 * 12)]
+                ("kernel_ms", ctypes.c_double * len(KERNEL_CLASSES)),
+                ("kernel_launches", ctypes.c_uint64 * len(KERNEL_CLASSES)),
+                ("kernel_bytes", ctypes.c_uint64 * len(KERNEL_CLASSES))]
 
     def to_dict(self) -> dict:
         r = self.rounds

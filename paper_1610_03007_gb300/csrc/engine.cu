@@ -40,13 +40,15 @@ namespace gbsa {
 namespace {
 
 constexpr uint32_t DEFAULT_SPIN_LIMIT = 1u << 20;  // ~1 s with the 1 us back-off cap
+// ISA writes are bucketed by position when this many may be pending.
+constexpr uint32_t BUCKET_MIN = 1u << 22;
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
   size_t ctrl, plan, hist, dbase, bytehist, code, segoff;
   size_t ka, kb, va, vb, act0, act1, upd, isa, gs0, gs1, gn0, gn1, gh0, gh1, gold;
-  size_t lg, loff, lbase, lold, tfirst;
+  size_t lg, loff, lbase, lold, tfirst, bcount;
   size_t st_sort, st_ren, total;
   size_t st_sort_bytes, st_ren_bytes;
   uint32_t max_groups, max_large, max_tiles;
@@ -89,6 +91,7 @@ Layout make_layout(uint64_t N, uint32_t S) {
   L.loff = take((size_t)L.max_large * 4);
   L.lbase = take((size_t)L.max_large * 4);
   L.lold = take((size_t)L.max_large * 4);
+  L.bcount = take((size_t)BUCKET_BLOCKS_MAX * RADIX * 4);
   L.max_tiles = (uint32_t)((Nm + REFINE_MIN_NOMINAL - 1) / REFINE_MIN_NOMINAL);
   L.tfirst = take(((size_t)L.max_tiles + 1) * 4);
   const uint64_t ts = std::max<uint64_t>(1, (N + SORT_TILE_MIN - 1) / SORT_TILE_MIN);
@@ -201,6 +204,7 @@ struct Build {
   uint32_t *gstart[2] = {nullptr, nullptr}, *gname[2] = {nullptr, nullptr};
   uint32_t *ghead[2] = {nullptr, nullptr}, *gold = nullptr;
   uint32_t *lg = nullptr, *loff = nullptr, *lbase = nullptr, *lold = nullptr, *tfirst = nullptr;
+  uint32_t *bcount = nullptr;  // position-bucketing counts (BUCKET_BLOCKS_MAX x 256)
   // launch bookkeeping
   uint32_t epoch = 0, slot = 0;
   uint32_t spin = DEFAULT_SPIN_LIMIT;
@@ -217,6 +221,11 @@ struct Build {
     cudaEvent_t a, b;
   };
   bool prof = false;
+  // Launches whose byte counts wait for the round's control block.
+  static constexpr uint64_t PENDING = ~0ull;
+  struct Pending {
+    uint32_t scatter = 0, apply = 0, bucket_upd = 0, bucket_surv = 0;
+  } pend;
   std::vector<cudaEvent_t> evpool;
   size_t evused = 0;
   std::vector<Rec> recs;
@@ -257,6 +266,7 @@ struct Build {
     loff = at<uint32_t>(L.loff);
     lbase = at<uint32_t>(L.lbase);
     lold = at<uint32_t>(L.lold);
+    bcount = at<uint32_t>(L.bcount);
     tfirst = at<uint32_t>(L.tfirst);
     st_sort = at<uint64_t>(L.st_sort);
     st_ren = at<uint64_t>(L.st_ren);
@@ -412,7 +422,7 @@ struct Build {
   }
 
   // Large groups and the refine tile map of the list just written.
-  sa_status classify(int out, uint64_t cap_groups) {
+  sa_status classify(int out, uint64_t cap_groups, uint32_t apply_bound) {
     ClassifyArgs ca{};
     ca.gstart = gstart[out];
     ca.gname = gname[out];
@@ -431,10 +441,76 @@ struct Build {
     sa_status s = launch(SA_K_CLASSIFY, 0, 16 * cap_groups,
                          [&] { return launch_classify(ca, sm_count(), st); });
     if (s != SA_OK) return s;
-    // ISA entries of the rename's survivors whose name changed.
-    return launch(SA_K_APPLY, 0, 0, [&] {
-      return launch_apply_names(act[out], gname[out], gold, isa, N + S + 1, ctrl, sm_count(), st);
+    // ISA entries of the rename's survivors whose name changed, bucketed by
+    // position first when there can be many.
+    const uint64_t *src = act[out];
+    const uint32_t *lo = &ctrl->rc.m_s;
+    if (apply_bound >= BUCKET_MIN) {
+      s = bucket(src, lo, &ctrl->rc.m_l, apply_bound, 2);
+      if (s != SA_OK) return s;
+      src = kb;
+      lo = ctrl->zero;
+    }
+    ++pend.apply;
+    return launch(SA_K_APPLY, 0, PENDING, [&] {
+      return launch_apply_names(src, lo, &ctrl->rc.m_l, apply_bound, gname[out], gold, isa,
+                                N + S + 1, st);
     });
+  }
+
+  // Position bucketing of `count` entries starting at `lo` into keys
+  // buffer B (free whenever ISA writes are pending). `src_tag` tells the
+  // byte settlement which count applies (0: queued updates, 2: survivors).
+  sa_status bucket(const uint64_t *in, const uint32_t *lo, const uint32_t *count,
+                   uint32_t max_count, int src_tag) {
+    BucketArgs ba{};
+    ba.in = in;
+    ba.lo = lo;
+    ba.count = count;
+    ba.max_count = max_count;
+    const uint32_t bits = bits_for(N + S);
+    ba.shift = bits > 8 ? bits - 8 : 0;
+    ba.blocks = std::min<uint32_t>(BUCKET_BLOCKS_MAX, 4 * sm_count());
+    ba.counts = bcount;
+    ba.out = kb;
+    ++(src_tag ? pend.bucket_surv : pend.bucket_upd);
+    sa_status s = launch(SA_K_BUCKET, src_tag, PENDING,
+                         [&] { return launch_bucket_count(ba, st); });
+    if (s != SA_OK) return s;
+    s = launch(SA_K_BUCKET, src_tag, 0, [&] { return launch_bucket_offsets(ba, st); });
+    if (s != SA_OK) return s;
+    return launch(SA_K_BUCKET, src_tag | 1, PENDING,
+                  [&] { return launch_bucket_scatter(ba, st); });
+  }
+
+  // ISA[i'] = new for the queued updates (at most `bound` of them).
+  sa_status scatter(uint32_t bound) {
+    const uint64_t *src = upd;
+    if (bound >= BUCKET_MIN) {
+      sa_status s = bucket(upd, nullptr, &ctrl->rc.upd, bound, 0);
+      if (s != SA_OK) return s;
+      src = kb;
+    }
+    ++pend.scatter;
+    return launch(SA_K_SCATTER, 0, PENDING, [&] {
+      return launch_scatter_updates(src, bound, isa, N + S + 1, ctrl, st);
+    });
+  }
+
+  // Byte counts of the launches whose sizes are known only from this
+  // round's control block: scatter and apply read 8 and write 4 bytes per
+  // entry; bucketing reads 8 (histogram), then reads and writes 8.
+  void settle(const HostCtrl &hc) {
+    bytes += pend.scatter * 12ull * hc.upd + pend.apply * 12ull * hc.m_l +
+             pend.bucket_upd * 24ull * hc.upd + pend.bucket_surv * 24ull * hc.m_l;
+    pend = Pending{};
+    for (Rec &r : recs) {
+      if (r.bytes != PENDING) continue;
+      if (r.cls == SA_K_SCATTER) r.bytes = 12ull * hc.upd;
+      if (r.cls == SA_K_APPLY) r.bytes = 12ull * hc.m_l;
+      if (r.cls == SA_K_BUCKET)
+        r.bytes = ((r.pass & 1) ? 16ull : 8ull) * ((r.pass & 2) ? hc.m_l : hc.upd);
+    }
   }
 
   // Rename (round 0 or large groups) reads 12 bytes per item; writes 4
@@ -539,13 +615,14 @@ struct Build {
     int cur = 0;  // the active list, group starts and names of this round
     s = rename(N32, true, cb, c0, 0, nullptr, nullptr, 0, cur, ctrl->zero);
     if (s != SA_OK) return s;
-    s = classify(cur, N / 2 + 1);
+    s = classify(cur, N / 2 + 1, N32);
     if (s != SA_OK) return s;
     HostCtrl hc{};
     s = read_ctrl(hc);
     if (s != SA_OK) return s;
     uint32_t m = N32;
     const uint64_t rb0 = rename_bytes(m, hc.m_next(), hc.g_next());
+    settle(hc);
     s = flush(hc.pass_mask, rb0);
     if (s != SA_OK) return s;
     record(0, m, hc, bits0);
@@ -554,11 +631,10 @@ struct Build {
     // ISA output or the trace; a text resolved in round 0 skips them.
     const bool want_trace = opt.trace_isa && opt.trace_cap > 0 && S == 1;
     if (hc.m_next() > 0 || isa_out || want_trace) {
-      s = launch(SA_K_SCATTER, 0, 12ull * hc.upd, [&] {
-        return launch_scatter_updates(upd, N32, isa, N + S + 1, ctrl, sm_count(), st);
-      });
+      // Its records settle with round 0's counts, before round 1 reads new ones.
+      s = scatter(hc.upd);
       if (s != SA_OK) return s;
-      bytes += 12ull * hc.upd;
+      settle(hc);
     }
     if (want_trace) CK(cudaMemcpyAsync(opt.trace_isa, isa, N * 4, cudaMemcpyDeviceToDevice, st));
 
@@ -629,11 +705,9 @@ struct Build {
         s = rename(mL, false, 0, 0, W, lbase, lold, GL, nxt, &ctrl->rc.m_s);
         if (s != SA_OK) return s;
       }
-      s = launch(SA_K_SCATTER, 0, 0, [&] {
-        return launch_scatter_updates(upd, m, isa, N + S + 1, ctrl, sm_count(), st);
-      });
+      s = scatter(m);
       if (s != SA_OK) return s;
-      s = classify(nxt, G);
+      s = classify(nxt, G, mL);
       if (s != SA_OK) return s;
       if (opt.trace_isa && round < opt.trace_cap && S == 1)
         CK(cudaMemcpyAsync(opt.trace_isa + (size_t)round * N, isa, N * 4,
@@ -643,16 +717,13 @@ struct Build {
       // Settle the byte counts that depend on this round's results.
       const uint64_t rbl = mL ? rename_bytes(mL, hc.m_l, hc.g_l) : 0;
       const uint64_t rfb = refine_bytes(m - mL, G - GL, hc.m_s, hc.g_s, hc.upd);
-      if (prof && stats) {
-        for (Rec &r : recs) {
-          if (r.cls == SA_K_REFINE) r.bytes = rfb;
-          if (r.cls == SA_K_SCATTER) r.bytes = 12ull * hc.upd;
-        }
-      }
+      for (Rec &r : recs)
+        if (r.cls == SA_K_REFINE) r.bytes = rfb;
+      settle(hc);
       s = flush(hc.pass_mask, rbl);
       if (s != SA_OK) return s;
       record(round, m, hc, kbits);
-      bytes += (mL ? (uint64_t)hc.passes * 24 * mL : 0) + rbl + rfb + 12ull * hc.upd + 8ull * G;
+      bytes += (mL ? (uint64_t)hc.passes * 24 * mL : 0) + rbl + rfb + 8ull * G;
       cur = nxt;
       h *= 2;
       ++round;

@@ -627,47 +627,70 @@ cudaError_t launch_refine(const RefineArgs &a, cudaStream_t stream) {
   return cudaErrorInvalidValue;
 }
 
-// ---- names of the rename's survivors ------------------------------------------
+// ---- ISA writes of new names ------------------------------------------------
+// One block per 2048-entry chunk, 8 independent entries per thread; blocks
+// start in chunk order, so after position bucketing the ISA being written
+// stays a narrow window.
+
+constexpr int WB_ITEMS = 8;
+constexpr int WB_CHUNK = 256 * WB_ITEMS;
 
 __global__ void __launch_bounds__(256) k_apply_names(const uint64_t *__restrict__ act,
+                                                    const uint32_t *lo_p, const uint32_t *count_p,
                                                     const uint32_t *__restrict__ gname,
                                                     const uint32_t *__restrict__ gold,
-                                                    uint32_t *isa, uint64_t isa_len, Ctrl *ctrl) {
-  const uint32_t lo = ctrl->rc.m_s, hi = lo + ctrl->rc.m_l;
-  for (uint64_t x = lo + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < hi;
-       x += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t e = act[x];
-    const uint32_t g = (uint32_t)(e >> 32), ip = (uint32_t)e;
+                                                    uint32_t *isa, uint64_t isa_len) {
+  const uint64_t lo = *lo_p, n = *count_p;
+  const uint64_t c0 = (uint64_t)blockIdx.x * WB_CHUNK;
+  if (c0 >= n) return;
+  uint64_t e[WB_ITEMS];
+#pragma unroll
+  for (int k = 0; k < WB_ITEMS; ++k) {
+    const uint64_t x = c0 + (uint64_t)k * 256 + threadIdx.x;
+    e[k] = x < n ? act[lo + x] : ~0ull;
+  }
+#pragma unroll
+  for (int k = 0; k < WB_ITEMS; ++k) {
+    if (e[k] == ~0ull) continue;
+    const uint32_t g = (uint32_t)(e[k] >> 32), ip = (uint32_t)e[k];
     const uint32_t name = __ldg(gname + g);
     if (name != __ldg(gold + g) && ip < isa_len) isa[ip] = name;
   }
 }
 
-cudaError_t launch_apply_names(const uint64_t *act, const uint32_t *gname, const uint32_t *gold,
-                               uint32_t *isa, uint64_t isa_len, Ctrl *ctrl, int num_sms,
-                               cudaStream_t stream) {
-  k_apply_names<<<num_sms * 8, 256, 0, stream>>>(act, gname, gold, isa, isa_len, ctrl);
+cudaError_t launch_apply_names(const uint64_t *act, const uint32_t *lo, const uint32_t *count,
+                               uint32_t max_count, const uint32_t *gname, const uint32_t *gold,
+                               uint32_t *isa, uint64_t isa_len, cudaStream_t stream) {
+  const uint64_t blocks = ((uint64_t)max_count + WB_CHUNK - 1) / WB_CHUNK;
+  if (blocks == 0) return cudaSuccess;
+  k_apply_names<<<(unsigned)blocks, 256, 0, stream>>>(act, lo, count, gname, gold, isa, isa_len);
   return cudaGetLastError();
 }
-
-// ---- deferred ISA updates -----------------------------------------------------
 
 __global__ void __launch_bounds__(256) k_scatter_updates(const uint64_t *__restrict__ upd,
                                                         uint32_t max_upd, uint32_t *isa,
                                                         uint64_t isa_len, Ctrl *ctrl) {
-  const uint32_t n = min(ctrl->rc.upd, max_upd);
-  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
-       x += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t u = upd[x];
-    const uint32_t ip = (uint32_t)u;
-    if (ip < isa_len) isa[ip] = (uint32_t)(u >> 32);
+  const uint64_t n = min(ctrl->rc.upd, max_upd);
+  const uint64_t c0 = (uint64_t)blockIdx.x * WB_CHUNK;
+  if (c0 >= n) return;
+  uint64_t u[WB_ITEMS];
+#pragma unroll
+  for (int k = 0; k < WB_ITEMS; ++k) {
+    const uint64_t x = c0 + (uint64_t)k * 256 + threadIdx.x;
+    u[k] = x < n ? upd[x] : ~0ull;
+  }
+#pragma unroll
+  for (int k = 0; k < WB_ITEMS; ++k) {
+    const uint32_t ip = (uint32_t)u[k];
+    if (u[k] != ~0ull && ip < isa_len) isa[ip] = (uint32_t)(u[k] >> 32);
   }
 }
 
 cudaError_t launch_scatter_updates(const uint64_t *upd, uint32_t max_upd, uint32_t *isa,
-                                   uint64_t isa_len, Ctrl *ctrl, int num_sms,
-                                   cudaStream_t stream) {
-  k_scatter_updates<<<num_sms * 8, 256, 0, stream>>>(upd, max_upd, isa, isa_len, ctrl);
+                                   uint64_t isa_len, Ctrl *ctrl, cudaStream_t stream) {
+  const uint64_t blocks = ((uint64_t)max_upd + WB_CHUNK - 1) / WB_CHUNK;
+  if (blocks == 0) return cudaSuccess;
+  k_scatter_updates<<<(unsigned)blocks, 256, 0, stream>>>(upd, max_upd, isa, isa_len, ctrl);
   return cudaGetLastError();
 }
 

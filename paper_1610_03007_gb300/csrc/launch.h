@@ -175,16 +175,34 @@ struct RefineArgs {
 };
 cudaError_t launch_refine(const RefineArgs &a, cudaStream_t stream);
 
-// ISA[i'] = gname[g] for the rename's survivors (act[rc.m_s, rc.m_s +
-// rc.m_l)) whose group name differs from their parent's.
-cudaError_t launch_apply_names(const uint64_t *act, const uint32_t *gname, const uint32_t *gold,
-                               uint32_t *isa, uint64_t isa_len, Ctrl *ctrl, int num_sms,
-                               cudaStream_t stream);
+// ISA[i'] = gname[g] for the entries act[*lo, *lo + *count) whose group
+// name differs from their parent's (the rename's survivors, or a bucketed
+// copy of them); *count <= max_count. Blocks take consecutive chunks in
+// launch order.
+cudaError_t launch_apply_names(const uint64_t *act, const uint32_t *lo, const uint32_t *count,
+                               uint32_t max_count, const uint32_t *gname, const uint32_t *gold,
+                               uint32_t *isa, uint64_t isa_len, cudaStream_t stream);
 
-// ISA[i'] = new for the ctrl->rc.upd queued updates.
+// ISA[i'] = new for the min(ctrl->rc.upd, max_upd) queued updates; blocks
+// take consecutive chunks in launch order.
 cudaError_t launch_scatter_updates(const uint64_t *upd, uint32_t max_upd, uint32_t *isa,
-                                   uint64_t isa_len, Ctrl *ctrl, int num_sms,
-                                   cudaStream_t stream);
+                                   uint64_t isa_len, Ctrl *ctrl, cudaStream_t stream);
+
+// ---- position bucketing of ISA writes (k_bucket.cu) ------------------------
+constexpr uint32_t BUCKET_BLOCKS_MAX = 1024;
+struct BucketArgs {
+  const uint64_t *in;     // entries (x << 32) | i'
+  const uint32_t *lo;     // device word: first entry (NULL: 0)
+  const uint32_t *count;  // device word: number of entries
+  uint32_t max_count;     // capacity of `in` past *lo and of `out`
+  uint32_t shift;         // bucket of an entry: min(i' >> shift, 255)
+  uint32_t blocks;        // partition blocks (<= BUCKET_BLOCKS_MAX)
+  uint32_t *counts;       // blocks x 256 words: counts, then run starts
+  uint64_t *out;          // entries grouped by bucket
+};
+cudaError_t launch_bucket_count(const BucketArgs &a, cudaStream_t stream);
+cudaError_t launch_bucket_offsets(const BucketArgs &a, cudaStream_t stream);
+cudaError_t launch_bucket_scatter(const BucketArgs &a, cudaStream_t stream);
 
 // ---- output (k_gather.cu) ------------------------------------------------
 // isa_out[p] = isa[p + s] - off_s for text s (single text: a copy).

@@ -155,6 +155,20 @@ def test_scaled_workloads_elementwise(gb, orc, recipe):
     assert np.array_equal(gpu_sa(gb, t), orc.pd_sa(t)[0])
 
 
+def test_bucketed_isa_writes_elementwise(gb, orc):
+    """Above 2^22 pending ISA writes the names go through position buckets
+    (round 0's survivors and the later rounds' queued updates): SA and ISA
+    equal the oracle's at a ragged size where both paths run."""
+    n = 5 * (1 << 20) + 77
+    t = gen.text("zipf_repeats", 2003, n)
+    sa, isa, stats, _ = gb.sa_build_ex(dev_text(t), isa=True, profile=True)
+    want_sa, want_isa, _, _ = orc.pd_sa(t)
+    assert stats["active"][1] >= 1 << 22
+    assert stats["kernels"]["bucket"]["launches"] >= 4
+    assert np.array_equal(sa.cpu().numpy().view(np.uint32), want_sa)
+    assert np.array_equal(isa.cpu().numpy().view(np.uint32), want_isa)
+
+
 def test_workload_2_full_size_properties(gb, orc):
     """n = 2^28 repeated Zipf text, in the benchmark's launch configuration:
     the linear-time checker (permutation + adjacent order through the ranks),
