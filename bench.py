@@ -106,6 +106,7 @@ class ClockSampler:
 
 
 KERNEL_SOURCES = {"onesweep": "k_sort.cu", "refine": "k_refine.cu", "rename": "k_rename.cu",
+                  "bucket": "k_bucket.cu",
                   "scatter": "k_refine.cu", "apply": "k_refine.cu", "pack": "k_pack.cu"}
 
 

@@ -443,6 +443,7 @@ struct Build {
     if (s != SA_OK) return s;
     // ISA entries of the rename's survivors whose name changed, bucketed by
     // position first when there can be many.
+    if (apply_bound == 0) return SA_OK;
     const uint64_t *src = act[out];
     const uint32_t *lo = &ctrl->rc.m_s;
     if (apply_bound >= BUCKET_MIN) {
@@ -485,6 +486,7 @@ struct Build {
 
   // ISA[i'] = new for the queued updates (at most `bound` of them).
   sa_status scatter(uint32_t bound) {
+    if (bound == 0) return SA_OK;
     const uint64_t *src = upd;
     if (bound >= BUCKET_MIN) {
       sa_status s = bucket(upd, nullptr, &ctrl->rc.upd, bound, 0);
