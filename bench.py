@@ -22,6 +22,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import re
 import subprocess
 import sys
@@ -139,6 +140,25 @@ def ncu_traffic(kernel: str):
     return float(m_r.group(1))
 
 
+def cpu_model() -> str:
+    """The host CPU as /proc/cpuinfo names it ("model name" on x86; the ARM
+    implementer and part numbers on Arm servers, 0x41/0xd4f = Neoverse V2)."""
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                fields.setdefault(k.strip(), v.strip())
+    except OSError:
+        pass
+    if "model name" in fields:
+        return fields["model name"]
+    if "CPU part" in fields:
+        return (f"{platform.machine()} CPU implementer {fields.get('CPU implementer', '?')} "
+                f"part {fields['CPU part']}")
+    return platform.machine()
+
+
 def cpu_baseline():
     """The oracle as it stands, one host core, on a bounded sample: the same
     recipe at n = 2^23."""
@@ -150,6 +170,7 @@ def cpu_baseline():
     o.pd_sa(t)
     dt = time.perf_counter() - t0
     return {"value": CPU_SAMPLE_N / dt / 1e6, "unit": "MB/s", "cores": 1, "kind": "oracle",
+            "cpu_model": cpu_model(), "nproc": os.cpu_count(),
             "sample": f"zipf_repeats recipe at n=2^23 (base 32 KiB x 256 copies), one "
                       f"prefix-doubling-with-discarding build, {dt:.1f} s on "
                       f"{os.cpu_count()} visible host cores (1 used)"}
@@ -180,6 +201,7 @@ def run_reference(args):
                                    "0.1% substitutions (sampled at n=2^20 for the CPU oracle)",
                        "n": REF_STEP_N},
             "cpu_baseline": {"value": value, "unit": "MB/s", "cores": 1, "kind": "oracle",
+                             "cpu_model": cpu_model(), "nproc": os.cpu_count(),
                              "sample": sample},
             "e2e": {"value": value, "unit": "MB/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
