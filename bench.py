@@ -274,6 +274,30 @@ def run_plain(args):
     clocks = sampler.stop()
     stats = st
 
+    # BWT of the built SA through sa_bwt, timed alone on the same stream
+    # (text, SA and BWT together exceed L2).
+    sa_dev = step(profile=False)[0]
+    lib = gbsa.load()
+    bwt_buf = torch.empty(n + 1, dtype=torch.uint8, device=dev)
+    prim = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    def bwt_call():
+        rc = lib.sa_bwt(text.data_ptr(), n, sa_dev.data_ptr(), bwt_buf.data_ptr(),
+                        prim.data_ptr(), stream.cuda_stream)
+        if rc != 0:
+            raise RuntimeError(f"sa_bwt failed: {rc}")
+
+    for _ in range(3):
+        bwt_call()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record(stream)
+    for _ in range(5):
+        bwt_call()
+    b1.record(stream)
+    torch.cuda.synchronize()
+    bwt_ms = b0.elapsed_time(b1) / 5
+    del sa_dev, bwt_buf
+
     # End to end through the host entry point: pinned host text in, host SA
     # out, copies inside the timed region.
     h_text = torch.from_numpy(t_host).pin_memory()
@@ -330,6 +354,10 @@ def run_plain(args):
                 "d2h_bytes_per_step": 4 * n, "ms_per_step": e2e_ms},
         "gpu_launches": launches,
         "clocks": clocks,
+        "bwt": {"ms": bwt_ms, "bytes_per_row": 6,
+                "gbs": 6.0 * (n + 1) / (bwt_ms * 1e-3) / 1e9,
+                "frac": 6.0 * (n + 1) / (bwt_ms * 1e-3) / 1e9 / hbm,
+                "note": "sa_bwt on the built SA, outside the timed step"},
     }
     line["cpu_baseline"] = cpu_baseline() if (world == 1 and not args.no_cpu) else None
     print(json.dumps(line), flush=True)

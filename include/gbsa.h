@@ -292,6 +292,25 @@ void sa_server_get_stats(sa_server *s, sa_server_stats *out);
  * the server. */
 void sa_server_destroy(sa_server *s);
 
+/* ---- Burrows-Wheeler transform from the suffix array ------------------
+ * The direct consumer of SA named as future work at the end of the paper
+ * (Section 6); BWT[r] = T[SA[r] - 1] by the definitions of Section 2.
+ * Rows are those of T$ (n + 1): row 0 is the suffix $ alone, preceded by
+ * T[n - 1]; row r >= 1 is the suffix sa[r - 1], preceded by
+ * T[sa[r - 1] - 1], except the row whose suffix is T itself, which holds $
+ * stored as byte 0; its row index is the primary index.
+ * text        : DEVICE, n bytes, read only.
+ * sa          : DEVICE, n uint32, the suffix array of text (sa_build).
+ * bwt_out     : DEVICE, n + 1 bytes, written.
+ * primary_out : DEVICE, one uint64, written with the primary index
+ *               (0 for n = 0).
+ * Stream-ordered on `stream`; allocates nothing. Returns SA_ERR_INVALID_ARG
+ * for a NULL pointer (text and sa may be NULL when n = 0) and
+ * SA_ERR_TOO_LARGE for n > SA_MAX_N. An sa that is not a suffix array of
+ * text gives an unspecified BWT but no out-of-bounds access. */
+sa_status sa_bwt(const uint8_t *text, uint64_t n, const uint32_t *sa, uint8_t *bwt_out,
+                 uint64_t *primary_out, gbsa_stream_t stream);
+
 /* Human-readable name of a status code (static string). */
 const char *sa_status_string(sa_status s);
 

@@ -30,7 +30,8 @@ EXPORTED = ("sa_build", "sa_workspace_bytes", "sa_build_ex", "sa_build_batched",
             "sa_batched_workspace_bytes", "sa_build_batched_ex", "sa_build_host",
             "sa_sort_pairs", "sa_sort_workspace_bytes", "sa_status_string",
             "sa_build_noalloc", "sa_request_footprint", "sa_server_create", "sa_server_submit",
-            "sa_server_poll", "sa_server_wait", "sa_server_get_stats", "sa_server_destroy")
+            "sa_server_poll", "sa_server_wait", "sa_server_get_stats", "sa_server_destroy",
+            "sa_bwt")
 
 
 class SAError(RuntimeError):
@@ -132,6 +133,7 @@ def load(path: str | None = None):
     lib.sa_build_host.argtypes = [vp, u64, vp, vp]
     lib.sa_build_noalloc.argtypes = [vp, u64, vp, vp]
     lib.sa_sort_pairs.argtypes = [vp, vp, u64, u32, u32, vp, sz, vp]
+    lib.sa_bwt.argtypes = [vp, u64, vp, vp, vp, vp]
     lib.sa_sort_workspace_bytes.argtypes = [u64]
     lib.sa_sort_workspace_bytes.restype = sz
     lib.sa_request_footprint.argtypes = [u64]
@@ -288,6 +290,22 @@ def sa_sort_pairs(keys, vals, begin_bit=0, end_bit=64, workspace=None, stream=No
                              workspace.numel() if workspace is not None else 0,
                              _stream(stream)), "sa_sort_pairs")
     return keys, vals
+
+
+def sa_bwt(text, sa, stream=None):
+    """Burrows-Wheeler transform of text$ from its suffix array (CUDA uint8
+    and int32 tensors). Returns (bwt uint8 tensor of n + 1 rows, primary
+    index); the $ is stored as 0 at the primary row."""
+    torch = _torch()
+    lib = load()
+    t = _dev_u8(text)
+    n = t.numel()
+    assert sa.numel() == n and sa.is_cuda
+    bwt = torch.empty(n + 1, dtype=torch.uint8, device=t.device)
+    prim = torch.zeros(1, dtype=torch.int64, device=t.device)
+    _check(lib.sa_bwt(t.data_ptr() if n else None, n, sa.data_ptr() if n else None,
+                      bwt.data_ptr(), prim.data_ptr(), _stream(stream)), "sa_bwt")
+    return bwt, int(prim.item())
 
 
 def status_string(s: int) -> str:

@@ -60,6 +60,10 @@ def test_host_side_argument_checks(lib):
     assert lib.sa_build_batched(None, off.ctypes.data, 1, None, None) == 2
     assert lib.sa_sort_pairs(None, None, 10, 8, 8, None, 0, None) == 1   # empty bit range
     assert lib.sa_sort_pairs(None, None, 10, 0, 65, None, 0, None) == 1
+    # BWT: NULL outputs, NULL inputs with n > 0, n above 2^31 (no GPU work)
+    assert lib.sa_bwt(None, 0, None, None, None, None) == 1
+    assert lib.sa_bwt(None, 5, None, 8, 8, None) == 1
+    assert lib.sa_bwt(8, (1 << 31) + 1, 8, 8, 8, None) == 2
 
 
 def test_workspace_model(lib):
