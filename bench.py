@@ -395,21 +395,15 @@ def run_batched(args, emit=True):
                      dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(profile=False, items=0):
-        return gbsa.sa_build_batched(texts, off, sa_out=sa, workspace=ws, stats=True,
-                                     profile=profile, sort_items=items or best_items)
+    # Radix tile and key width picked by measurement (the batched build is
+    # sort-bound).
+    from paper_1610_03007_gb300 import autotune
+    tuned = autotune.tune_batched(texts, off, sa, ws)
+    best = tuned["params"]
 
-    # Radix tile picked by measurement (the batched build is sort-bound).
-    best_items, cand = 16, {}
-    for items in (16, 12, 8):
-        step(items=items)
-        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        c0.record(stream)
-        step(items=items)
-        c1.record(stream)
-        torch.cuda.synchronize()
-        cand[items] = c0.elapsed_time(c1)
-    best_items = min(cand, key=cand.get)
+    def step(profile=False):
+        return gbsa.sa_build_batched(texts, off, sa_out=sa, workspace=ws, stats=True,
+                                     profile=profile, **best)
     for _ in range(max(args.warmup, 1)):
         step()
     torch.cuda.synchronize()
@@ -456,8 +450,9 @@ def run_batched(args, emit=True):
            "config": {"workload": f"{count} uniform-DNA texts, lengths log-uniform in "
                                   f"[1 KiB, 4 MiB], one SA per text", "total_bytes": N,
                       "seed": BATCH_SEED, "rounds": st["rounds"],
-                      "tuned": {"sort_items": best_items,
-                                "candidates_ms": {str(k): round(v, 2) for k, v in cand.items()}}},
+                      "tuned": {"params": best,
+                                "candidates_ms": {k: round(v, 2)
+                                                  for k, v in tuned["tried"].items()}}},
            "per_text_plain": {"value": N / (plain_ms * 1e-3) / 1e6, "unit": "MB/s",
                               "ms": plain_ms, "calls": count},
            "speedup_vs_per_text": plain_ms / ms,

@@ -231,7 +231,7 @@ def sa_build_ex(text, *, isa=False, workspace=None, h0_chars=0, spin_limit=0,
 
 
 def sa_build_batched(texts, offsets, sa_out=None, workspace=None, stream=None, stats=False,
-                     profile=False, refine_shape=0, sort_items=0):
+                     profile=False, refine_shape=0, sort_items=0, h0_chars=0):
     """SAs of many texts in one launch sequence.
 
     texts: 1-D uint8 CUDA tensor (the texts concatenated); offsets: host
@@ -249,7 +249,7 @@ def sa_build_batched(texts, offsets, sa_out=None, workspace=None, stream=None, s
     if workspace is None and N:
         workspace = torch.empty(wsb, dtype=torch.uint8, device=t.device)
     st = Stats()
-    opt = Options(0, 0, 0, None, 0, 0, refine_shape, sort_items, 1 if profile else 0)
+    opt = Options(h0_chars, 0, 0, None, 0, 0, refine_shape, sort_items, 1 if profile else 0)
     rc = lib.sa_build_batched_ex(t.data_ptr(), off.ctypes.data, count,
                                  sa_out.data_ptr() if N else None,
                                  workspace.data_ptr() if workspace is not None else None,

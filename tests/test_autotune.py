@@ -22,3 +22,12 @@ def test_buckets():
     assert autotune.bucket(1) == 0
     assert autotune.bucket(1 << 28) == 28
     assert autotune.bucket((1 << 28) - 1) == 27
+
+
+def test_key_width_candidates_fill_whole_digit_passes():
+    # batched DNA: 2 bits per character, 12 text-id bits -> 7..3 passes
+    assert autotune.key_width_candidates(26, 2) == [22, 18, 14, 10, 6]
+    # one text over 8-bit characters: 8 characters fill 64 bits
+    assert autotune.key_width_candidates(8, 8) == [7, 6, 5, 4, 3]
+    # nothing at or above the maximum, nothing below two characters
+    assert all(2 <= c < 4 for c in autotune.key_width_candidates(4, 8))

@@ -85,9 +85,9 @@ def batched_reference(orc, flat, off):
     return out
 
 
-def run_batched(gb, flat, off):
+def run_batched(gb, flat, off, **opt):
     import torch
-    sa = gb.sa_build_batched(torch.from_numpy(flat).cuda(), off)
+    sa = gb.sa_build_batched(torch.from_numpy(flat).cuda(), off, **opt)
     torch.cuda.synchronize()
     return sa.cpu().numpy().view(np.uint32)
 
@@ -114,6 +114,18 @@ def test_batched_repeats_and_mixed_alphabets(gb, orc):
     off = np.zeros(len(parts) + 1, dtype=np.uint64)
     off[1:] = np.cumsum([p.size for p in parts])
     assert np.array_equal(run_batched(gb, flat, off), batched_reference(orc, flat, off))
+
+
+@pytest.mark.parametrize("h0", [2, 7, 13])
+def test_batched_key_widths(gb, orc, h0):
+    """Fewer characters per initial key than fit (the tuner's key width):
+    short keys leave more suffixes tied for the doubling rounds."""
+    flat, off = gen.batch(77, 300, 1, 6000)
+    parts = [flat, gen.text("zipf_repeats", 5, 9000), np.zeros(40, np.uint8)]
+    flat2 = np.concatenate(parts)
+    off2 = np.concatenate([off, [off[-1] + 9000, off[-1] + 9040]]).astype(np.uint64)
+    assert np.array_equal(run_batched(gb, flat2, off2, h0_chars=h0),
+                          batched_reference(orc, flat2, off2))
 
 
 def test_bounded_wait_expires_and_context_survives(gb, orc):

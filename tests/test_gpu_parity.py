@@ -228,6 +228,20 @@ def test_every_refine_tile_shape(gb, orc, shape, recipe):
     assert np.array_equal(isa.cpu().numpy().view(np.uint32), oisa)
 
 
+@pytest.mark.parametrize("recipe,n", [("zipf_repeats", 300007), ("dna", 1 << 18),
+                                      ("bytes", 65537), ("markov", 200003)])
+@pytest.mark.parametrize("h0", [1, 3, 5, 12])
+def test_key_widths(gb, orc, recipe, n, h0):
+    """The tuner's key width: h0 characters per initial key (capped at what
+    fits), so more rounds resolve what round 0 would have."""
+    t = gen.text(recipe, 911 + h0, n)
+    sa, isa, stats, _ = gb.sa_build_ex(dev_text(t), isa=True, h0_chars=h0)
+    assert stats["chars_per_key"] <= h0
+    want_sa, want_isa, _, _ = orc.pd_sa(t)
+    assert np.array_equal(sa.cpu().numpy().view(np.uint32), want_sa)
+    assert np.array_equal(isa.cpu().numpy().view(np.uint32), want_isa)
+
+
 @pytest.mark.parametrize("items", [8, 12, 16])
 def test_every_radix_tile_size(gb, orc, items):
     """Each radix-pass tile size gives the oracle's SA (round 0 sorts all n
