@@ -40,7 +40,7 @@ def build(mutant: int = 0, force: bool = False) -> str:
     return out
 
 
-MUTANTS = (1, 2, 3, 4, 5, 6, 7, 8, 9)
+MUTANTS = (1, 2, 3, 4, 5, 6, 7, 8, 9, 10)
 
 
 class Oracle:
@@ -63,6 +63,10 @@ class Oracle:
         lib.oracle_suffix_rank.restype = i64
         lib.oracle_bwt.argtypes = [p, i64, p, p, p]
         lib.oracle_bwt.restype = None
+        lib.oracle_lcp_pair.argtypes = [p, i64, i64, i64]
+        lib.oracle_lcp_pair.restype = i64
+        lib.oracle_lcp.argtypes = [p, i64, p, p]
+        lib.oracle_lcp.restype = None
         lib.oracle_bwt_invert.argtypes = [p, i64, i64, p]
         lib.oracle_bwt_invert.restype = ctypes.c_int
         self._lib = lib
@@ -136,6 +140,19 @@ class Oracle:
         self._lib.oracle_bwt(T.ctypes.data, T.size, s.ctypes.data, out.ctypes.data,
                              ctypes.byref(prim))
         return out, int(prim.value)
+
+    def lcp_pair(self, t, a: int, b: int) -> int:
+        """Longest common prefix of suffixes a and b (the definition)."""
+        T = self._text(t)
+        return int(self._lib.oracle_lcp_pair(T.ctypes.data, T.size, a, b))
+
+    def lcp(self, t, sa) -> np.ndarray:
+        """LCP array of T for its suffix array sa (lcp[0] = 0)."""
+        T = self._text(t)
+        s = np.ascontiguousarray(sa, dtype=np.uint32)
+        out = np.zeros(T.size, dtype=np.uint32)
+        self._lib.oracle_lcp(T.ctypes.data, T.size, s.ctypes.data, out.ctypes.data)
+        return out
 
     def bwt_invert(self, bwt, primary: int) -> np.ndarray:
         b = np.ascontiguousarray(bwt, dtype=np.uint8)

@@ -324,3 +324,22 @@ int oracle_bwt_invert(const uint8_t *bwt, int64_t n, int64_t primary, uint8_t *o
   free(occ);
   return 0;
 }
+
+/* ---- LCP array (a consumer of SA, Section 6), by its definition -------- */
+
+int64_t oracle_lcp_pair(const uint8_t *T, int64_t n, int64_t a, int64_t b) {
+  int64_t l = 0;
+#if ORACLE_MUTANT == 10
+  /* mutant: stops one character before the end of text */
+  while (a + l < n - 1 && b + l < n - 1 && T[a + l] == T[b + l]) ++l;
+#else
+  while (a + l < n && b + l < n && T[a + l] == T[b + l]) ++l;
+#endif
+  return l;
+}
+
+void oracle_lcp(const uint8_t *T, int64_t n, const uint32_t *sa, uint32_t *lcp) {
+  if (n <= 0) return;
+  lcp[0] = 0;
+  for (int64_t j = 1; j < n; ++j) lcp[j] = (uint32_t)oracle_lcp_pair(T, n, sa[j - 1], sa[j]);
+}

@@ -11,8 +11,10 @@
  * Pins (tests/test_oracle.py): the worked examples Ex 1, Ex 2 and Ex 3,
  * closed forms (a^n, (ab)^m, all-distinct), brute force over every binary
  * string up to length 14 against Python's own bytes ordering, the
- * invariants (permutation, ISA[SA[j]] = j, BWT inversion reproduces T) and
- * planted-mutant builds of this file, each of which must fail a pin.
+ * invariants (permutation, ISA[SA[j]] = j, BWT inversion reproduces T),
+ * the LCP array's textbook and closed-form values and brute force against
+ * Python's own prefix comparison, and planted-mutant builds of this file,
+ * each of which must fail a pin.
  */
 #ifndef GBSA_ORACLE_H
 #define GBSA_ORACLE_H
@@ -89,6 +91,16 @@ void oracle_bwt(const uint8_t *T, int64_t n, const uint32_t *sa, uint8_t *bwt,
 
 /* Inverts oracle_bwt by LF-mapping; writes n bytes to out. Returns 0. */
 int oracle_bwt_invert(const uint8_t *bwt, int64_t n, int64_t primary, uint8_t *out);
+
+/* Longest common prefix of the suffixes T[a,n) and T[b,n): the number of
+ * leading characters they share, compared one by one (Section 2's suffix
+ * order; the LCP array of Section 6's future work is built from it). */
+int64_t oracle_lcp_pair(const uint8_t *T, int64_t n, int64_t a, int64_t b);
+
+/* LCP array by its definition: lcp[0] = 0 and, for j >= 1, lcp[j] =
+ * oracle_lcp_pair(sa[j-1], sa[j]) for the suffix array sa of T.
+ * O(n * average LCP). */
+void oracle_lcp(const uint8_t *T, int64_t n, const uint32_t *sa, uint32_t *lcp);
 
 #ifdef __cplusplus
 }

@@ -172,8 +172,46 @@ def pin_rank(o):
     return bad
 
 
+def py_lcp(t: bytes):
+    """LCP of adjacent suffixes in Python's bytes order: independent of
+    oracle.c (os.path.commonprefix on the two suffixes)."""
+    import os
+    order = py_sa(t)
+    return [0] + [len(os.path.commonprefix([t[order[j - 1]:], t[order[j]:]]))
+                  for j in range(1, len(t))]
+
+
+def pin_lcp(o):
+    bad = []
+    if list(o.lcp(b"banana", o.naive_sa(b"banana"))) != [0, 1, 3, 0, 0, 2]:  # textbook
+        bad.append("banana")
+    for n in (1, 2, 5, 64):  # a^n: adjacent suffixes a^j, a^(j+1)
+        if list(o.lcp(b"a" * n, o.naive_sa(b"a" * n))) != list(range(n)):
+            bad.append(f"a^{n}")
+    for m in (1, 4, 9):  # (ab)^m: 0, 2, .., 2m-2 | 0, 1, 3, .., 2m-3
+        t = b"ab" * m
+        want = [2 * k for k in range(m)] + [0] + [2 * k + 1 for k in range(m - 1)]
+        if list(o.lcp(t, o.naive_sa(t))) != want:
+            bad.append(f"(ab)^{m}")
+    t = bytes(range(200))  # all distinct: no shared prefix
+    if any(o.lcp(t, o.naive_sa(t))):
+        bad.append("distinct")
+    for L in range(1, 11):
+        for tup in itertools.product(b"ab", repeat=L):
+            t = bytes(tup)
+            if list(o.lcp(t, o.naive_sa(t))) != py_lcp(t):
+                bad.append(f"brute {t!r}")
+                return bad
+    t = gen.text("zipf_repeats", 21, 3000).tobytes()
+    if list(o.lcp(t, o.naive_sa(t))) != py_lcp(t):
+        bad.append("zipf_repeats")
+    if o.lcp_pair(b"abcabd", 0, 3) != 2 or o.lcp_pair(b"aaaa", 1, 2) != 2:
+        bad.append("pair")
+    return bad
+
+
 PINS = [pin_examples, pin_closed_forms, pin_bruteforce, pin_random, pin_checker,
-        pin_bwt, pin_rank]
+        pin_bwt, pin_rank, pin_lcp]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
