@@ -296,7 +296,27 @@ def run_plain(args):
     b1.record(stream)
     torch.cuda.synchronize()
     bwt_ms = b0.elapsed_time(b1) / 5
-    del sa_dev, bwt_buf
+    del bwt_buf
+
+    # LCP array of the built SA through sa_lcp (caller workspace), timed the
+    # same way.
+    lcp_buf = torch.empty(n, dtype=torch.int32, device=dev)
+    lcp_ws = torch.empty(int(lib.sa_lcp_workspace_bytes(n)), dtype=torch.uint8, device=dev)
+
+    def lcp_call():
+        rc = lib.sa_lcp(text.data_ptr(), n, sa_dev.data_ptr(), lcp_buf.data_ptr(),
+                        lcp_ws.data_ptr(), lcp_ws.numel(), stream.cuda_stream)
+        if rc != 0:
+            raise RuntimeError(f"sa_lcp failed: {rc}")
+
+    lcp_call()
+    b0.record(stream)
+    for _ in range(3):
+        lcp_call()
+    b1.record(stream)
+    torch.cuda.synchronize()
+    lcp_ms = b0.elapsed_time(b1) / 3
+    del sa_dev, lcp_buf, lcp_ws
 
     # End to end through the host entry point: pinned host text in, host SA
     # out, copies inside the timed region.
@@ -358,6 +378,10 @@ def run_plain(args):
                 "gbs": 6.0 * (n + 1) / (bwt_ms * 1e-3) / 1e9,
                 "frac": 6.0 * (n + 1) / (bwt_ms * 1e-3) / 1e9 / hbm,
                 "note": "sa_bwt on the built SA, outside the timed step"},
+        "lcp": {"ms": lcp_ms, "bytes_per_position": 30,
+                "gbs": 30.0 * n / (lcp_ms * 1e-3) / 1e9,
+                "frac": 30.0 * n / (lcp_ms * 1e-3) / 1e9 / hbm,
+                "note": "sa_lcp on the built SA, outside the timed step"},
     }
     line["cpu_baseline"] = cpu_baseline() if (world == 1 and not args.no_cpu) else None
     print(json.dumps(line), flush=True)

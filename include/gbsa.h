@@ -311,6 +311,26 @@ void sa_server_destroy(sa_server *s);
 sa_status sa_bwt(const uint8_t *text, uint64_t n, const uint32_t *sa, uint8_t *bwt_out,
                  uint64_t *primary_out, gbsa_stream_t stream);
 
+/* ---- LCP array from the suffix array -----------------------------------
+ * The other direct consumer of SA named as future work (Section 6):
+ * lcp_out[0] = 0 and, for j >= 1, lcp_out[j] = the length of the longest
+ * common prefix of the suffixes sa[j-1] and sa[j] (Section 2's order).
+ * Computed in the permuted form of Kasai et al.'s algorithm (Phi, PLCP).
+ * text      : DEVICE, n bytes, read only.
+ * sa        : DEVICE, n uint32, the suffix array of text (sa_build).
+ * lcp_out   : DEVICE, n uint32, written.
+ * workspace : DEVICE, ws_bytes >= sa_lcp_workspace_bytes(n), 256-byte
+ *             aligned; NULL to have it allocated and freed stream-ordered
+ *             on `stream` (cudaMallocAsync).
+ * Stream-ordered on `stream`. Returns SA_ERR_INVALID_ARG for a NULL text,
+ * sa or lcp_out with n > 0, or a short or misaligned workspace;
+ * SA_ERR_TOO_LARGE for n > SA_MAX_N; SA_ERR_OOM if the allocation fails.
+ * An sa that is not a suffix array of text gives unspecified values but no
+ * out-of-bounds access. n = 0 writes nothing. */
+size_t sa_lcp_workspace_bytes(uint64_t n);
+sa_status sa_lcp(const uint8_t *text, uint64_t n, const uint32_t *sa, uint32_t *lcp_out,
+                 void *workspace, size_t ws_bytes, gbsa_stream_t stream);
+
 /* Human-readable name of a status code (static string). */
 const char *sa_status_string(sa_status s);
 

@@ -31,7 +31,7 @@ EXPORTED = ("sa_build", "sa_workspace_bytes", "sa_build_ex", "sa_build_batched",
             "sa_sort_pairs", "sa_sort_workspace_bytes", "sa_status_string",
             "sa_build_noalloc", "sa_request_footprint", "sa_server_create", "sa_server_submit",
             "sa_server_poll", "sa_server_wait", "sa_server_get_stats", "sa_server_destroy",
-            "sa_bwt")
+            "sa_bwt", "sa_lcp", "sa_lcp_workspace_bytes")
 
 
 class SAError(RuntimeError):
@@ -134,6 +134,9 @@ def load(path: str | None = None):
     lib.sa_build_noalloc.argtypes = [vp, u64, vp, vp]
     lib.sa_sort_pairs.argtypes = [vp, vp, u64, u32, u32, vp, sz, vp]
     lib.sa_bwt.argtypes = [vp, u64, vp, vp, vp, vp]
+    lib.sa_lcp.argtypes = [vp, u64, vp, vp, vp, sz, vp]
+    lib.sa_lcp_workspace_bytes.argtypes = [u64]
+    lib.sa_lcp_workspace_bytes.restype = sz
     lib.sa_sort_workspace_bytes.argtypes = [u64]
     lib.sa_sort_workspace_bytes.restype = sz
     lib.sa_request_footprint.argtypes = [u64]
@@ -306,6 +309,27 @@ def sa_bwt(text, sa, stream=None):
     _check(lib.sa_bwt(t.data_ptr() if n else None, n, sa.data_ptr() if n else None,
                       bwt.data_ptr(), prim.data_ptr(), _stream(stream)), "sa_bwt")
     return bwt, int(prim.item())
+
+
+def sa_lcp(text, sa, workspace=None, stream=None):
+    """LCP array of text from its suffix array (CUDA uint8 and int32
+    tensors): int32 tensor, lcp[0] = 0, lcp[j] = longest common prefix of
+    the suffixes sa[j-1] and sa[j]."""
+    torch = _torch()
+    lib = load()
+    t = _dev_u8(text)
+    n = t.numel()
+    assert sa.numel() == n and sa.is_cuda
+    lcp = torch.empty(n, dtype=torch.int32, device=t.device)
+    if n and workspace is None:
+        workspace = torch.empty(int(lib.sa_lcp_workspace_bytes(n)), dtype=torch.uint8,
+                                device=t.device)
+    _check(lib.sa_lcp(t.data_ptr() if n else None, n, sa.data_ptr() if n else None,
+                      lcp.data_ptr() if n else None,
+                      workspace.data_ptr() if workspace is not None else None,
+                      workspace.numel() if workspace is not None else 0, _stream(stream)),
+           "sa_lcp")
+    return lcp
 
 
 def status_string(s: int) -> str:

@@ -64,6 +64,14 @@ def test_host_side_argument_checks(lib):
     assert lib.sa_bwt(None, 0, None, None, None, None) == 1
     assert lib.sa_bwt(None, 5, None, 8, 8, None) == 1
     assert lib.sa_bwt(8, (1 << 31) + 1, 8, 8, 8, None) == 2
+    # LCP: NULL arrays with n > 0, n above 2^31, a short or misaligned
+    # workspace; n = 0 does nothing (no GPU work in any of these)
+    assert lib.sa_lcp(None, 5, None, None, None, 0, None) == 1
+    assert lib.sa_lcp(8, (1 << 31) + 1, 8, 8, None, 0, None) == 2
+    assert lib.sa_lcp(256, 100, 256, 256, 256, 10, None) == 1
+    assert lib.sa_lcp(256, 100, 256, 256, 257, 1 << 20, None) == 1
+    assert lib.sa_lcp(None, 0, None, None, None, 0, None) == 0
+    assert lib.sa_lcp_workspace_bytes(1000) >= 8000
 
 
 def test_workspace_model(lib):
