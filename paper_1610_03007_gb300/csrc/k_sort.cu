@@ -144,6 +144,7 @@ struct OsSmem {
   uint32_t match[OS_WARPS][RADIX];  // per-warp peer masks (zero between uses)
   uint16_t whist[OS_WARPS][RADIX];  // per-warp counts, then per-warp prefixes
   uint32_t start[RADIX];            // tile-local start of each digit run
+  uint32_t count[RADIX];            // the tile's count of each digit (early, by atomics)
   uint32_t goff[RADIX];             // global index of a run = goff + local index
   uint32_t tmp[OS_WARPS + 1];
   uint32_t tile;
@@ -171,6 +172,7 @@ __global__ void __launch_bounds__(OS_BLOCK, OS_ITEMS >= 16 ? 3 : (OS_ITEMS >= 12
     (&S.whist[0][0])[x] = 0;
     (&S.match[0][0])[x] = 0u;
   }
+  S.count[tid] = 0u;
   __syncthreads();
   if (S.bail) return;
   const uint32_t tile = S.tile;
@@ -201,27 +203,47 @@ __global__ void __launch_bounds__(OS_BLOCK, OS_ITEMS >= 16 ? 3 : (OS_ITEMS >= 12
   __syncthreads();
   if (S.bail) return;
 
-  // Rank: warp-striped items, item k of lane l at warp*512 + k*32 + l, so
-  // the order (warp, k, lane) is the input order inside the tile.
+  // Warp-striped items: item k of lane l at warp*32*ITEMS + k*32 + l, so
+  // the order (warp, k, lane) is the input order inside the tile. Items
+  // past the end read as all ones: they take the largest digit and come
+  // last in the tile.
   uint64_t key[OS_ITEMS];
   uint32_t pos[OS_ITEMS];
-  uint16_t *wh = S.whist[warp];
-  uint32_t *mt = S.match[warp];
-  const uint32_t lt = lanemask_lt();
   const uint32_t dmax = (1u << a.bits) - 1u;
 #pragma unroll
   for (int k = 0; k < OS_ITEMS; ++k) {
     const uint32_t li = warp * (32 * OS_ITEMS) + k * 32 + lane;
-    const bool valid = li < count;
-    key[k] = valid ? S.keys[li] : ~0ull;
-    // Items past the end take the largest digit and come last in the tile.
-    const uint32_t d = valid ? digit_of(key[k], a.shift, a.bits) : dmax;
-    pos[k] = warp_rank_digit(d, mt, wh, lane, lt);
+    key[k] = li < count ? S.keys[li] : ~0ull;
   }
+  // Early counts: the tile's digit histogram by shared-memory atomics
+  // (independent, so cheap), published before the ranking so that the
+  // successors' look-backs find this tile's aggregate while it ranks.
+#pragma unroll
+  for (int k = 0; k < OS_ITEMS; ++k) {
+    const uint32_t li = warp * (32 * OS_ITEMS) + k * 32 + lane;
+    if (li < count) atomicAdd(&S.count[digit_of(key[k], a.shift, a.bits)], 1u);
+  }
+  __syncthreads();
+  const uint32_t d = tid;  // thread d owns digit d and its status word
+  const uint32_t mine = S.count[d];
+  uint64_t *st = a.status + (uint64_t)tile * RADIX + d;
+  if (a.inject && tile == 0) {
+    // Test hook: this tile never publishes, so the next tile's wait expires.
+    if (d == 0) S.bail = 1;
+  } else {
+    status_store(st, status_word(a.epoch, tile == 0 ? ST_INC : ST_AGG, mine));
+  }
+
+  // Rank within the tile: stable, by per-warp peer masks and counts.
+  uint16_t *wh = S.whist[warp];
+  uint32_t *mt = S.match[warp];
+  const uint32_t lt = lanemask_lt();
+#pragma unroll
+  for (int k = 0; k < OS_ITEMS; ++k)
+    pos[k] = warp_rank_digit(digit_of(key[k], a.shift, a.bits), mt, wh, lane, lt);
   __syncthreads();
 
   // Thread d: counts of digit d per warp -> per-warp exclusive prefixes.
-  const uint32_t d = tid;
   uint32_t total = 0;
 #pragma unroll
   for (int w = 0; w < OS_WARPS; ++w) {
@@ -229,28 +251,23 @@ __global__ void __launch_bounds__(OS_BLOCK, OS_ITEMS >= 16 ? 3 : (OS_ITEMS >= 12
     S.whist[w][d] = (uint16_t)total;
     total += c;
   }
-  const uint32_t invalid = OS_TILE - count;
-  const uint32_t mine = total - (d == dmax ? invalid : 0u);  // this tile's real count
   uint32_t tile_total;
   const uint32_t start = block_exclusive<OS_BLOCK>(total, OpAdd(), 0u, S.tmp, tile_total);
   S.start[d] = start;
 
-  // Publish and look back (thread d owns the status word of digit d).
-  uint64_t *st = a.status + (uint64_t)tile * RADIX + d;
-  if (a.inject && tile == 0) {
-    // Test hook: this tile never publishes, so the next tile's wait expires.
-    if (d == 0) S.bail = 1;
-  } else if (tile == 0) {
-    status_store(st, status_word(a.epoch, ST_INC, mine));
-    S.goff[d] = a.digit_base[d] - start;
-  } else {
-    status_store(st, status_word(a.epoch, ST_AGG, mine));
-    uint32_t excl = 0;
-    if (look_back_w<LB_WINDOW>(a.status, RADIX, d, tile, a.epoch, OpAdd(), excl, a.ctrl, a.spin_limit)) {
-      status_store(st, status_word(a.epoch, ST_INC, excl + mine));
-      S.goff[d] = a.digit_base[d] + excl - start;
+  // Look back over the predecessors (their aggregates were published early).
+  if (!S.bail) {
+    if (tile == 0) {
+      S.goff[d] = a.digit_base[d] - start;
     } else {
-      S.bail = 1;
+      uint32_t excl = 0;
+      if (look_back_w<LB_WINDOW>(a.status, RADIX, d, tile, a.epoch, OpAdd(), excl, a.ctrl,
+                                 a.spin_limit)) {
+        status_store(st, status_word(a.epoch, ST_INC, excl + mine));
+        S.goff[d] = a.digit_base[d] + excl - start;
+      } else {
+        S.bail = 1;
+      }
     }
   }
   __syncthreads();
