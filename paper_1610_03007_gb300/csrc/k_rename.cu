@@ -42,8 +42,11 @@ constexpr int RN_WARPS = RN_BLOCK / 32;
 static_assert(RN_TILE == RENAME_TILE, "tile size mismatch");
 
 struct RnSmem {
+  // Loading: the tile's keys and values; writing: staged queued updates
+  // (keys) and, in round 0, the SA entries by tile index (vals).
   uint64_t keys[RN_TILE + RN_TILE / 16];  // element e at e + e/16 (no bank conflicts)
   uint32_t vals[RN_TILE + RN_TILE / 32];  // element e at e + e/32
+  uint64_t surv[RN_TILE];                 // staged next-list entries of the survivors
   uint64_t prev_key, next_key;
   uint32_t prev_val, next_val;
   uint32_t tmp[RN_WARPS + 1];
@@ -54,7 +57,7 @@ struct RnSmem {
 __device__ __forceinline__ uint32_t kidx(uint32_t e) { return e + (e >> 4); }
 __device__ __forceinline__ uint32_t vidx(uint32_t e) { return e + (e >> 5); }
 
-// 64 registers: 4 blocks of 256 threads per SM (26 KB of shared memory each).
+// 64 registers: 4 blocks of 256 threads per SM (42 KB of shared memory each).
 __global__ void __launch_bounds__(RN_BLOCK, 4) k_rename(RenameArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   RnSmem &S = *reinterpret_cast<RnSmem *>(smem_raw);
@@ -184,13 +187,22 @@ __global__ void __launch_bounds__(RN_BLOCK, 4) k_rename(RenameArgs a) {
     }
     S.upd_base = S.upd_local ? atomicAdd(&a.ctrl->rc.upd, S.upd_local) : 0u;
   }
+  // Outputs are staged in shared memory and written with consecutive
+  // addresses afterwards: queued updates in the keys area, survivors' list
+  // entries in `surv`, and (round 0, where a unique item's name is its own
+  // position in the sorted order) SA entries by tile index in the vals area.
+  uint64_t *st_upd = S.keys;
+  uint32_t *st_sa = S.vals;
+  if (a.round0)
+    for (uint32_t e = tid; e < count; e += RN_BLOCK) st_sa[e] = NO_NAME;
   __syncthreads();
-  uint32_t run_upd = S.upd_base + my_upd;
   const uint32_t m_off = __ldg(a.off_in), g_off = __ldg(a.off_in + 1);
 
+  uint32_t run_upd = my_upd;
   uint32_t run_head = S.carry[0] > ex_head ? S.carry[0] : ex_head;
-  uint32_t run_surv = m_off + S.carry[1] + ex_surv;
+  uint32_t run_surv = ex_surv;
   uint32_t run_hs = g_off + S.carry[2] + ex_hs;
+  const uint32_t surv0 = m_off + S.carry[1];
 #pragma unroll
   for (int k = 0; k < RN_ITEMS; ++k) {
     if (l0 + k < count) {
@@ -212,7 +224,7 @@ __global__ void __launch_bounds__(RN_BLOCK, 4) k_rename(RenameArgs a) {
       if (f[k] && f[k + 1]) {
         // Unique: its name is its rank, final (Algorithm 5 discards it). SA
         // holds the index local to the suffix's own text.
-        a.upd[run_upd++] = ((uint64_t)head << 32) | ip;
+        st_upd[run_upd++] = ((uint64_t)head << 32) | ip;
         uint32_t local = ip;
         if (a.S > 1) {
           if (a.round0) {
@@ -222,19 +234,31 @@ __global__ void __launch_bounds__(RN_BLOCK, 4) k_rename(RenameArgs a) {
             local = local_index(ip, a.seg_off, a.S);
           }
         }
-        a.sa[head] = local;
+        if (a.round0)
+          st_sa[l0 + k] = local;  // head == j here
+        else
+          a.sa[head] = local;
       } else {
         // Survivors get their names, and their ISA entries, once the group
         // sizes are known (k_classify, k_apply_names).
         if (f[k]) {
           ++run_hs;
-          a.gstart_out[run_hs - 1] = run_surv;
+          a.gstart_out[run_hs - 1] = surv0 + run_surv;
           a.ghead_out[run_hs - 1] = head;
           a.gold_out[run_hs - 1] = a.round0 ? NO_NAME : __ldg(a.old_in + g);
         }
-        a.act_out[run_surv] = ((uint64_t)(run_hs - 1) << 32) | ip;
+        S.surv[run_surv] = ((uint64_t)(run_hs - 1) << 32) | ip;
         ++run_surv;
       }
+    }
+  }
+  __syncthreads();
+  for (uint32_t e = tid; e < S.upd_local; e += RN_BLOCK) a.upd[S.upd_base + e] = st_upd[e];
+  for (uint32_t e = tid; e < tot_surv; e += RN_BLOCK) a.act_out[surv0 + e] = S.surv[e];
+  if (a.round0) {
+    for (uint32_t e = tid; e < count; e += RN_BLOCK) {
+      const uint32_t v = st_sa[e];
+      if (v != NO_NAME) a.sa[base + e] = v;
     }
   }
 }
