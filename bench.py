@@ -49,6 +49,24 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def max_over_ranks(value: float, distributed: bool) -> float:
+    """The largest of every rank's value (the slowest replica's time); the
+    value itself on a single process. Runs on the gloo group, host side."""
+    if not distributed:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replicas_value(n_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job input MB/s: every rank built its own n-character text in at
+    most ms milliseconds."""
+    return n_per_rank * world / (ms * 1e-3) / 1e6
+
+
 def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
         int(os.environ.get("LOCAL_RANK", "0"))
@@ -265,12 +283,7 @@ def run_plain(args):
             a["bytes"] += v["bytes"]
     ev1.record(stream)
     torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if pg:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, pg is not None)
     clocks = sampler.stop()
     stats = st
 
@@ -344,7 +357,7 @@ def run_plain(args):
     ratio = ncu_traffic(dname)
     avg_bytes = d["bytes"] / max(d["launches"], 1)
     traffic = ratio * avg_bytes if ratio is not None else None
-    value = n * world / (ms * 1e-3) / 1e6
+    value = replicas_value(n, world, ms)
     path_gbs = bytes_model / args.steps / (ms * 1e-3) / 1e9
     line = {
         "metric": "input MB/s suffix-sorted", "value": value, "unit": "MB/s",
