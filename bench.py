@@ -26,6 +26,7 @@ import platform
 import re
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -80,7 +81,7 @@ class ClockSampler:
 
     def __init__(self, gpu_index: int):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"gbsa_clocks_{os.getpid()}.csv")
         self.gpu = gpu_index
 
     def start(self):
