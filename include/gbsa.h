@@ -331,6 +331,27 @@ size_t sa_lcp_workspace_bytes(uint64_t n);
 sa_status sa_lcp(const uint8_t *text, uint64_t n, const uint32_t *sa, uint32_t *lcp_out,
                  void *workspace, size_t ws_bytes, gbsa_stream_t stream);
 
+/* ---- DC3 (difference cover modulo 3) -----------------------------------
+ * The suffix array by the skew algorithm (Karkkainen and Sanders; the
+ * paper's Section 3, Algorithms 7-10, gives its distributed form): the
+ * suffixes at positions i mod 3 != 0 are ranked by recursion on the string
+ * of their triples' names, those at i mod 3 = 0 are sorted by (T[i], rank
+ * of i + 1), and the two are merged. Same result as sa_build.
+ * text        : DEVICE, n bytes, read only.
+ * sa_out      : DEVICE, n uint32, written with SA.
+ * trace_names : DEVICE or NULL; if set, n0 + n2 uint32 (n0 = (n+2)/3,
+ *               n2 = n/3) are written: the top level's recursion string,
+ *               the 1-based names of the triples at positions 1 mod 3
+ *               (with the position n itself when n mod 3 = 1), then at
+ *               positions 2 mod 3.
+ * Memory comes from the library's stream-ordered pool; the call
+ * synchronises `stream` once per recursion level and before returning.
+ * Returns SA_ERR_INVALID_ARG for a NULL text or sa_out with n > 0,
+ * SA_ERR_TOO_LARGE for n > SA_MAX_N, SA_ERR_OOM if memory runs out.
+ * n = 0 writes nothing. */
+sa_status sa_build_dc3(const uint8_t *text, uint64_t n, uint32_t *sa_out, uint32_t *trace_names,
+                       gbsa_stream_t stream);
+
 /* Human-readable name of a status code (static string). */
 const char *sa_status_string(sa_status s);
 

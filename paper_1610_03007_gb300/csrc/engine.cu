@@ -782,6 +782,11 @@ sa_status run_with_workspace(Build &B, void *workspace, size_t ws_bytes) {
 }
 
 }  // namespace
+
+// The library's private stream-ordered pool, for the other entry points.
+cudaError_t library_pool_alloc(void **p, size_t bytes, cudaStream_t st) {
+  return pool_alloc(p, bytes, st);
+}
 }  // namespace gbsa
 
 using namespace gbsa;

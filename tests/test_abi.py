@@ -72,6 +72,10 @@ def test_host_side_argument_checks(lib):
     assert lib.sa_lcp(256, 100, 256, 256, 257, 1 << 20, None) == 1
     assert lib.sa_lcp(None, 0, None, None, None, 0, None) == 0
     assert lib.sa_lcp_workspace_bytes(1000) >= 8000
+    # DC3: NULL arrays with n > 0, n above 2^31, n = 0 (no GPU work)
+    assert lib.sa_build_dc3(None, 5, None, None, None) == 1
+    assert lib.sa_build_dc3(8, (1 << 31) + 1, 8, None, None) == 2
+    assert lib.sa_build_dc3(None, 0, None, None, None) == 0
 
 
 def test_workspace_model(lib):
