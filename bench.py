@@ -332,6 +332,23 @@ def run_plain(args):
     lcp_ms = b0.elapsed_time(b1) / 3
     del sa_dev, lcp_buf, lcp_ws
 
+    # The same suffix array by DC3 (sa_build_dc3), for comparison.
+    dc3_sa = torch.empty(n, dtype=torch.int32, device=dev)
+
+    def dc3_call():
+        rc = lib.sa_build_dc3(text.data_ptr(), n, dc3_sa.data_ptr(), None, stream.cuda_stream)
+        if rc != 0:
+            raise RuntimeError(f"sa_build_dc3 failed: {rc}")
+
+    dc3_call()
+    b0.record(stream)
+    for _ in range(2):
+        dc3_call()
+    b1.record(stream)
+    torch.cuda.synchronize()
+    dc3_ms = b0.elapsed_time(b1) / 2
+    del dc3_sa
+
     # End to end through the host entry point: pinned host text in, host SA
     # out, copies inside the timed region.
     h_text = torch.from_numpy(t_host).pin_memory()
@@ -396,6 +413,8 @@ def run_plain(args):
                 "gbs": 30.0 * n / (lcp_ms * 1e-3) / 1e9,
                 "frac": 30.0 * n / (lcp_ms * 1e-3) / 1e9 / hbm,
                 "note": "sa_lcp on the built SA, outside the timed step"},
+        "dc3": {"ms": dc3_ms, "value": n / (dc3_ms * 1e-3) / 1e6, "unit": "MB/s",
+                "note": "the same text by sa_build_dc3 (skew algorithm), outside the timed step"},
     }
     line["cpu_baseline"] = cpu_baseline() if (world == 1 and not args.no_cpu) else None
     print(json.dumps(line), flush=True)

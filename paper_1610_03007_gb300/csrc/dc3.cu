@@ -17,10 +17,11 @@
 //   5. S12 (from SA_R, the dummy dropped) and S0 are merged with the skew
 //      comparison: for i = 1 mod 3 compare (t[i], rank(i+1)); for
 //      i = 2 mod 3 compare (t[i], t[i+1], rank(i+2)).
-// The merge is merge path: each block finds its output range's split by a
-// binary search, stages both input ranges with the comparison data of every
-// element (character pairs and ranks) in shared memory, and each thread
-// merges 4 outputs.
+// The merge is merge path: the elements of both inputs are first written out
+// in order with their comparison data (character pair, neighbours' ranks);
+// each block finds its output range's split by a binary search over those
+// arrays, stages both input slices in shared memory, and each thread merges
+// 4 outputs.
 //
 // Level 0 reads the 8-bit text as t[i] = T[i] + 1 (K = 256), so 0 is the
 // end of text, smaller than every character (Section 2's order).
@@ -80,16 +81,18 @@ __global__ void k_dc3_rekey(const uint32_t *__restrict__ t, uint32_t m, uint32_t
   }
 }
 
-// flags[k] = 1 where the triple of vals[k] differs from its predecessor's.
+// flags[k] = 1 where the triple of vals[k] differs from its predecessor's:
+// the sorted keys hold the whole triple (two_stage = 0) or its first two
+// names, the third then read from t.
 __global__ void k_dc3_flags(const uint32_t *__restrict__ t, uint32_t m,
-                            const uint32_t *__restrict__ vals, uint32_t *__restrict__ flags) {
+                            const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                            int two_stage, uint32_t *__restrict__ flags) {
   for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
        k += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t p = vals[k];
     uint32_t f = 1;
     if (k > 0) {
-      const uint32_t q = vals[k - 1];
-      f = (t[p] != t[q] || t[p + 1] != t[q + 1] || t[p + 2] != t[q + 2]) ? 1u : 0u;
+      f = keys[k] != keys[k - 1] ? 1u : 0u;
+      if (!f && two_stage) f = t[vals[k] + 2] != t[vals[k - 1] + 2] ? 1u : 0u;
     }
     flags[k] = f;
   }
@@ -238,6 +241,7 @@ struct MergeArgs {
   const uint32_t *s0;    // positions 0 mod 3 in suffix order
   uint32_t n, n0, skip;  // skip: 1 if SA_R starts with the dummy position
   uint32_t na, nb;       // |S12| (dummy dropped), |S0|
+  Elt *ea, *eb;          // the two inputs' elements, in order (built by k_dc3_elts)
   uint32_t *sa;          // out: n positions
 };
 
@@ -251,12 +255,23 @@ __device__ __forceinline__ Elt make_elt(const MergeArgs &a, uint32_t p) {
   return e;
 }
 
-__device__ __forceinline__ Elt elt_a(const MergeArgs &a, uint32_t k) {
-  const uint32_t s = a.sa12[a.skip + k];
-  return make_elt(a, s < a.n0 ? 3u * s + 1u : 3u * (s - a.n0) + 2u);
+// The elements of both inputs with their comparison data, in order: the
+// gathers happen once, in parallel, and the merge reads contiguous arrays.
+__global__ void k_dc3_elts(MergeArgs a) {
+  const uint64_t total = (uint64_t)a.na + a.nb;
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    if (k < a.na) {
+      const uint32_t s = a.sa12[a.skip + k];
+      a.ea[k] = make_elt(a, s < a.n0 ? 3u * s + 1u : 3u * (s - a.n0) + 2u);
+    } else {
+      a.eb[k - a.na] = make_elt(a, a.s0[k - a.na]);
+    }
+  }
 }
 
-__device__ __forceinline__ Elt elt_b(const MergeArgs &a, uint32_t k) { return make_elt(a, a.s0[k]); }
+__device__ __forceinline__ Elt elt_a(const MergeArgs &a, uint32_t k) { return a.ea[k]; }
+__device__ __forceinline__ Elt elt_b(const MergeArgs &a, uint32_t k) { return a.eb[k]; }
 
 // Does the sample suffix x come before the suffix y = 0 mod 3?
 __device__ __forceinline__ bool before(const Elt &x, const Elt &y) {
@@ -408,7 +423,7 @@ struct Dc3 {
         k_dc3_rekey<<<grid(n02), DC_BLOCK, 0, st>>>(t, n02, b, 0, vals, keys);
         if ((s = ok()) != SA_OK || (s = sort(keys, vals, n02, 2 * b)) != SA_OK) return s;
       }
-      k_dc3_flags<<<grid(n02), DC_BLOCK, 0, st>>>(t, n02, vals, tmp);
+      k_dc3_flags<<<grid(n02), DC_BLOCK, 0, st>>>(t, n02, keys, vals, 3 * b > 64 ? 1 : 0, tmp);
       if ((s = ok()) != SA_OK || (s = scan(tmp, tmp, n02, sums)) != SA_OK) return s;
       if (cudaMemsetAsync(R, 0, ((size_t)n02 + 3) * 4, st) != cudaSuccess) return SA_ERR_CUDA;
       k_dc3_scatter_names<<<grid(n02), DC_BLOCK, 0, st>>>(n02, n0, vals, tmp, R);
@@ -455,6 +470,8 @@ struct Dc3 {
     ma.na = n02 - ma.skip;
     ma.nb = n0;
     ma.sa = sa;
+    if ((s = sc.get(&ma.ea, ma.na)) != SA_OK || (s = sc.get(&ma.eb, ma.nb)) != SA_OK) return s;
+    k_dc3_elts<<<grid((uint64_t)ma.na + ma.nb), DC_BLOCK, 0, st>>>(ma);
     k_dc3_merge<<<(unsigned)(((uint64_t)n + MG_TILE - 1) / MG_TILE), DC_BLOCK, 0, st>>>(ma);
     return ok();
   }
