@@ -294,7 +294,7 @@ void sa_server_destroy(sa_server *s);
 
 /* ---- Burrows-Wheeler transform from the suffix array ------------------
  * The direct consumer of SA named as future work at the end of the paper
- * (Section 6); BWT[r] = T[SA[r] - 1] by the definitions of Section 2.
+ * (Section 3, the Conclusion); BWT[r] = T[SA[r] - 1] by the definitions of Section 2.
  * Rows are those of T$ (n + 1): row 0 is the suffix $ alone, preceded by
  * T[n - 1]; row r >= 1 is the suffix sa[r - 1], preceded by
  * T[sa[r - 1] - 1], except the row whose suffix is T itself, which holds $
@@ -312,7 +312,7 @@ sa_status sa_bwt(const uint8_t *text, uint64_t n, const uint32_t *sa, uint8_t *b
                  uint64_t *primary_out, gbsa_stream_t stream);
 
 /* ---- LCP array from the suffix array -----------------------------------
- * The other direct consumer of SA named as future work (Section 6):
+ * The other direct consumer of SA named as future work (Section 3):
  * lcp_out[0] = 0 and, for j >= 1, lcp_out[j] = the length of the longest
  * common prefix of the suffixes sa[j-1] and sa[j] (Section 2's order).
  * Computed in the permuted form of Kasai et al.'s algorithm (Phi, PLCP).
@@ -333,7 +333,7 @@ sa_status sa_lcp(const uint8_t *text, uint64_t n, const uint32_t *sa, uint32_t *
 
 /* ---- DC3 (difference cover modulo 3) -----------------------------------
  * The suffix array by the skew algorithm (Karkkainen and Sanders; the
- * paper's Section 3, Algorithms 7-10, gives its distributed form): the
+ * paper's Section 2.2, Algorithm 7, gives its distributed form): the
  * suffixes at positions i mod 3 != 0 are ranked by recursion on the string
  * of their triples' names, those at i mod 3 = 0 are sorted by (T[i], rank
  * of i + 1), and the two are merged. Same result as sa_build.

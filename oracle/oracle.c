@@ -325,7 +325,7 @@ int oracle_bwt_invert(const uint8_t *bwt, int64_t n, int64_t primary, uint8_t *o
   return 0;
 }
 
-/* ---- LCP array (a consumer of SA, Section 6), by its definition -------- */
+/* ---- LCP array (a consumer of SA, Section 3), by its definition -------- */
 
 int64_t oracle_lcp_pair(const uint8_t *T, int64_t n, int64_t a, int64_t b) {
   int64_t l = 0;

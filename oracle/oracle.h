@@ -94,7 +94,7 @@ int oracle_bwt_invert(const uint8_t *bwt, int64_t n, int64_t primary, uint8_t *o
 
 /* Longest common prefix of the suffixes T[a,n) and T[b,n): the number of
  * leading characters they share, compared one by one (Section 2's suffix
- * order; the LCP array of Section 6's future work is built from it). */
+ * order; the LCP array of Section 3's future work is built from it). */
 int64_t oracle_lcp_pair(const uint8_t *T, int64_t n, int64_t a, int64_t b);
 
 /* LCP array by its definition: lcp[0] = 0 and, for j >= 1, lcp[j] =

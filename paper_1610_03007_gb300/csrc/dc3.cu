@@ -1,5 +1,5 @@
 // DC3 (the skew algorithm of Karkkainen and Sanders, CPM 2003; the paper's
-// Section 3, Algorithms 7-10, gives its distributed form): the suffix array
+// Section 2.2, Algorithm 7, gives its distributed form): the suffix array
 // by recursion on the difference cover D3 = {1, 2}.
 //
 // One level, on a text t of n integers in [1, K] padded with three zeros:

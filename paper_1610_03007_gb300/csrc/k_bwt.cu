@@ -1,5 +1,5 @@
 // Burrows-Wheeler transform from the suffix array: the direct consumer of
-// SA named as future work at the end of the paper (Section 6), and the
+// SA named as future work at the end of the paper (Section 3), and the
 // identity BWT[r] = T[SA[r] - 1] of the definition (Section 2: SA orders
 // the suffixes; the BWT lists the character preceding each one).
 //

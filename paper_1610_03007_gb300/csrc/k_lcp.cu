@@ -1,5 +1,5 @@
 // LCP array from the suffix array: a direct consumer of SA named as future
-// work at the end of the paper (Section 6). lcp[0] = 0 and, for j >= 1,
+// work at the end of the paper (Section 3). lcp[0] = 0 and, for j >= 1,
 // lcp[j] is the longest common prefix of the suffixes SA[j-1] and SA[j]
 // (Section 2's suffix order).
 //
