@@ -6,7 +6,8 @@ two share no code, headers or helpers.
 
 ctypes bindings over oracle.c (plain sequential C, integer only), which
 follows Section 2 (definition of SA/ISA and the $ sentinel) and Section 2.1
-(prefix doubling: Algorithms 1, 2, 4, 5 and 6) of Bingmann, Gog & Kurpicz,
+(prefix doubling: Algorithms 1, 2, 4, 5 and 6, and its a-fold form of
+the Prefix Quadrupling subsection) of Bingmann, Gog & Kurpicz,
 "Scalable Construction of Text Indexes" (arXiv 1610.03007).
 """
 from __future__ import annotations
@@ -40,7 +41,7 @@ def build(mutant: int = 0, force: bool = False) -> str:
     return out
 
 
-MUTANTS = (1, 2, 3, 4, 5, 6, 7, 8, 9, 10)
+MUTANTS = (1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12)
 
 
 class Oracle:
@@ -53,6 +54,8 @@ class Oracle:
         lib.oracle_naive_sa.restype = None
         lib.oracle_pd_sa.argtypes = [p, i64, i64, p, p, p, i64]
         lib.oracle_pd_sa.restype = i64
+        lib.oracle_pq_sa.argtypes = [p, i64, i64, i64, p, p, p, i64]
+        lib.oracle_pq_sa.restype = i64
         lib.oracle_check_sa.argtypes = [p, i64, p, p]
         lib.oracle_check_sa.restype = ctypes.c_int
         lib.oracle_check_permutation.argtypes = [p, i64, p]
@@ -87,8 +90,9 @@ class Oracle:
         self._lib.oracle_naive_sa(T.ctypes.data, T.size, sa.ctypes.data)
         return sa
 
-    def pd_sa(self, t, h0: int = 1, trace_cap: int = 0):
-        """Prefix doubling with discarding (Section 2.1, Algorithms 1/2/4/5/6).
+    def pd_sa(self, t, h0: int = 1, trace_cap: int = 0, a: int = 2):
+        """Prefix doubling with discarding (Section 2.1, Algorithms 1/2/4/5/6);
+        a = 3 or 4 ranks a-tuples of names per round (Prefix Quadrupling).
 
         Returns (sa, isa, rounds, trace) where trace has shape
         (min(rounds+1, trace_cap), n): names after the initial naming and
@@ -98,10 +102,15 @@ class Oracle:
         sa = np.empty(n, dtype=np.uint32)
         isa = np.empty(n, dtype=np.uint32)
         trace = np.zeros((max(trace_cap, 0), n), dtype=np.uint32)
-        rounds = self._lib.oracle_pd_sa(T.ctypes.data, n, h0, sa.ctypes.data,
-                                        isa.ctypes.data,
-                                        trace.ctypes.data if trace_cap > 0 else None,
-                                        trace_cap)
+        tp = trace.ctypes.data if trace_cap > 0 else None
+        if a == 2:
+            rounds = self._lib.oracle_pd_sa(T.ctypes.data, n, h0, sa.ctypes.data,
+                                            isa.ctypes.data, tp, trace_cap)
+        else:
+            rounds = self._lib.oracle_pq_sa(T.ctypes.data, n, h0, a, sa.ctypes.data,
+                                            isa.ctypes.data, tp, trace_cap)
+            if rounds < 0:
+                raise ValueError(f"multiplier a={a} outside [2, 4]")
         return sa, isa, int(rounds), trace[: min(rounds + 1, trace_cap)]
 
     def check_sa(self, t, sa) -> tuple[int, int]:

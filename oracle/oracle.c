@@ -67,21 +67,34 @@ static int qs_prefix_h(const void *x, const void *y, void *c) {
   return cmp_prefix(s->T, a, la, b, lb);
 }
 
-/* (partner name, position) of one suffix inside a group being refined. */
+/* The partner names r[0..a-2] of one suffix (the names of i + h, i + 2h,
+ * ..., each shifted by one, 0 past the end) and its position, for one
+ * suffix inside a group being refined. */
+#define ORACLE_MAX_A 4
 typedef struct {
-  uint64_t r2;
+  uint64_t r[ORACLE_MAX_A - 1];
   uint32_t pos;
-} name_pair;
+} name_tuple;
 
-static int qs_pair(const void *x, const void *y) {
-  const name_pair *a = (const name_pair *)x, *b = (const name_pair *)y;
-  return (a->r2 > b->r2) - (a->r2 < b->r2);
+/* Lexicographic order of the partner tuples (the group shares the first
+ * name, so only the partners are compared). Unused entries are 0. */
+static int qs_tuple(const void *x, const void *y) {
+  const name_tuple *a = (const name_tuple *)x, *b = (const name_tuple *)y;
+  for (int k = 0; k < ORACLE_MAX_A - 1; ++k)
+    if (a->r[k] != b->r[k]) return a->r[k] < b->r[k] ? -1 : 1;
+  return 0;
 }
 
 int64_t oracle_pd_sa(const uint8_t *T, int64_t n, int64_t h0, uint32_t *sa,
                      uint32_t *isa_out, uint32_t *trace, int64_t trace_cap) {
+  return oracle_pq_sa(T, n, h0, 2, sa, isa_out, trace, trace_cap);
+}
+
+int64_t oracle_pq_sa(const uint8_t *T, int64_t n, int64_t h0, int64_t a, uint32_t *sa,
+                     uint32_t *isa_out, uint32_t *trace, int64_t trace_cap) {
   if (n <= 0) return 0;
   if (h0 < 1) h0 = 1;
+  if (a < 2 || a > ORACLE_MAX_A) return -1;
   uint32_t *isa = isa_out ? isa_out : (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
 
   /* Initial names (Algorithm 1, first lines; Algorithm 5, first four lines):
@@ -103,7 +116,7 @@ int64_t oracle_pd_sa(const uint8_t *T, int64_t n, int64_t h0, uint32_t *sa,
   }
   if (trace && trace_cap > 0) memcpy(trace, isa, (size_t)n * sizeof(uint32_t));
 
-  name_pair *pairs = (name_pair *)malloc((size_t)n * sizeof(name_pair));
+  name_tuple *tup = (name_tuple *)malloc((size_t)n * sizeof(name_tuple));
   uint32_t *fresh = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
   int64_t rounds = 0;
   int64_t h = h0; /* characters resolved by the current names */
@@ -129,33 +142,44 @@ int64_t oracle_pd_sa(const uint8_t *T, int64_t n, int64_t h0, uint32_t *sa,
       if (ge - gs > 1) {
         any = 1;
         /* Partner names through the ISA (Algorithm 4): the name of suffix
-         * i + h if it exists, shifted by one so that the sentinel 0 sorts
-         * below every real name. */
+         * i + k*h for k = 1 .. a-1 (a = 2: the pair of Algorithm 4; a = 4:
+         * the rank quadruple of prefix quadrupling) if it exists, shifted
+         * by one so that the sentinel 0 sorts below every real name. */
         for (int64_t j = gs; j < ge; ++j) {
           uint32_t i = sa[j];
+          memset(&tup[j], 0, sizeof(name_tuple));
+          for (int64_t k = 1; k < a; ++k) {
 #if ORACLE_MUTANT == 1
-          uint64_t r2 = (i + h < n) ? (uint64_t)isa[i + h] : 0; /* literal sentinel */
+            int64_t at = i + k * h;
+            uint64_t r = (at < n) ? (uint64_t)isa[at] : 0; /* literal sentinel */
 #elif ORACLE_MUTANT == 2
-          int64_t off = h / 2 > 0 ? h / 2 : 1; /* the prose's i + 2^(k-1) */
-          uint64_t r2 = (i + off < n) ? (uint64_t)isa[i + off] + 1 : 0;
+            int64_t off = h / 2 > 0 ? h / 2 : 1; /* the prose's i + 2^(k-1) */
+            int64_t at = i + k * off;
+            uint64_t r = (at < n) ? (uint64_t)isa[at] + 1 : 0;
 #elif ORACLE_MUTANT == 5
-          uint64_t r2 = (i + h < n) ? (uint64_t)isa[i + h] : (uint64_t)n + 1;
+            int64_t at = i + k * h;
+            uint64_t r = (at < n) ? (uint64_t)isa[at] : (uint64_t)n + 1;
+#elif ORACLE_MUTANT == 11
+            int64_t at = i + (k == 3 ? 2 : k) * h; /* mutant: last partner repeated */
+            uint64_t r = (at < n) ? (uint64_t)isa[at] + 1 : 0;
 #else
-          uint64_t r2 = (i + h < n) ? (uint64_t)isa[i + h] + 1 : 0;
+            int64_t at = i + k * h;
+            uint64_t r = (at < n) ? (uint64_t)isa[at] + 1 : 0;
 #endif
-          pairs[j].r2 = r2;
-          pairs[j].pos = i;
+            tup[j].r[k - 1] = r;
+          }
+          tup[j].pos = i;
         }
-        /* Sort the group by its partner names (the group shares r). */
-        qsort(pairs + gs, (size_t)(ge - gs), sizeof(name_pair), qs_pair);
+        /* Sort the group by its partner tuples (the group shares r). */
+        qsort(tup + gs, (size_t)(ge - gs), sizeof(name_tuple), qs_tuple);
         /* NameDiscarding (Algorithm 6, corrected): all members share the
          * old name r = group head; a new subgroup starts where the partner
-         * name changes; new name = r + (subgroup start - group start). */
-        uint32_t r = isa[pairs[gs].pos];
+         * tuple changes; new name = r + (subgroup start - group start). */
+        uint32_t r = isa[tup[gs].pos];
         int64_t sub = gs;
         for (int64_t j = gs; j < ge; ++j) {
-          if (j > gs && pairs[j].r2 != pairs[j - 1].r2) sub = j;
-          sa[j] = pairs[j].pos;
+          if (j > gs && qs_tuple(&tup[j], &tup[j - 1]) != 0) sub = j;
+          sa[j] = tup[j].pos;
 #if ORACLE_MUTANT == 4
           fresh[j] = r + (uint32_t)(sub - gs) + (sub > gs ? 1u : 0u);
 #else
@@ -187,11 +211,15 @@ int64_t oracle_pd_sa(const uint8_t *T, int64_t n, int64_t h0, uint32_t *sa,
         j = e;
       }
     }
-    h *= 2;
+#if ORACLE_MUTANT == 12
+    h *= 2; /* mutant: resolved length doubled whatever a is */
+#else
+    h *= a; /* the names now resolve a*h characters */
+#endif
     if (trace && rounds < trace_cap)
       memcpy(trace + rounds * n, isa, (size_t)n * sizeof(uint32_t));
   }
-  free(pairs);
+  free(tup);
   free(fresh);
   if (!isa_out) free(isa);
   return rounds;

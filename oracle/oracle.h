@@ -13,8 +13,10 @@
  * string up to length 14 against Python's own bytes ordering, the
  * invariants (permutation, ISA[SA[j]] = j, BWT inversion reproduces T),
  * the LCP array's textbook and closed-form values and brute force against
- * Python's own prefix comparison, and planted-mutant builds of this file,
- * each of which must fail a pin.
+ * Python's own prefix comparison, the per-round names of the a-fold
+ * variant against head ranks of a^k-length prefixes computed by brute
+ * force, and planted-mutant builds of this file, each of which must fail a
+ * pin.
  */
 #ifndef GBSA_ORACLE_H
 #define GBSA_ORACLE_H
@@ -58,6 +60,17 @@ void oracle_naive_sa(const uint8_t *T, int64_t n, uint32_t *sa);
  *  - all partner names of a round are read before any name of that round
  *    is rewritten. */
 int64_t oracle_pd_sa(const uint8_t *T, int64_t n, int64_t h0, uint32_t *sa,
+                     uint32_t *isa, uint32_t *trace, int64_t trace_cap);
+
+/* Prefix doubling generalised to a-fold growth (Section 2.1, Prefix
+ * Quadrupling): a round sorts each group by the tuple of the names of
+ * i + h, i + 2h, ..., i + (a-1)h (each + 1, 0 past the end), in place of
+ * the single partner name, so the resolved length grows from h to a*h; the
+ * comparison (lexicographic on the tuple) and NameDiscarding (a new
+ * subgroup where the tuple changes) are adapted accordingly, everything
+ * else is oracle_pd_sa, which is this function with a = 2. a in [2, 4];
+ * returns -1 for any other a, else the number of refinement rounds. */
+int64_t oracle_pq_sa(const uint8_t *T, int64_t n, int64_t h0, int64_t a, uint32_t *sa,
                      uint32_t *isa, uint32_t *trace, int64_t trace_cap);
 
 /* Checker of Burkhardt & Kaerkkaeinen (CPM 2003) for the definition above:

@@ -85,6 +85,9 @@ def pin_bruteforce(o, max_ab=12, max_4=6):
                 for h0 in (1, 2):
                     if list(o.pd_sa(t, h0=h0)[0]) != want:
                         bad.append(f"pd h0={h0} {t!r}")
+                for a in (3, 4):
+                    if list(o.pd_sa(t, h0=1, a=a)[0]) != want:
+                        bad.append(f"pq a={a} {t!r}")
                 if bad:
                     return bad
     return bad
@@ -210,8 +213,58 @@ def pin_lcp(o):
     return bad
 
 
+def head_ranks(t: bytes, H: int):
+    """Name of every suffix after resolving H characters, by definition:
+    the number of suffixes whose first H characters compare smaller (the
+    head rank of its group, Section 2's lexicographic names; a unique
+    suffix's head rank is its rank). Python's bytes order, no oracle code."""
+    import bisect
+    keys = [t[i:i + H] for i in range(len(t))]
+    order = sorted(keys)
+    return [bisect.bisect_left(order, k) for k in keys]
+
+
+def pin_multiplier(o):
+    """Prefix doubling and its a-fold form (Prefix Quadrupling): after round
+    k the names are the head ranks of the (h0 * a^k)-character prefixes, and
+    the rounds stop at the first k where those prefixes are all distinct."""
+    bad = []
+    g = read_golden("ex1_ex2_bdacbdacb.txt")
+    texts = [g["text"].encode(), b"a" * 37, b"ab" * 19, b"abaababaabaab", b"mississippi"]
+    rng = np.random.default_rng(11)
+    for n, sigma in ((60, 2), (90, 3), (150, 4), (120, 26)):
+        texts.append(bytes(rng.integers(97, 97 + sigma, n, dtype=np.uint8)))
+    texts.append(gen.text("zipf_repeats", 5, 200).tobytes())
+    texts.append(gen.text("dna", 6, 256).tobytes())
+    for t in texts:
+        n = len(t)
+        for a in (2, 3, 4):
+            for h0 in (1, 2, 3):
+                _, isa, rounds, trace = o.pd_sa(t, h0=h0, trace_cap=64, a=a)
+                want_rounds = 0
+                while len(set(t[i:i + h0 * a ** want_rounds] for i in range(n))) < n:
+                    want_rounds += 1
+                if rounds != want_rounds:
+                    bad.append(f"a={a} h0={h0} rounds {rounds} != {want_rounds} ({t[:12]!r})")
+                    continue
+                for k in range(rounds + 1):
+                    if list(trace[k]) != head_ranks(t, h0 * a ** k):
+                        bad.append(f"a={a} h0={h0} names after round {k} ({t[:12]!r})")
+                        break
+                if sorted(isa.tolist()) != list(range(n)):
+                    bad.append(f"a={a} h0={h0} final names not a permutation")
+    for n in (1, 2, 5, 16, 17, 64, 65, 1000):  # a^n: smallest k with h0 * a^k >= n
+        for a in (3, 4):
+            k = 0
+            while a ** k < n:
+                k += 1
+            if o.pd_sa(b"z" * n, h0=1, a=a)[2] != k:
+                bad.append(f"z^{n} a={a} rounds")
+    return bad
+
+
 PINS = [pin_examples, pin_closed_forms, pin_bruteforce, pin_random, pin_checker,
-        pin_bwt, pin_rank, pin_lcp]
+        pin_bwt, pin_rank, pin_lcp, pin_multiplier]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
@@ -241,3 +294,9 @@ def test_empty_and_tiny(orc):
     assert list(orc.pd_sa(b"ba")[0]) == [1, 0]
     assert list(orc.pd_sa(b"\x00\x00")[0]) == [1, 0]
     assert orc.check_sa(b"", np.zeros(0, dtype=np.uint32))[0] == 0
+    for a in (3, 4):
+        assert orc.pd_sa(b"", a=a)[0].size == 0
+        assert list(orc.pd_sa(b"x", a=a)[0]) == [0]
+        assert list(orc.pd_sa(b"ba", a=a)[0]) == [1, 0]
+    with pytest.raises(ValueError):
+        orc.pd_sa(b"abc", a=5)
