@@ -97,6 +97,14 @@ typedef struct {
    * and the per-kernel-class times, launch counts and algorithmic bytes are
    * returned in sa_stats (adds a few microseconds per launch). */
   uint32_t profile;
+  /* Growth factor a of the resolved prefix per round (Section 2.1, Prefix
+   * Quadrupling: substrings of length a^k instead of 2^k). Each round ranks
+   * the names of i, i + h, ..., i + (a-1)h, so h grows a-fold and fewer
+   * rounds run; 0 or 2 = doubling (default), 3 = tripling, 4 =
+   * quadrupling. Any other value: SA_ERR_INVALID_ARG. The SA and ISA are
+   * the same for every a; trace_isa holds the names after each round, at
+   * h0 * a^k resolved characters. */
+  uint32_t multiplier;
 } sa_options;
 
 /* Kernel classes of the per-kernel statistics. */

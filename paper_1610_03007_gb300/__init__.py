@@ -45,7 +45,7 @@ class Options(ctypes.Structure):
                 ("inject_stall", ctypes.c_uint32), ("trace_isa", ctypes.c_void_p),
                 ("trace_cap", ctypes.c_uint32), ("paper_names", ctypes.c_uint32),
                 ("refine_shape", ctypes.c_uint32), ("sort_items", ctypes.c_uint32),
-                ("profile", ctypes.c_uint32)]
+                ("profile", ctypes.c_uint32), ("multiplier", ctypes.c_uint32)]
 
 
 KERNEL_CLASSES = ("byte_hist", "pack", "digit_hist", "plan", "onesweep", "rename", "gather",
@@ -206,8 +206,11 @@ def sa_build(text, sa_out=None, stream=None):
 
 def sa_build_ex(text, *, isa=False, workspace=None, h0_chars=0, spin_limit=0,
                 inject_stall=0, trace_cap=0, paper_names=False, refine_shape=0, sort_items=0,
-                profile=False, stream=None):
+                profile=False, multiplier=0, stream=None):
     """sa_build with options. Returns (sa, isa or None, stats dict, trace or None).
+
+    multiplier: growth factor a of the resolved prefix per round (0 or 2:
+    doubling; 3, 4: tripling, quadrupling).
 
     workspace: a uint8 CUDA tensor of at least workspace_bytes(n) bytes, or
     None to let torch's caching allocator provide one."""
@@ -224,7 +227,8 @@ def sa_build_ex(text, *, isa=False, workspace=None, h0_chars=0, spin_limit=0,
     trace = torch.zeros((trace_cap, n), dtype=torch.int32, device=dev) if trace_cap else None
     opt = Options(h0_chars, spin_limit, inject_stall,
                   trace.data_ptr() if trace is not None and n else None, trace_cap,
-                  1 if paper_names else 0, refine_shape, sort_items, 1 if profile else 0)
+                  1 if paper_names else 0, refine_shape, sort_items, 1 if profile else 0,
+                  multiplier)
     st = Stats()
     rc = lib.sa_build_ex(t.data_ptr(), n, sa.data_ptr() if n else None,
                          isa_t.data_ptr() if isa_t is not None and n else None,
@@ -235,7 +239,7 @@ def sa_build_ex(text, *, isa=False, workspace=None, h0_chars=0, spin_limit=0,
 
 
 def sa_build_batched(texts, offsets, sa_out=None, workspace=None, stream=None, stats=False,
-                     profile=False, refine_shape=0, sort_items=0, h0_chars=0):
+                     profile=False, refine_shape=0, sort_items=0, h0_chars=0, multiplier=0):
     """SAs of many texts in one launch sequence.
 
     texts: 1-D uint8 CUDA tensor (the texts concatenated); offsets: host
@@ -253,7 +257,8 @@ def sa_build_batched(texts, offsets, sa_out=None, workspace=None, stream=None, s
     if workspace is None and N:
         workspace = torch.empty(wsb, dtype=torch.uint8, device=t.device)
     st = Stats()
-    opt = Options(h0_chars, 0, 0, None, 0, 0, refine_shape, sort_items, 1 if profile else 0)
+    opt = Options(h0_chars, 0, 0, None, 0, 0, refine_shape, sort_items, 1 if profile else 0,
+                  multiplier)
     rc = lib.sa_build_batched_ex(t.data_ptr(), off.ctypes.data, count,
                                  sa_out.data_ptr() if N else None,
                                  workspace.data_ptr() if workspace is not None else None,

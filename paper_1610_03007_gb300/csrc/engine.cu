@@ -9,6 +9,10 @@
 //   keys; small groups: tile-local refine (k_refine.cu); then the rename of
 //   the large groups, the queued ISA updates and the classification of the
 //   new groups.
+// With sa_options.multiplier a = 3 or 4 (Section 2.1, Prefix Quadrupling) a
+// round ranks the names of i, i + h, .., i + (a-1)h and h grows a-fold: the
+// sorts become two stable sorts (later partners, then group and first
+// partner) and the boundary tests compare the whole tuple.
 // The loop ends when no suffix is active (every name unique; the paper's
 // loop bound is one round short, so the count decides). SA is complete then:
 // each suffix wrote SA[name] = i when its name became unique.
@@ -48,7 +52,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 struct Layout {
   size_t ctrl, plan, hist, dbase, bytehist, code, segoff;
   size_t ka, kb, va, vb, act0, act1, upd, isa, gs0, gs1, gn0, gn1, gh0, gh1, gold;
-  size_t lg, loff, lbase, lold, tfirst, bcount;
+  size_t lg, loff, lbase, lold, tfirst, bcount, pm1;
   size_t st_sort, st_ren, total;
   size_t st_sort_bytes, st_ren_bytes;
   uint32_t max_groups, max_large, max_tiles;
@@ -92,6 +96,7 @@ Layout make_layout(uint64_t N, uint32_t S) {
   L.lbase = take((size_t)L.max_large * 4);
   L.lold = take((size_t)L.max_large * 4);
   L.bcount = take((size_t)BUCKET_BLOCKS_MAX * RADIX * 4);
+  L.pm1 = take(8);
   L.max_tiles = (uint32_t)((Nm + REFINE_MIN_NOMINAL - 1) / REFINE_MIN_NOMINAL);
   L.tfirst = take(((size_t)L.max_tiles + 1) * 4);
   const uint64_t ts = std::max<uint64_t>(1, (N + SORT_TILE_MIN - 1) / SORT_TILE_MIN);
@@ -205,6 +210,7 @@ struct Build {
   uint32_t *ghead[2] = {nullptr, nullptr}, *gold = nullptr;
   uint32_t *lg = nullptr, *loff = nullptr, *lbase = nullptr, *lold = nullptr, *tfirst = nullptr;
   uint32_t *bcount = nullptr;  // position-bucketing counts (BUCKET_BLOCKS_MAX x 256)
+  uint32_t *pm1 = nullptr;     // (passes, pass mask) of the first sort of an a-tuple round
   // launch bookkeeping
   uint32_t epoch = 0, slot = 0;
   uint32_t spin = DEFAULT_SPIN_LIMIT;
@@ -214,6 +220,7 @@ struct Build {
   uint32_t naming = NAMES_RETAIN;
   uint32_t shape = 0, nominal = 512;  // refine tile shape and window
   uint32_t sort_items = SORT_ITEMS_DEFAULT;  // keys per thread of the radix pass
+  uint32_t mult = 2;  // a: names ranked per round (2: doubling, 4: quadrupling)
   // per-kernel profiling (events on the build's stream)
   struct Rec {
     int cls, pass;
@@ -267,6 +274,7 @@ struct Build {
     lbase = at<uint32_t>(L.lbase);
     lold = at<uint32_t>(L.lold);
     bcount = at<uint32_t>(L.bcount);
+    pm1 = at<uint32_t>(L.pm1);
     tfirst = at<uint32_t>(L.tfirst);
     st_sort = at<uint64_t>(L.st_sort);
     st_ren = at<uint64_t>(L.st_ren);
@@ -300,14 +308,16 @@ struct Build {
   }
 
   // After a stream sync: fold the recorded launches into the statistics.
-  sa_status flush(uint32_t pass_mask, uint64_t rename_bytes_now) {
+  sa_status flush(uint32_t pass_mask, uint64_t rename_bytes_now, uint32_t mask1 = 0) {
     if (!prof || !stats) {
       recs.clear();
       evused = 0;
       return SA_OK;
     }
     for (const Rec &r : recs) {
-      if (r.cls == SA_K_ONESWEEP && !((pass_mask >> r.pass) & 1u)) continue;
+      if (r.cls == SA_K_ONESWEEP &&
+          !(((r.pass >= 32 ? mask1 : pass_mask) >> (r.pass & 31)) & 1u))
+        continue;
       float ms = 0.f;
       CK(cudaEventElapsedTime(&ms, r.a, r.b));
       stats->kernel_ms[r.cls] += ms;
@@ -339,7 +349,9 @@ struct Build {
 
   // Radix sort of (ka, va)[0, m) by the digits of spec; result where the
   // device plan says (plan->kfinal / vfinal).
-  sa_status sort(uint32_t m, const DigitSpec &spec, bool hist_ready = false) {
+  // chain 1: the first of the two sorts of an a-tuple round (its kept
+  // passes are copied to pm1 afterwards; profile records tag pass + 32).
+  sa_status sort(uint32_t m, const DigitSpec &spec, bool hist_ready = false, int chain = 0) {
     sa_status s = SA_OK;
     if (!hist_ready) {
       CK(cudaMemsetAsync(hist, 0, (size_t)spec.P * RADIX * 4, st));
@@ -368,10 +380,12 @@ struct Build {
       pa.spin_limit = spin;
       pa.inject = inject_pending ? 1u : 0u;
       pa.items = sort_items;
-      s = launch(SA_K_ONESWEEP, (int)p, 24ull * m, [&] { return launch_onesweep(pa, st); });
+      s = launch(SA_K_ONESWEEP, (int)p + 32 * chain, 24ull * m,
+                 [&] { return launch_onesweep(pa, st); });
       if (s != SA_OK) return s;
     }
     inject_pending = false;
+    if (chain == 1) CK(cudaMemcpyAsync(pm1, &ctrl->passes, 8, cudaMemcpyDeviceToDevice, st));
     return SA_OK;
   }
 
@@ -389,8 +403,10 @@ struct Build {
   // round; writes the next active list at the device-side offsets `off_in`.
   sa_status rename(uint32_t m, bool round0, uint32_t cb, uint32_t c0, uint32_t W,
                    const uint32_t *base_in, const uint32_t *old_in, uint32_t g_in, int out,
-                   const uint32_t *off_in) {
+                   const uint32_t *off_in, bool wide = false) {
     RenameArgs ra{};
+    ra.sec_buf[0] = wide ? ka : nullptr;
+    ra.sec_buf[1] = wide ? kb : nullptr;
     ra.plan = plan;
     ra.m = m;
     ra.round0 = round0 ? 1u : 0u;
@@ -523,13 +539,14 @@ struct Build {
     return 12ull * m + 12 * u + 8ull * surv + 12ull * groups;
   }
 
-  // Refine: 8 bytes read and a 4-byte gather per item, 8 bytes of group
-  // table per input group, 8 per survivor and per new group, 4 (SA) per
-  // unique item, 8 per queued update.
+  // Refine: 8 bytes read and a - 1 4-byte gathers per item, 8 bytes of
+  // group table per input group, 8 per survivor and per new group, 4 (SA)
+  // per unique item, 8 per queued update.
   static uint64_t refine_bytes(uint32_t m, uint32_t G, uint32_t surv, uint32_t groups,
-                               uint32_t upd_n) {
+                               uint32_t upd_n, uint32_t a) {
     const uint64_t u = m - surv;
-    return 12ull * m + 8ull * G + 8ull * surv + 8ull * groups + 4 * u + 8ull * upd_n;
+    return (8ull + 4ull * (a - 1)) * m + 8ull * G + 8ull * surv + 8ull * groups + 4 * u +
+           8ull * upd_n;
   }
 
   void record(uint32_t r, uint32_t m, const HostCtrl &hc, uint32_t kbits) {
@@ -554,6 +571,7 @@ struct Build {
     nominal = REFINE_SHAPE[shape].cap / 2;
     if (opt.sort_items == 8 || opt.sort_items == 12 || opt.sort_items == 16)
       sort_items = opt.sort_items;
+    mult = opt.multiplier ? opt.multiplier : 2;  // checked by the entry points
     // Clear what must start at zero; the ISA starts all-ones so every end
     // slot reads as the sentinel.
     CK(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
@@ -664,16 +682,51 @@ struct Build {
         ga.GL = GL;
         ga.h = (uint32_t)h;
         ga.W = W;
+        ga.mult = mult;
         ga.isa = isa;
         ga.isa_len = N + S + 1;
         ga.keys = ka;
         ga.vals = va;
-        s = launch(SA_K_GATHER, 0, 24ull * mL, [&] { return launch_gather_large(ga, st); });
+        // a > 2: the queued-update list and the next active list are free
+        // until the refine below, and hold the per-item keys until then.
+        ga.key1_stash = upd;
+        ga.sec_stash = act[nxt];
+        const uint64_t gb = mult == 2 ? 24ull * mL : (32ull + 4ull * (mult - 1) + 16ull) * mL;
+        s = launch(SA_K_GATHER, 0, gb, [&] { return launch_gather_large(ga, st); });
         if (s != SA_OK) return s;
-        bytes += 24ull * mL;
+        bytes += gb;
         kbits = W + (GL > 1 ? bits_for(GL - 1) : 0);
-        s = sort(mL, spec_for(kbits));
-        if (s != SA_OK) return s;
+        if (mult > 2) {
+          // LSD over the tuple: later partners first, then (group, r2).
+          s = sort(mL, spec_for(mult == 4 ? 2 * W : W), false, 1);
+          if (s != SA_OK) return s;
+          WideArgs wa{};
+          wa.plan = plan;
+          wa.m = m;
+          wa.mL = mL;
+          wa.GL = GL;
+          wa.W = W;
+          wa.act = act[cur];
+          wa.gstart = gstart[cur];
+          wa.lg = lg;
+          wa.loff = loff;
+          wa.key1_stash = upd;
+          wa.sec_stash = act[nxt];
+          wa.ka = ka;
+          wa.kb = kb;
+          wa.va = va;
+          wa.ctrl = ctrl;
+          s = launch(SA_K_GATHER, 1, 24ull * mL, [&] { return launch_wide_rekey(wa, st); });
+          if (s != SA_OK) return s;
+          s = sort(mL, spec_for(kbits));
+          if (s != SA_OK) return s;
+          s = launch(SA_K_GATHER, 2, 40ull * mL, [&] { return launch_wide_finish(wa, st); });
+          if (s != SA_OK) return s;
+          bytes += 64ull * mL;
+        } else {
+          s = sort(mL, spec_for(kbits));
+          if (s != SA_OK) return s;
+        }
       }
       // Small groups: refined tile by tile; name changes are queued.
       RefineArgs rf{};
@@ -689,6 +742,7 @@ struct Build {
       rf.tiles = (m + nominal - 1) / nominal;
       rf.h = (uint32_t)h;
       rf.W = W;
+      rf.mult = mult;
       rf.isa = isa;
       rf.isa_len = N + S + 1;
       rf.N = N32;
@@ -704,7 +758,7 @@ struct Build {
       s = launch(SA_K_REFINE, 0, 0, [&] { return launch_refine(rf, st); });
       if (s != SA_OK) return s;
       if (mL > 0) {
-        s = rename(mL, false, 0, 0, W, lbase, lold, GL, nxt, &ctrl->rc.m_s);
+        s = rename(mL, false, 0, 0, W, lbase, lold, GL, nxt, &ctrl->rc.m_s, mult > 2);
         if (s != SA_OK) return s;
       }
       s = scatter(m);
@@ -714,20 +768,23 @@ struct Build {
       if (opt.trace_isa && round < opt.trace_cap && S == 1)
         CK(cudaMemcpyAsync(opt.trace_isa + (size_t)round * N, isa, N * 4,
                            cudaMemcpyDeviceToDevice, st));
+      uint32_t p1[2] = {0, 0};  // the first sort's (passes, mask) in a-tuple rounds
+      if (mL > 0 && mult > 2) CK(cudaMemcpyAsync(p1, pm1, 8, cudaMemcpyDeviceToHost, st));
       s = read_ctrl(hc);
       if (s != SA_OK) return s;
+      hc.passes += p1[0];
       // Settle the byte counts that depend on this round's results.
       const uint64_t rbl = mL ? rename_bytes(mL, hc.m_l, hc.g_l) : 0;
-      const uint64_t rfb = refine_bytes(m - mL, G - GL, hc.m_s, hc.g_s, hc.upd);
+      const uint64_t rfb = refine_bytes(m - mL, G - GL, hc.m_s, hc.g_s, hc.upd, mult);
       for (Rec &r : recs)
         if (r.cls == SA_K_REFINE) r.bytes = rfb;
       settle(hc);
-      s = flush(hc.pass_mask, rbl);
+      s = flush(hc.pass_mask, rbl, p1[1]);
       if (s != SA_OK) return s;
       record(round, m, hc, kbits);
       bytes += (mL ? (uint64_t)hc.passes * 24 * mL : 0) + rbl + rfb + 8ull * G;
       cur = nxt;
-      h *= 2;
+      h *= mult;
       ++round;
     }
     // ---- output ----
@@ -759,6 +816,10 @@ sa_status check_offsets(const uint64_t *offsets, uint32_t count) {
     if (offsets[k + 1] < offsets[k]) return SA_ERR_INVALID_ARG;
   if (offsets[count] > SA_MAX_N) return SA_ERR_TOO_LARGE;
   return SA_OK;
+}
+
+bool bad_options(const sa_options *opt) {
+  return opt && opt->multiplier != 0 && (opt->multiplier < 2 || opt->multiplier > 4);
 }
 
 sa_status run_with_workspace(Build &B, void *workspace, size_t ws_bytes) {
@@ -803,6 +864,7 @@ GBSA_API sa_status sa_build_ex(const uint8_t *text, uint64_t n, uint32_t *sa_out
                                const sa_options *opt, sa_stats *stats, gbsa_stream_t stream) {
   if (n > SA_MAX_N) return SA_ERR_TOO_LARGE;
   if (n > 0 && (!text || !sa_out)) return SA_ERR_INVALID_ARG;
+  if (bad_options(opt)) return SA_ERR_INVALID_ARG;
   if (stats) memset(stats, 0, sizeof(sa_stats));
   cudaStream_t st = (cudaStream_t)stream;
   if (n == 0) return SA_OK;
@@ -837,6 +899,7 @@ GBSA_API sa_status sa_build_batched_ex(const uint8_t *texts, const uint64_t *off
   sa_status s = check_offsets(offsets, count);
   if (s != SA_OK) return s;
   if (count > (1u << 20)) return SA_ERR_TOO_LARGE;
+  if (bad_options(opt)) return SA_ERR_INVALID_ARG;
   const uint64_t N = offsets[count];
   if (stats) memset(stats, 0, sizeof(sa_stats));
   if (N == 0) return SA_OK;

@@ -127,13 +127,80 @@ __global__ void __launch_bounds__(256) k_gather_large(GatherLargeArgs a) {
   const uint32_t ip = (uint32_t)e;
   const uint64_t at = min((uint64_t)ip + a.h, a.isa_len - 1);
   const uint32_t r2 = __ldg(a.isa + at) + 1u;
-  a.keys[j] = ((uint64_t)lo << a.W) | r2;
-  a.vals[j] = ip;
+  const uint64_t key1 = ((uint64_t)lo << a.W) | r2;
+  if (a.mult == 2) {
+    a.keys[j] = key1;
+    a.vals[j] = ip;
+    return;
+  }
+  // a-tuples: the later partners are sorted first (keys), item j rides
+  // along; (group, r2) and the later partners are kept by item.
+  const uint32_t r3 = r2 ? __ldg(a.isa + min((uint64_t)ip + (uint64_t)2 * a.h, a.isa_len - 1)) + 1u : 0u;
+  uint32_t r4 = 0;
+  if (a.mult == 4 && r3) r4 = __ldg(a.isa + min((uint64_t)ip + (uint64_t)3 * a.h, a.isa_len - 1)) + 1u;
+  const uint64_t sec = a.mult == 4 ? (((uint64_t)r3 << a.W) | r4) : (uint64_t)r3;
+  a.keys[j] = sec;
+  a.vals[j] = j;
+  a.key1_stash[j] = key1;
+  a.sec_stash[j] = sec;
 }
 
 cudaError_t launch_gather_large(const GatherLargeArgs &a, cudaStream_t stream) {
   if (a.mL == 0) return cudaSuccess;
   k_gather_large<<<(unsigned)(((uint64_t)a.mL + 255) / 256), 256, 0, stream>>>(a);
+  return cudaGetLastError();
+}
+
+// Between the two sorts of an a-tuple round: the items, in the order of
+// their later partners, get their (group, r2) keys back as the input of the
+// second (stable) sort.
+__global__ void __launch_bounds__(256) k_wide_rekey(WideArgs a) {
+  const uint64_t x64 = (uint64_t)blockIdx.x * 256 + threadIdx.x;
+  if (x64 >= a.mL) return;
+  const uint32_t x = (uint32_t)x64;
+  const uint32_t j = a.plan->vfinal[x];
+  if (j >= a.mL) {  // never taken unless a logic error
+    raise_error(a.ctrl, ERR_INTERNAL, 11);
+    return;
+  }
+  a.ka[x] = a.key1_stash[j];
+  a.va[x] = j;
+}
+
+// After the second sort: each position gets its item's gapped position (for
+// k_rename) and its later partners, written to the sort buffer that does
+// not hold the result.
+__global__ void __launch_bounds__(256) k_wide_finish(WideArgs a) {
+  const uint64_t y64 = (uint64_t)blockIdx.x * 256 + threadIdx.x;
+  if (y64 >= a.mL) return;
+  const uint32_t y = (uint32_t)y64;
+  const SortPlan *p = a.plan;
+  const uint32_t j = p->vfinal[y];
+  const uint32_t lo = (uint32_t)(p->kfinal[y] >> a.W);
+  if (j >= a.mL || lo >= a.GL || j < __ldg(a.loff + lo)) {  // never taken unless a logic error
+    raise_error(a.ctrl, ERR_INTERNAL, 12);
+    return;
+  }
+  const uint32_t g = __ldg(a.lg + lo);
+  const uint64_t at = (uint64_t)__ldg(a.gstart + g) + (j - __ldg(a.loff + lo));
+  if (at >= a.m) {  // never taken unless a logic error
+    raise_error(a.ctrl, ERR_INTERNAL, 13);
+    return;
+  }
+  const uint32_t ip = (uint32_t)a.act[at];
+  const_cast<uint32_t *>(p->vfinal)[y] = ip;
+  (p->final_idx ? a.ka : a.kb)[y] = a.sec_stash[j];
+}
+
+cudaError_t launch_wide_rekey(const WideArgs &a, cudaStream_t stream) {
+  if (a.mL == 0) return cudaSuccess;
+  k_wide_rekey<<<(unsigned)(((uint64_t)a.mL + 255) / 256), 256, 0, stream>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wide_finish(const WideArgs &a, cudaStream_t stream) {
+  if (a.mL == 0) return cudaSuccess;
+  k_wide_finish<<<(unsigned)(((uint64_t)a.mL + 255) / 256), 256, 0, stream>>>(a);
   return cudaGetLastError();
 }
 
@@ -151,11 +218,24 @@ struct RfCfg {
   static_assert(DPT >= 1 && RADIX % BLOCK == 0, "digits per thread");
 };
 
-template <int BLOCK, int CAP>
+// Per-slot data of a tile when a round ranks a-tuples (a = 3 or 4): the
+// first sort orders the slots by their later partner names, the second by
+// (local group, first partner name) and keeps that order among ties.
+template <int CAP, bool WIDE>
+struct RfWide {
+  uint64_t key1[CAP];  // (local group << W) | r2
+  uint64_t sec[CAP];   // r3 (a = 3) or (r3 << W) | r4 (a = 4)
+  uint32_t ip[CAP];    // gapped position
+};
+template <int CAP>
+struct RfWide<CAP, false> {};
+
+template <int BLOCK, int CAP, bool WIDE>
 struct RfSmem {
   using C = RfCfg<BLOCK, CAP>;
   uint64_t keys[CAP + CAP / 16];  // padded (e + e/16) after the last pass
   uint32_t vals[CAP + CAP / 32];  // padded (e + e/32) after the last pass
+  RfWide<CAP, WIDE> w;
   union {
     uint32_t gsrc[C::MAXG];             // loading: first position of each local group
     uint32_t match[C::WARPS][RADIX];    // sorting: per-warp peer masks
@@ -167,7 +247,7 @@ struct RfSmem {
   uint32_t goff[C::MAXG + 1];           // start of the local group in the tile
   uint32_t tmp[2][4 * C::WARPS];        // scan scratch (double-buffered)
   uint32_t flag, all_small, upd_local, upd_base, surv_base, grp_base;
-  unsigned long long orv;
+  unsigned long long orv, orv2;
 };
 
 // One-barrier exclusive sum over the block: warp scans, warp totals in
@@ -256,10 +336,11 @@ __device__ __forceinline__ void rf_block_scan4(uint32_t mx, uint32_t s1, uint32_
 // contiguous chunk [w*C, (w+1)*C) with C = 32 * ceil(cnt / BLOCK), so every
 // warp does the same useful work and (warp, slot, lane) is the input order.
 // The last pass writes the padded layout read by the rename phase (at
-// least one pass always runs). Four barriers per pass.
-template <int BLOCK, int CAP>
-__device__ void rf_tile_sort(RfSmem<BLOCK, CAP> &S, uint32_t cnt, unsigned long long varying,
-                             uint32_t nbits) {
+// least one pass always runs; with pad_out false it writes the plain
+// layout). Four barriers per pass.
+template <int BLOCK, int CAP, bool WIDE>
+__device__ void rf_tile_sort(RfSmem<BLOCK, CAP, WIDE> &S, uint32_t cnt,
+                             unsigned long long varying, uint32_t nbits, bool pad_out) {
   using C = RfCfg<BLOCK, CAP>;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t lt = lanemask_lt();
@@ -279,7 +360,7 @@ __device__ void rf_tile_sort(RfSmem<BLOCK, CAP> &S, uint32_t cnt, unsigned long 
     const bool kept = ((varying >> (p * RADIX_BITS)) & 0xFFull) != 0ull;
     if (!kept && p != last) continue;
     const uint32_t shift = p * RADIX_BITS;
-    const bool pad = p == last;
+    const bool pad = pad_out && p == last;
     uint64_t key[C::ITEMS];
     uint32_t val[C::ITEMS], pos[C::ITEMS];
     uint16_t *wh = S.whist[buf][warp];
@@ -339,16 +420,17 @@ __device__ void rf_tile_sort(RfSmem<BLOCK, CAP> &S, uint32_t cnt, unsigned long 
 
 // Up to 8 slots per thread: 64 registers (4 blocks of 256 or 8 of 128 per
 // SM); 16 slots: 128 registers (such tiles fit 2 blocks per SM anyway).
-template <int BLOCK, int CAP>
+template <int BLOCK, int CAP, bool WIDE>
 __global__ void __launch_bounds__(BLOCK, (CAP / BLOCK > 8 ? 512 : 1024) / BLOCK)
     k_refine(RefineArgs a) {
   using C = RfCfg<BLOCK, CAP>;
-  using Sm = RfSmem<BLOCK, CAP>;
+  using Sm = RfSmem<BLOCK, CAP, WIDE>;
   extern __shared__ __align__(128) uint8_t smem_raw[];
   Sm &S = *reinterpret_cast<Sm *>(smem_raw);
   const int tid = threadIdx.x;
   if (tid == 0) {
     S.orv = 0ull;
+    S.orv2 = 0ull;
     S.upd_local = 0u;
     S.flag = has_error(a.ctrl) ? 1u : 0u;
   }
@@ -442,44 +524,101 @@ __global__ void __launch_bounds__(BLOCK, (CAP / BLOCK > 8 ? 512 : 1024) / BLOCK)
       r2v[k] = __ldg(a.isa + at) + 1u;
     }
   }
-  unsigned long long orv = 0ull;
-  uint64_t key0 = 0ull;
+  // a = 3, 4 (Prefix Quadrupling): the names of i' + 2h and i' + 3h as well,
+  // 0 once an earlier one is the end sentinel (ties on a non-zero name
+  // imply the later offsets stay inside the text; the rest never decide).
+  uint64_t secv[WIDE ? C::ITEMS : 1];
+  if constexpr (WIDE) {
+    uint32_t r3v[C::ITEMS], r4v[C::ITEMS];
+#pragma unroll
+    for (int k = 0; k < C::ITEMS; ++k) {
+      const uint32_t q = k * BLOCK + tid;
+      r3v[k] = r4v[k] = 0;
+      if ((uint32_t)k < K && q < cnt) {
+        const uint64_t ip = (uint32_t)ent[k];
+        r3v[k] = __ldg(a.isa + min(ip + (uint64_t)2 * a.h, a.isa_len - 1)) + 1u;
+        if (a.mult == 4) r4v[k] = __ldg(a.isa + min(ip + (uint64_t)3 * a.h, a.isa_len - 1)) + 1u;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < C::ITEMS; ++k) {
+      const uint32_t r3 = r2v[k] ? r3v[k] : 0u;
+      const uint32_t r4 = r3 ? r4v[k] : 0u;
+      secv[k] = a.mult == 4 ? (((uint64_t)r3 << a.W) | r4) : (uint64_t)r3;
+    }
+  }
+  unsigned long long orv = 0ull, orv2 = 0ull;
 #pragma unroll
   for (int k = 0; k < C::ITEMS; ++k) {
     const uint32_t q = k * BLOCK + tid;
     if ((uint32_t)k < K && q < cnt) {
       const uint32_t lgq = (uint32_t)(ent[k] >> 32) - g0;
       const uint64_t key = ((uint64_t)lgq << a.W) | r2v[k];
-      S.keys[q] = key;
-      S.vals[q] = (uint32_t)ent[k];
-      if (q == 0) key0 = key;
+      if constexpr (WIDE) {
+        S.w.key1[q] = key;
+        S.w.sec[q] = secv[k];
+        S.w.ip[q] = (uint32_t)ent[k];
+        S.keys[q] = secv[k];
+        S.vals[q] = q;
+      } else {
+        S.keys[q] = key;
+        S.vals[q] = (uint32_t)ent[k];
+      }
     }
   }
   // Bits that vary inside the tile: OR of (key ^ first key). Every key
   // shares the first key's local group 0 bits only when ng == 1, so the
   // reference key is the tile's first key, read after the barrier.
   __syncthreads();
-  key0 = S.keys[0];
+  if constexpr (WIDE) {
+    const uint64_t key0 = S.w.key1[0], sec0 = S.w.sec[0];
 #pragma unroll
-  for (int k = 0; k < C::ITEMS; ++k) {
-    const uint32_t q = k * BLOCK + tid;
-    if ((uint32_t)k < K && q < cnt) orv |= S.keys[q] ^ key0;
+    for (int k = 0; k < C::ITEMS; ++k) {
+      const uint32_t q = k * BLOCK + tid;
+      if ((uint32_t)k < K && q < cnt) {
+        orv |= S.w.key1[q] ^ key0;
+        orv2 |= S.w.sec[q] ^ sec0;
+      }
+    }
+  } else {
+    const uint64_t key0 = S.keys[0];
+#pragma unroll
+    for (int k = 0; k < C::ITEMS; ++k) {
+      const uint32_t q = k * BLOCK + tid;
+      if ((uint32_t)k < K && q < cnt) orv |= S.keys[q] ^ key0;
+    }
   }
 #pragma unroll
-  for (int d = 16; d > 0; d >>= 1) orv |= __shfl_xor_sync(0xffffffffu, orv, d);
+  for (int d = 16; d > 0; d >>= 1) {
+    orv |= __shfl_xor_sync(0xffffffffu, orv, d);
+    if constexpr (WIDE) orv2 |= __shfl_xor_sync(0xffffffffu, orv2, d);
+  }
   if ((tid & 31) == 0 && orv) atomicOr(&S.orv, orv);
+  if (WIDE && (tid & 31) == 0 && orv2) atomicOr(&S.orv2, orv2);
   __syncthreads();
   const uint32_t gbits = ng > 1 ? 32u - __clz(ng - 1) : 0u;
-  rf_tile_sort<BLOCK, CAP>(S, cnt, S.orv, a.W + gbits);
+  if constexpr (WIDE) {
+    // LSD over the tuple: the later partners first, then (group, r2); both
+    // sorts are stable, so ties on (group, r2) keep the first sort's order.
+    rf_tile_sort<BLOCK, CAP, WIDE>(S, cnt, S.orv2, a.mult == 4 ? 2 * a.W : a.W, false);
+#pragma unroll
+    for (int k = 0; k < C::ITEMS; ++k) {
+      const uint32_t q = k * BLOCK + tid;
+      if ((uint32_t)k < K && q < cnt) S.keys[q] = S.w.key1[S.vals[q]];
+    }
+    __syncthreads();
+  }
+  rf_tile_sort<BLOCK, CAP, WIDE>(S, cnt, S.orv, a.W + gbits, true);
 
   // Rename in blocked layout: items tid*K .. tid*K+K-1 of the sorted tile.
   const uint32_t l0 = tid * K;
   bool f[C::ITEMS + 1];
   {
-    uint64_t prev = 0ull;
+    uint64_t prev = 0ull, prev2 = 0ull;
     if (l0 > 0 && l0 - 1 < cnt) {
       const uint32_t e = l0 - 1;
       prev = S.keys[e + (e >> 4)];
+      if constexpr (WIDE) prev2 = S.w.sec[S.vals[e + (e >> 5)]];
     }
 #pragma unroll
     for (int k = 0; k <= C::ITEMS; ++k) {
@@ -489,6 +628,11 @@ __global__ void __launch_bounds__(BLOCK, (CAP / BLOCK > 8 ? 512 : 1024) / BLOCK)
         const uint64_t kcur = S.keys[j + (j >> 4)];
         f[k] = (j == 0) || kcur != prev;
         prev = kcur;
+        if constexpr (WIDE) {
+          const uint64_t scur = S.w.sec[S.vals[j + (j >> 5)]];
+          f[k] = f[k] || scur != prev2;
+          prev2 = scur;
+        }
       }
     }
   }
@@ -575,7 +719,8 @@ __global__ void __launch_bounds__(BLOCK, (CAP / BLOCK > 8 ? 512 : 1024) / BLOCK)
     if ((uint32_t)k < K && j < cnt) {
       if (f[k]) run_head = j;
       const uint64_t kk = S.keys[j + (j >> 4)];
-      const uint32_t ip = S.vals[j + (j >> 5)];
+      uint32_t ip = S.vals[j + (j >> 5)];
+      if constexpr (WIDE) ip = S.w.ip[ip];
       const uint32_t lgq = (uint32_t)(kk >> a.W);
       const uint32_t name = name_of(lgq, run_head, rend[k]);
       if (name >= a.N || ip >= a.isa_len) {  // never taken unless a logic error
@@ -599,31 +744,39 @@ __global__ void __launch_bounds__(BLOCK, (CAP / BLOCK > 8 ? 512 : 1024) / BLOCK)
   }
 }
 
-template <int BLOCK, int CAP>
+template <int BLOCK, int CAP, bool WIDE>
 cudaError_t launch_refine_t(const RefineArgs &a, cudaStream_t stream) {
   static bool configured = false;
-  const int smem = (int)sizeof(RfSmem<BLOCK, CAP>);
+  const int smem = (int)sizeof(RfSmem<BLOCK, CAP, WIDE>);
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_refine<BLOCK, CAP>,
+    cudaError_t e = cudaFuncSetAttribute(k_refine<BLOCK, CAP, WIDE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_refine<BLOCK, CAP>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    e = cudaFuncSetAttribute(k_refine<BLOCK, CAP, WIDE>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  k_refine<BLOCK, CAP><<<a.tiles, BLOCK, smem, stream>>>(a);
+  k_refine<BLOCK, CAP, WIDE><<<a.tiles, BLOCK, smem, stream>>>(a);
   return cudaGetLastError();
+}
+
+template <bool WIDE>
+cudaError_t launch_refine_w(const RefineArgs &a, cudaStream_t stream) {
+  switch (a.shape) {
+    case 0: return launch_refine_t<128, 1024, WIDE>(a, stream);
+    case 1: return launch_refine_t<256, 2048, WIDE>(a, stream);
+    case 2: return launch_refine_t<256, 4096, WIDE>(a, stream);
+    case 3: return launch_refine_t<256, 1024, WIDE>(a, stream);
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_refine(const RefineArgs &a, cudaStream_t stream) {
   if (a.tiles == 0) return cudaSuccess;
-  switch (a.shape) {
-    case 0: return launch_refine_t<128, 1024>(a, stream);
-    case 1: return launch_refine_t<256, 2048>(a, stream);
-    case 2: return launch_refine_t<256, 4096>(a, stream);
-    case 3: return launch_refine_t<256, 1024>(a, stream);
-  }
+  if (a.mult == 2) return launch_refine_w<false>(a, stream);
+  if (a.mult == 3 || a.mult == 4) return launch_refine_w<true>(a, stream);
   return cudaErrorInvalidValue;
 }
 

@@ -126,11 +126,15 @@ __global__ void __launch_bounds__(RN_BLOCK, 4) k_rename(RenameArgs a) {
 #pragma unroll
     for (int k = 0; k < RN_ITEMS + 2; ++k) is_tail[k] = tail(key[k], val[k]);
   }
+  // a-tuple rounds: items with equal keys are still apart if their later
+  // partners differ (sorted alongside, in the other key buffer).
+  const uint64_t *SEC = a.sec_buf[0] ? a.sec_buf[a.plan->final_idx ^ 1u] : nullptr;
 #pragma unroll
   for (int k = 0; k <= RN_ITEMS; ++k) {
     const uint64_t j = (uint64_t)base + l0 + k;
     bool b = (j == 0) || (j >= a.m) || key[k + 1] != key[k];
     if (a.round0 && j > 0 && j < a.m) b = b || is_tail[k + 1] || is_tail[k];
+    if (SEC && !b) b = SEC[j] != SEC[j - 1];
     f[k] = b;
   }
   uint32_t th_head = 0, th_surv = 0, th_hs = 0, th_uniq = 0;

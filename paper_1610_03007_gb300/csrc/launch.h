@@ -72,6 +72,9 @@ struct RenameArgs {
   const uint32_t *seg_off;   // S+1 ungapped offsets
   uint32_t S;
   uint32_t W;                // later rounds: group ordinal g = key >> W
+  // a-tuple rounds: {ka, kb}; the later partners of sorted position j are
+  // in the buffer that does not hold the keys. {NULL, NULL} otherwise.
+  const uint64_t *sec_buf[2];
   const uint32_t *base_in;   // later rounds: head rank - start of group g
   const uint32_t *old_in;    // later rounds: name of group g (round 0: NULL)
   uint32_t g_in;             // later rounds: groups in base_in (bounds guard)
@@ -138,19 +141,45 @@ struct ClassifyArgs {
 cudaError_t launch_classify(const ClassifyArgs &a, int num_sms, cudaStream_t stream);
 
 // keys[j] = (k << W) | r2 for the j-th item of the large groups, k = large
-// group ordinal; vals[j] = gapped position.
+// group ordinal; vals[j] = gapped position. With a = 3 or 4 (a-tuples of
+// names per round) instead keys[j] = the later partners (r3, or
+// (r3 << W) | r4), vals[j] = j, and both keys are also kept by item in the
+// stashes for k_wide_rekey / k_wide_finish.
 struct GatherLargeArgs {
   const uint64_t *act;
   const uint32_t *gstart;
   const uint32_t *lg, *loff;
   uint32_t mL, GL;
   uint32_t h, W;
+  uint32_t mult;            // a: 2, 3 or 4
   const uint32_t *isa;
   uint64_t isa_len;
   uint64_t *keys;
   uint32_t *vals;
+  uint64_t *key1_stash;     // a > 2: (k << W) | r2 by item
+  uint64_t *sec_stash;      // a > 2: later partners by item
 };
 cudaError_t launch_gather_large(const GatherLargeArgs &a, cudaStream_t stream);
+
+// The two steps between and after the sorts of an a-tuple round (a > 2).
+// rekey: (ka, va)[x] = (key1_stash[j], j) for j = plan->vfinal[x].
+// finish: plan->vfinal[y] = gapped position of item j = plan->vfinal[y];
+// the other key buffer (kb if the result is in ka, else ka) gets
+// sec_stash[j] at y.
+struct WideArgs {
+  const SortPlan *plan;
+  uint32_t m;               // items in the active list (bounds guard)
+  uint32_t mL, GL, W;
+  const uint64_t *act;
+  const uint32_t *gstart;
+  const uint32_t *lg, *loff;
+  const uint64_t *key1_stash, *sec_stash;
+  uint64_t *ka, *kb;
+  uint32_t *va;
+  Ctrl *ctrl;
+};
+cudaError_t launch_wide_rekey(const WideArgs &a, cudaStream_t stream);
+cudaError_t launch_wide_finish(const WideArgs &a, cudaStream_t stream);
 
 struct RefineArgs {
   const uint64_t *act;      // current active list (g << 32) | i'
@@ -162,6 +191,7 @@ struct RefineArgs {
   uint32_t shape;           // index into REFINE_SHAPE
   uint32_t m, G, tiles;
   uint32_t h, W;
+  uint32_t mult;            // a: names of i' + h .. i' + (a-1)h are ranked (2, 3, 4)
   const uint32_t *isa;      // read only (updates are deferred)
   uint64_t isa_len;
   uint32_t N;

@@ -31,7 +31,7 @@
 
 #define GBSA_API extern "C" __attribute__((visibility("default")))
 
-// Largest text accepted: 2^18 bytes; its workspace is about 16.7 MiB.
+// Largest text accepted: 2^18 bytes; its workspace is about 17.8 MiB.
 constexpr uint64_t NOALLOC_MAX_N = 1ull << 18;
 constexpr size_t NOALLOC_SCRATCH_BYTES = 20ull << 20;  // 20 MiB
 
