@@ -349,6 +349,20 @@ def run_plain(args):
     dc3_ms = b0.elapsed_time(b1) / 2
     del dc3_sa
 
+    # The same build with a-fold rounds (prefix tripling and quadrupling):
+    # fewer rounds, each ranking a - 1 partner names.
+    mult = {"2": {"ms": ms, "rounds": stats["rounds"]}}
+    for a in (3, 4):
+        gbsa.sa_build_ex(text, workspace=ws, multiplier=a, **params)
+        b0.record(stream)
+        for _ in range(2):
+            mst = gbsa.sa_build_ex(text, workspace=ws, multiplier=a, **params)[2]
+        b1.record(stream)
+        torch.cuda.synchronize()
+        mult[str(a)] = {"ms": b0.elapsed_time(b1) / 2, "rounds": mst["rounds"]}
+    for v in mult.values():
+        v["value"] = n / (v["ms"] * 1e-3) / 1e6
+
     # End to end through the host entry point: pinned host text in, host SA
     # out, copies inside the timed region.
     h_text = torch.from_numpy(t_host).pin_memory()
@@ -415,6 +429,9 @@ def run_plain(args):
                 "note": "sa_lcp on the built SA, outside the timed step"},
         "dc3": {"ms": dc3_ms, "value": n / (dc3_ms * 1e-3) / 1e6, "unit": "MB/s",
                 "note": "the same text by sa_build_dc3 (skew algorithm), outside the timed step"},
+        "multiplier": {"by_a": mult, "unit": "MB/s",
+                       "note": "the same text with sa_options.multiplier a (a-fold rounds, "
+                               "Prefix Quadrupling); a = 3, 4 outside the timed step"},
     }
     line["cpu_baseline"] = cpu_baseline() if (world == 1 and not args.no_cpu) else None
     print(json.dumps(line), flush=True)
