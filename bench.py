@@ -288,80 +288,83 @@ def run_plain(args):
     clocks = sampler.stop()
     stats = st
 
-    # BWT of the built SA through sa_bwt, timed alone on the same stream
-    # (text, SA and BWT together exceed L2).
-    sa_dev = step(profile=False)[0]
-    lib = gbsa.load()
-    bwt_buf = torch.empty(n + 1, dtype=torch.uint8, device=dev)
-    prim = torch.zeros(1, dtype=torch.int64, device=dev)
+    bwt_ms = lcp_ms = dc3_ms = None
+    mult = None
+    if not args.build_only:
+        # BWT of the built SA through sa_bwt, timed alone on the same stream
+        # (text, SA and BWT together exceed L2).
+        sa_dev = step(profile=False)[0]
+        lib = gbsa.load()
+        bwt_buf = torch.empty(n + 1, dtype=torch.uint8, device=dev)
+        prim = torch.zeros(1, dtype=torch.int64, device=dev)
 
-    def bwt_call():
-        rc = lib.sa_bwt(text.data_ptr(), n, sa_dev.data_ptr(), bwt_buf.data_ptr(),
-                        prim.data_ptr(), stream.cuda_stream)
-        if rc != 0:
-            raise RuntimeError(f"sa_bwt failed: {rc}")
+        def bwt_call():
+            rc = lib.sa_bwt(text.data_ptr(), n, sa_dev.data_ptr(), bwt_buf.data_ptr(),
+                            prim.data_ptr(), stream.cuda_stream)
+            if rc != 0:
+                raise RuntimeError(f"sa_bwt failed: {rc}")
 
-    for _ in range(3):
-        bwt_call()
-    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    b0.record(stream)
-    for _ in range(5):
-        bwt_call()
-    b1.record(stream)
-    torch.cuda.synchronize()
-    bwt_ms = b0.elapsed_time(b1) / 5
-    del bwt_buf
-
-    # LCP array of the built SA through sa_lcp (caller workspace), timed the
-    # same way.
-    lcp_buf = torch.empty(n, dtype=torch.int32, device=dev)
-    lcp_ws = torch.empty(int(lib.sa_lcp_workspace_bytes(n)), dtype=torch.uint8, device=dev)
-
-    def lcp_call():
-        rc = lib.sa_lcp(text.data_ptr(), n, sa_dev.data_ptr(), lcp_buf.data_ptr(),
-                        lcp_ws.data_ptr(), lcp_ws.numel(), stream.cuda_stream)
-        if rc != 0:
-            raise RuntimeError(f"sa_lcp failed: {rc}")
-
-    lcp_call()
-    b0.record(stream)
-    for _ in range(3):
-        lcp_call()
-    b1.record(stream)
-    torch.cuda.synchronize()
-    lcp_ms = b0.elapsed_time(b1) / 3
-    del sa_dev, lcp_buf, lcp_ws
-
-    # The same suffix array by DC3 (sa_build_dc3), for comparison.
-    dc3_sa = torch.empty(n, dtype=torch.int32, device=dev)
-
-    def dc3_call():
-        rc = lib.sa_build_dc3(text.data_ptr(), n, dc3_sa.data_ptr(), None, stream.cuda_stream)
-        if rc != 0:
-            raise RuntimeError(f"sa_build_dc3 failed: {rc}")
-
-    dc3_call()
-    b0.record(stream)
-    for _ in range(2):
-        dc3_call()
-    b1.record(stream)
-    torch.cuda.synchronize()
-    dc3_ms = b0.elapsed_time(b1) / 2
-    del dc3_sa
-
-    # The same build with a-fold rounds (prefix tripling and quadrupling):
-    # fewer rounds, each ranking a - 1 partner names.
-    mult = {"2": {"ms": ms, "rounds": stats["rounds"]}}
-    for a in (3, 4):
-        gbsa.sa_build_ex(text, workspace=ws, multiplier=a, **params)
+        for _ in range(3):
+            bwt_call()
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         b0.record(stream)
-        for _ in range(2):
-            mst = gbsa.sa_build_ex(text, workspace=ws, multiplier=a, **params)[2]
+        for _ in range(5):
+            bwt_call()
         b1.record(stream)
         torch.cuda.synchronize()
-        mult[str(a)] = {"ms": b0.elapsed_time(b1) / 2, "rounds": mst["rounds"]}
-    for v in mult.values():
-        v["value"] = n / (v["ms"] * 1e-3) / 1e6
+        bwt_ms = b0.elapsed_time(b1) / 5
+        del bwt_buf
+
+        # LCP array of the built SA through sa_lcp (caller workspace), timed the
+        # same way.
+        lcp_buf = torch.empty(n, dtype=torch.int32, device=dev)
+        lcp_ws = torch.empty(int(lib.sa_lcp_workspace_bytes(n)), dtype=torch.uint8, device=dev)
+
+        def lcp_call():
+            rc = lib.sa_lcp(text.data_ptr(), n, sa_dev.data_ptr(), lcp_buf.data_ptr(),
+                            lcp_ws.data_ptr(), lcp_ws.numel(), stream.cuda_stream)
+            if rc != 0:
+                raise RuntimeError(f"sa_lcp failed: {rc}")
+
+        lcp_call()
+        b0.record(stream)
+        for _ in range(3):
+            lcp_call()
+        b1.record(stream)
+        torch.cuda.synchronize()
+        lcp_ms = b0.elapsed_time(b1) / 3
+        del sa_dev, lcp_buf, lcp_ws
+
+        # The same suffix array by DC3 (sa_build_dc3), for comparison.
+        dc3_sa = torch.empty(n, dtype=torch.int32, device=dev)
+
+        def dc3_call():
+            rc = lib.sa_build_dc3(text.data_ptr(), n, dc3_sa.data_ptr(), None, stream.cuda_stream)
+            if rc != 0:
+                raise RuntimeError(f"sa_build_dc3 failed: {rc}")
+
+        dc3_call()
+        b0.record(stream)
+        for _ in range(2):
+            dc3_call()
+        b1.record(stream)
+        torch.cuda.synchronize()
+        dc3_ms = b0.elapsed_time(b1) / 2
+        del dc3_sa
+
+        # The same build with a-fold rounds (prefix tripling and quadrupling):
+        # fewer rounds, each ranking a - 1 partner names.
+        mult = {"2": {"ms": ms, "rounds": stats["rounds"]}}
+        for a in (3, 4):
+            gbsa.sa_build_ex(text, workspace=ws, multiplier=a, **params)
+            b0.record(stream)
+            for _ in range(2):
+                mst = gbsa.sa_build_ex(text, workspace=ws, multiplier=a, **params)[2]
+            b1.record(stream)
+            torch.cuda.synchronize()
+            mult[str(a)] = {"ms": b0.elapsed_time(b1) / 2, "rounds": mst["rounds"]}
+        for v in mult.values():
+            v["value"] = n / (v["ms"] * 1e-3) / 1e6
 
     # End to end through the host entry point: pinned host text in, host SA
     # out, copies inside the timed region.
@@ -419,20 +422,24 @@ def run_plain(args):
                 "d2h_bytes_per_step": 4 * n, "ms_per_step": e2e_ms},
         "gpu_launches": launches,
         "clocks": clocks,
-        "bwt": {"ms": bwt_ms, "bytes_per_row": 6,
-                "gbs": 6.0 * (n + 1) / (bwt_ms * 1e-3) / 1e9,
-                "frac": 6.0 * (n + 1) / (bwt_ms * 1e-3) / 1e9 / hbm,
-                "note": "sa_bwt on the built SA, outside the timed step"},
-        "lcp": {"ms": lcp_ms, "bytes_per_position": 30,
-                "gbs": 30.0 * n / (lcp_ms * 1e-3) / 1e9,
-                "frac": 30.0 * n / (lcp_ms * 1e-3) / 1e9 / hbm,
-                "note": "sa_lcp on the built SA, outside the timed step"},
-        "dc3": {"ms": dc3_ms, "value": n / (dc3_ms * 1e-3) / 1e6, "unit": "MB/s",
-                "note": "the same text by sa_build_dc3 (skew algorithm), outside the timed step"},
-        "multiplier": {"by_a": mult, "unit": "MB/s",
-                       "note": "the same text with sa_options.multiplier a (a-fold rounds, "
-                               "Prefix Quadrupling); a = 3, 4 outside the timed step"},
     }
+    if not args.build_only:
+        line.update({
+            "bwt": {"ms": bwt_ms, "bytes_per_row": 6,
+                    "gbs": 6.0 * (n + 1) / (bwt_ms * 1e-3) / 1e9,
+                    "frac": 6.0 * (n + 1) / (bwt_ms * 1e-3) / 1e9 / hbm,
+                    "note": "sa_bwt on the built SA, outside the timed step"},
+            "lcp": {"ms": lcp_ms, "bytes_per_position": 30,
+                    "gbs": 30.0 * n / (lcp_ms * 1e-3) / 1e9,
+                    "frac": 30.0 * n / (lcp_ms * 1e-3) / 1e9 / hbm,
+                    "note": "sa_lcp on the built SA, outside the timed step"},
+            "dc3": {"ms": dc3_ms, "value": n / (dc3_ms * 1e-3) / 1e6, "unit": "MB/s",
+                    "note": "the same text by sa_build_dc3 (skew algorithm), outside the "
+                            "timed step"},
+            "multiplier": {"by_a": mult, "unit": "MB/s",
+                           "note": "the same text with sa_options.multiplier a (a-fold rounds, "
+                                   "Prefix Quadrupling); a = 3, 4 outside the timed step"},
+        })
     line["cpu_baseline"] = cpu_baseline() if (world == 1 and not args.no_cpu) else None
     print(json.dumps(line), flush=True)
     if pg:
@@ -632,6 +639,9 @@ def main():
     ap.add_argument("--n", type=int, default=0, help="override the text length (testing)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--no-tune", action="store_true", help="use the default tile parameters")
+    ap.add_argument("--build-only", action="store_true",
+                    help="plain workload: skip the BWT, LCP, DC3 and multiplier calls "
+                         "(a launch list of the builds alone)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
