@@ -41,7 +41,7 @@ def build(mutant: int = 0, force: bool = False) -> str:
     return out
 
 
-MUTANTS = (1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12)
+MUTANTS = (1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13)
 
 
 class Oracle:
@@ -70,6 +70,8 @@ class Oracle:
         lib.oracle_lcp_pair.restype = i64
         lib.oracle_lcp.argtypes = [p, i64, p, p]
         lib.oracle_lcp.restype = None
+        lib.oracle_dc7_names.argtypes = [p, i64, p]
+        lib.oracle_dc7_names.restype = i64
         lib.oracle_bwt_invert.argtypes = [p, i64, i64, p]
         lib.oracle_bwt_invert.restype = ctypes.c_int
         self._lib = lib
@@ -162,6 +164,14 @@ class Oracle:
         out = np.zeros(T.size, dtype=np.uint32)
         self._lib.oracle_lcp(T.ctypes.data, T.size, s.ctypes.data, out.ctypes.data)
         return out
+
+    def dc7_names(self, t) -> np.ndarray:
+        """DC7's first recursion text: names of the samples i = 0, 1, 3
+        (mod 7), i <= n, class by class (Section 2.2)."""
+        T = self._text(t)
+        out = np.zeros(3 * (T.size // 7 + 1), dtype=np.uint32)
+        m = self._lib.oracle_dc7_names(T.ctypes.data, T.size, out.ctypes.data)
+        return out[:m]
 
     def bwt_invert(self, bwt, primary: int) -> np.ndarray:
         b = np.ascontiguousarray(bwt, dtype=np.uint8)

@@ -225,6 +225,49 @@ int64_t oracle_pq_sa(const uint8_t *T, int64_t n, int64_t h0, int64_t a, uint32_
   return rounds;
 }
 
+/* ---- DC7 recursion text (Section 2.2) ---------------------------------- */
+
+#if ORACLE_MUTANT == 13
+#define DC7_WIN 6 /* mutant: one character short of the window */
+#else
+#define DC7_WIN 7
+#endif
+
+typedef struct {
+  int16_t c[7]; /* the window, -1 past the end of the text */
+  int64_t slot; /* index in the recursion text */
+} dc7_win;
+
+static int qs_dc7(const void *x, const void *y) {
+  const dc7_win *a = (const dc7_win *)x, *b = (const dc7_win *)y;
+  for (int k = 0; k < DC7_WIN; ++k)
+    if (a->c[k] != b->c[k]) return a->c[k] < b->c[k] ? -1 : 1;
+  return 0;
+}
+
+int64_t oracle_dc7_names(const uint8_t *T, int64_t n, uint32_t *out) {
+  static const int D7[3] = {0, 1, 3};
+  if (n < 0) return 0;
+  dc7_win *w = (dc7_win *)malloc((size_t)(3 * (n / 7 + 1) + 1) * sizeof(dc7_win));
+  int64_t m = 0;
+  for (int d = 0; d < 3; ++d)
+    for (int64_t i = D7[d]; i <= n; i += 7) {
+      for (int k = 0; k < 7; ++k) w[m].c[k] = i + k < n ? (int16_t)T[i + k] : (int16_t)-1;
+      w[m].slot = m;
+      ++m;
+    }
+  /* Sort the windows (a library sort), then name them in sorted order: a
+   * new name wherever the window differs from its predecessor. */
+  qsort(w, (size_t)m, sizeof(dc7_win), qs_dc7);
+  uint32_t name = 0;
+  for (int64_t k = 0; k < m; ++k) {
+    if (k == 0 || qs_dc7(&w[k], &w[k - 1]) != 0) ++name;
+    out[w[k].slot] = name;
+  }
+  free(w);
+  return m;
+}
+
 /* ---- checkers ----------------------------------------------------------- */
 
 int oracle_check_sa(const uint8_t *T, int64_t n, const uint32_t *sa, int64_t *bad) {

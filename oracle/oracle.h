@@ -73,6 +73,17 @@ int64_t oracle_pd_sa(const uint8_t *T, int64_t n, int64_t h0, uint32_t *sa,
 int64_t oracle_pq_sa(const uint8_t *T, int64_t n, int64_t h0, int64_t a, uint32_t *sa,
                      uint32_t *isa, uint32_t *trace, int64_t trace_cap);
 
+/* The recursion text of DC7's first level (Section 2.2, Algorithms 8-9):
+ * the sample positions of the difference cover D7 = {0, 1, 3} modulo 7,
+ * taken class by class (all i = 0 mod 7, then 1, then 3, each in text
+ * order, each class running up to and including the first position whose
+ * 7-character window reaches the end of the text: i <= n), each replaced
+ * by its lexicographic name: 1 + the number of distinct 7-character
+ * windows smaller than its own (characters past the end compare as the
+ * end of text, below every byte). Writes m names to out (capacity
+ * 3 * (n / 7 + 1)) and returns m. */
+int64_t oracle_dc7_names(const uint8_t *T, int64_t n, uint32_t *out);
+
 /* Checker of Burkhardt & Kaerkkaeinen (CPM 2003) for the definition above:
  * SA is a permutation of [0,n) and, for every adjacent pair a = SA[j],
  * b = SA[j+1], (T[a], rank(a+1)) < (T[b], rank(b+1)) with rank(n) = -1.

@@ -263,8 +263,39 @@ def pin_multiplier(o):
     return bad
 
 
+def py_dc7_names(t: bytes):
+    """DC7's first recursion text by definition, in Python: the samples
+    i = 0, 1, 3 (mod 7) with i <= n, class by class; each named 1 + the
+    number of distinct smaller 7-character windows (the end of text below
+    every byte, encoded -1)."""
+    n = len(t)
+    wins = []
+    for a in (0, 1, 3):
+        for i in range(a, n + 1, 7):
+            wins.append(tuple(t[i + k] if i + k < n else -1 for k in range(7)))
+    order = {w: r + 1 for r, w in enumerate(sorted(set(wins)))}
+    return [order[w] for w in wins]
+
+
+def pin_dc7_names(o):
+    bad = []
+    texts = [b"", b"x", b"ab", b"abcdefg", b"abcdefgh", b"a" * 50, b"ab" * 40,
+             b"mississippi" * 3, bytes(range(256))]
+    rng = np.random.default_rng(3)
+    for n, sigma in ((100, 2), (301, 3), (700, 256)):
+        texts.append(bytes(rng.integers(0, sigma, n, dtype=np.uint8)))
+    texts.append(gen.text("zipf_repeats", 8, 1500).tobytes())
+    for t in texts:
+        if list(o.dc7_names(t)) != py_dc7_names(t):
+            bad.append(f"dc7 names {t[:10]!r} (n={len(t)})")
+    for n in range(0, 30):  # sizes: every class runs to i <= n
+        if len(o.dc7_names(b"q" * n)) != sum(len(range(a, n + 1, 7)) for a in (0, 1, 3)):
+            bad.append(f"dc7 size n={n}")
+    return bad
+
+
 PINS = [pin_examples, pin_closed_forms, pin_bruteforce, pin_random, pin_checker,
-        pin_bwt, pin_rank, pin_lcp, pin_multiplier]
+        pin_bwt, pin_rank, pin_lcp, pin_multiplier, pin_dc7_names]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
