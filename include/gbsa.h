@@ -360,6 +360,31 @@ sa_status sa_lcp(const uint8_t *text, uint64_t n, const uint32_t *sa, uint32_t *
 sa_status sa_build_dc3(const uint8_t *text, uint64_t n, uint32_t *sa_out, uint32_t *trace_names,
                        gbsa_stream_t stream);
 
+/* ---- DC7 (difference cover modulo 7) -----------------------------------
+ * The suffix array by DC7 (Section 2.2, Algorithms 8-10): the suffixes at
+ * the positions of the difference cover D7 = {0, 1, 3} modulo 7 are ranked
+ * by recursion on the string of the names of their 7-character windows;
+ * every position's suffix is then placed within its class i mod 7 by at
+ * most three characters and one sample's rank, and the seven classes are
+ * merged, two suffixes comparing by their first l characters and the ranks
+ * l positions on, l the smallest offset taking both into D7. Same result
+ * as sa_build.
+ * text        : DEVICE, n bytes, read only.
+ * sa_out      : DEVICE, n uint32, written with SA.
+ * trace_names : DEVICE or NULL; if set, m = c0 + c1 + c3 uint32 are
+ *               written, c_a = floor((n - a) / 7) + 1 for a <= n (else 0):
+ *               the top level's recursion string, the 1-based names of the
+ *               7-character windows of the positions i = 0 mod 7 with
+ *               i <= n in text order, then of i = 1 mod 7, then of
+ *               i = 3 mod 7 (3 * (n / 7 + 1) entries always suffice).
+ * Memory (about 100 bytes per character at the top level) comes from the
+ * library's stream-ordered pool; the call synchronises `stream` twice per
+ * recursion level and before returning. Returns SA_ERR_INVALID_ARG for a
+ * NULL text or sa_out with n > 0, SA_ERR_TOO_LARGE for n > SA_MAX_N,
+ * SA_ERR_OOM if memory runs out. n = 0 writes nothing. */
+sa_status sa_build_dc7(const uint8_t *text, uint64_t n, uint32_t *sa_out, uint32_t *trace_names,
+                       gbsa_stream_t stream);
+
 /* Human-readable name of a status code (static string). */
 const char *sa_status_string(sa_status s);
 

@@ -31,7 +31,7 @@ EXPORTED = ("sa_build", "sa_workspace_bytes", "sa_build_ex", "sa_build_batched",
             "sa_sort_pairs", "sa_sort_workspace_bytes", "sa_status_string",
             "sa_build_noalloc", "sa_request_footprint", "sa_server_create", "sa_server_submit",
             "sa_server_poll", "sa_server_wait", "sa_server_get_stats", "sa_server_destroy",
-            "sa_bwt", "sa_lcp", "sa_lcp_workspace_bytes", "sa_build_dc3")
+            "sa_bwt", "sa_lcp", "sa_lcp_workspace_bytes", "sa_build_dc3", "sa_build_dc7")
 
 
 class SAError(RuntimeError):
@@ -135,6 +135,7 @@ def load(path: str | None = None):
     lib.sa_sort_pairs.argtypes = [vp, vp, u64, u32, u32, vp, sz, vp]
     lib.sa_bwt.argtypes = [vp, u64, vp, vp, vp, vp]
     lib.sa_build_dc3.argtypes = [vp, u64, vp, vp, vp]
+    lib.sa_build_dc7.argtypes = [vp, u64, vp, vp, vp]
     lib.sa_lcp.argtypes = [vp, u64, vp, vp, vp, sz, vp]
     lib.sa_lcp_workspace_bytes.argtypes = [u64]
     lib.sa_lcp_workspace_bytes.restype = sz
@@ -332,6 +333,26 @@ def sa_build_dc3(text, trace=False, stream=None):
     _check(lib.sa_build_dc3(t.data_ptr() if n else None, n, sa.data_ptr() if n else None,
                             tr.data_ptr() if tr is not None else None, _stream(stream)),
            "sa_build_dc3")
+    return (sa, tr) if trace else sa
+
+
+def sa_build_dc7(text, trace=False, stream=None):
+    """Suffix array by DC7 (difference cover {0, 1, 3} modulo 7). Returns
+    the int32 SA, and with trace=True also the top level's recursion string
+    (1-based names of the 7-character windows at positions 0, then 1, then
+    3 mod 7, each class up to and including position n)."""
+    torch = _torch()
+    lib = load()
+    t = _dev_u8(text)
+    n = t.numel()
+    sa = torch.empty(n, dtype=torch.int32, device=t.device)
+    tr = None
+    if trace:
+        m = sum((n - a) // 7 + 1 for a in (0, 1, 3) if a <= n)
+        tr = torch.zeros(max(m, 1), dtype=torch.int32, device=t.device)
+    _check(lib.sa_build_dc7(t.data_ptr() if n else None, n, sa.data_ptr() if n else None,
+                            tr.data_ptr() if tr is not None else None, _stream(stream)),
+           "sa_build_dc7")
     return (sa, tr) if trace else sa
 
 
