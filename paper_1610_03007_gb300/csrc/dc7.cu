@@ -207,50 +207,71 @@ __global__ void k_dc7_elts(const uint32_t *__restrict__ t, const uint32_t *__res
   }
 }
 
-// Does suffix x come before suffix y (the comparison of CompareDC7)?
-__device__ __forceinline__ bool less7(const Elt7 &x, const Elt7 &y) {
-  const uint32_t a = x.pos % 7, b = y.pos % 7;
+// The lookup table of CompareDC7 for classes a, b: l = l(a, b) in bits
+// 0-2, the rank slot of a at offset l in bits 3-4, that of b in bits 5-6.
+__device__ __forceinline__ uint32_t cmp7_entry(uint32_t a, uint32_t b) {
   const uint32_t l = l_pair(a, b);
+  return l | (d7_slot((a + l) % 7) << 3) | (d7_slot((b + l) % 7) << 5);
+}
+
+// Does suffix x come before suffix y (the comparison of CompareDC7)? lut
+// holds cmp7_entry for the 49 class pairs.
+__device__ __forceinline__ bool less7(const Elt7 &x, const Elt7 &y, const uint8_t *lut) {
+  const uint32_t e = lut[(x.pos % 7) * 7 + y.pos % 7];
+  const uint32_t l = e & 7u;
   for (uint32_t k = 0; k < l; ++k)
     if (x.c[k] != y.c[k]) return x.c[k] < y.c[k];
-  return x.r[d7_slot((a + l) % 7)] < y.r[d7_slot((b + l) % 7)];
+  return x.r[(e >> 3) & 3u] < y.r[(e >> 5) & 3u];
 }
 
 constexpr int MG7_ITEMS = 4;
 constexpr int MG7_TILE = DC_BLOCK * MG7_ITEMS;
 
-// Elements of A among the first d merged ones (merge path).
-__device__ uint32_t merge7_split(const Elt7 *ea, uint32_t na, const Elt7 *eb, uint32_t nb,
-                                 uint32_t d) {
+__device__ __forceinline__ void load_lut(uint8_t *lut) {
+  for (uint32_t x = threadIdx.x; x < 49; x += blockDim.x) lut[x] = (uint8_t)cmp7_entry(x / 7, x % 7);
+}
+
+// Merge path: split[b] = elements of A among the first min(b * tile, na + nb)
+// merged ones, for b = 0 .. blocks; one thread per block boundary, so that
+// the merge blocks start at once.
+__global__ void __launch_bounds__(DC_BLOCK) k_dc7_splits(const Elt7 *ea, uint32_t na,
+                                                         const Elt7 *eb, uint32_t nb,
+                                                         uint32_t blocks, uint32_t *split) {
+  __shared__ uint8_t lut[49];
+  load_lut(lut);
+  __syncthreads();
+  const uint64_t bidx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (bidx > blocks) return;
+  const uint32_t d = (uint32_t)min(bidx * MG7_TILE, (uint64_t)na + nb);
   uint32_t lo = d > nb ? d - nb : 0u, hi = d < na ? d : na;
   while (lo < hi) {
     const uint32_t mid = (lo + hi) >> 1;
-    if (less7(ea[mid], eb[d - 1 - mid]))
+    if (less7(ea[mid], eb[d - 1 - mid], lut))
       lo = mid + 1;
     else
       hi = mid;
   }
-  return lo;
+  split[bidx] = lo;
 }
 
-// out_e (POS = false) or out_pos (POS = true) = merge of A and B.
+// out_e (POS = false) or out_pos (POS = true) = merge of A and B, block b
+// covering outputs [b * tile, (b + 1) * tile) from the precomputed splits.
 template <bool POS>
 __global__ void __launch_bounds__(DC_BLOCK) k_dc7_merge(const Elt7 *ea, uint32_t na,
                                                         const Elt7 *eb, uint32_t nb,
+                                                        const uint32_t *__restrict__ split,
                                                         Elt7 *out_e, uint32_t *out_pos) {
   __shared__ Elt7 e[MG7_TILE];  // A slice, then B slice
   __shared__ uint16_t pick[MG7_TILE];
-  __shared__ uint32_t split[2];
+  __shared__ uint8_t lut[49];
+  load_lut(lut);
   const uint32_t total = na + nb;
   const uint32_t d0 = blockIdx.x * MG7_TILE;
   const uint32_t d1 = min(d0 + (uint32_t)MG7_TILE, total);
-  if (threadIdx.x == 0) split[0] = merge7_split(ea, na, eb, nb, d0);
-  if (threadIdx.x == 32) split[1] = merge7_split(ea, na, eb, nb, d1);
-  __syncthreads();
-  const uint32_t a0 = split[0], a1 = split[1];
+  const uint32_t a0 = split[blockIdx.x], a1 = split[blockIdx.x + 1];
   const uint32_t b0 = d0 - a0, b1 = d1 - a1;
   const uint32_t sa = a1 - a0, sb = b1 - b0, len = d1 - d0;
-  if (sa > len || sb > len || sa + sb != len) return;  // never taken unless unsorted
+  if (a1 < a0 || sa > len || sb > len || a1 > na) return;  // never taken unless unsorted
   for (uint32_t x = threadIdx.x; x < sa; x += DC_BLOCK) e[x] = ea[a0 + x];
   for (uint32_t x = threadIdx.x; x < sb; x += DC_BLOCK) e[sa + x] = eb[b0 + x];
   __syncthreads();
@@ -258,7 +279,7 @@ __global__ void __launch_bounds__(DC_BLOCK) k_dc7_merge(const Elt7 *ea, uint32_t
   uint32_t lo = dt > sb ? dt - sb : 0u, hi = dt < sa ? dt : sa;
   while (lo < hi) {
     const uint32_t mid = (lo + hi) >> 1;
-    if (less7(e[mid], e[sa + dt - 1 - mid]))
+    if (less7(e[mid], e[sa + dt - 1 - mid], lut))
       lo = mid + 1;
     else
       hi = mid;
@@ -267,7 +288,7 @@ __global__ void __launch_bounds__(DC_BLOCK) k_dc7_merge(const Elt7 *ea, uint32_t
 #pragma unroll
   for (int k = 0; k < MG7_ITEMS; ++k) {
     if (dt + k < len) {
-      const bool take_a = j >= sb || (i < sa && less7(e[i], e[sa + j]));
+      const bool take_a = j >= sb || (i < sa && less7(e[i], e[sa + j], lut));
       pick[dt + k] = (uint16_t)(take_a ? i++ : sa + j++);
     }
   }
@@ -349,15 +370,18 @@ struct Dc7 : DcxRun {
     return SA_OK;
   }
 
+  // split: at least total / tile + 2 words of scratch.
   sa_status merge(const Elt7 *a, uint32_t na, const Elt7 *b, uint32_t nb, Elt7 *out_e,
-                  uint32_t *out_pos) {
+                  uint32_t *out_pos, uint32_t *split) {
     const uint64_t total = (uint64_t)na + nb;
     if (total == 0) return SA_OK;
     const unsigned blocks = (unsigned)((total + MG7_TILE - 1) / MG7_TILE);
+    k_dc7_splits<<<(blocks + DC_BLOCK) / DC_BLOCK, DC_BLOCK, 0, st>>>(a, na, b, nb, blocks,
+                                                                     split);
     if (out_pos)
-      k_dc7_merge<true><<<blocks, DC_BLOCK, 0, st>>>(a, na, b, nb, nullptr, out_pos);
+      k_dc7_merge<true><<<blocks, DC_BLOCK, 0, st>>>(a, na, b, nb, split, nullptr, out_pos);
     else
-      k_dc7_merge<false><<<blocks, DC_BLOCK, 0, st>>>(a, na, b, nb, out_e, nullptr);
+      k_dc7_merge<false><<<blocks, DC_BLOCK, 0, st>>>(a, na, b, nb, split, out_e, nullptr);
     return ok();
   }
 
@@ -452,22 +476,24 @@ struct Dc7 : DcxRun {
 
     // 5. Elements and the merge tree.
     Elt7 *E, *E2;
+    uint32_t *sp;
     if ((s = sc.get(&E, n)) != SA_OK || (s = sc.get(&E2, n)) != SA_OK) return s;
+    if ((s = sc.get(&sp, (uint64_t)n / MG7_TILE + 2)) != SA_OK) return s;
     k_dc7_elts<<<grid(n), DC_BLOCK, 0, st>>>(t, R, n, c0, c1, cls, E);
     if ((s = ok()) != SA_OK) return s;
-    if ((s = merge(E + off[0], size[0], E + off[1], size[1], E2 + off[0], nullptr)) != SA_OK ||
-        (s = merge(E + off[2], size[2], E + off[3], size[3], E2 + off[2], nullptr)) != SA_OK ||
-        (s = merge(E + off[4], size[4], E + off[5], size[5], E2 + off[4], nullptr)) != SA_OK)
+    if ((s = merge(E + off[0], size[0], E + off[1], size[1], E2 + off[0], nullptr, sp)) != SA_OK ||
+        (s = merge(E + off[2], size[2], E + off[3], size[3], E2 + off[2], nullptr, sp)) != SA_OK ||
+        (s = merge(E + off[4], size[4], E + off[5], size[5], E2 + off[4], nullptr, sp)) != SA_OK)
       return s;
     if (size[6] && cudaMemcpyAsync(E2 + off[6], E + off[6], (size_t)size[6] * sizeof(Elt7),
                                    cudaMemcpyDeviceToDevice, st) != cudaSuccess)
       return SA_ERR_CUDA;
     if ((s = merge(E2 + off[0], off[2] - off[0], E2 + off[2], off[4] - off[2], E + off[0],
-                   nullptr)) != SA_OK ||
+                   nullptr, sp)) != SA_OK ||
         (s = merge(E2 + off[4], off[6] - off[4], E2 + off[6], off[7] - off[6], E + off[4],
-                   nullptr)) != SA_OK)
+                   nullptr, sp)) != SA_OK)
       return s;
-    return merge(E, off[4], E + off[4], off[7] - off[4], nullptr, sa);
+    return merge(E, off[4], E + off[4], off[7] - off[4], nullptr, sa, sp);
   }
 };
 
