@@ -125,16 +125,23 @@ __global__ void k_dc7_rekey(const uint32_t *__restrict__ t, uint32_t m, uint32_t
     keys[k] = pack_chars(t, vals[k], lo, hi, b);
 }
 
-// flags[k] = 1 where the window of vals[k] differs from its predecessor's.
+// flags[k] = 1 where the window of vals[k] differs from its predecessor's:
+// from the sorted keys when they hold whole windows (keys != NULL), else
+// from the text.
 __global__ void k_dc7_flags(const uint32_t *__restrict__ t, uint32_t m,
-                            const uint32_t *__restrict__ vals, uint32_t *__restrict__ flags) {
+                            const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                            uint32_t *__restrict__ flags) {
   for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
        k += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t f = 1;
     if (k > 0) {
-      const uint32_t p = vals[k], q = vals[k - 1];
-      f = 0;
-      for (int c = 0; c < 7; ++c) f |= t[p + c] != t[q + c] ? 1u : 0u;
+      if (keys) {
+        f = keys[k] != keys[k - 1] ? 1u : 0u;
+      } else {
+        const uint32_t p = vals[k], q = vals[k - 1];
+        f = 0;
+        for (int c = 0; c < 7; ++c) f |= t[p + c] != t[q + c] ? 1u : 0u;
+      }
     }
     flags[k] = f;
   }
@@ -173,38 +180,58 @@ __global__ void k_dc7_ranks(uint32_t m, const uint32_t *__restrict__ saR, uint32
 
 // A merge element: its position, the ranks of the samples at the offsets
 // l with (pos + l) mod 7 = 0, 1, 3 (0 past n), and its next six characters.
-struct Elt7 {
+// Padded to three 16-byte words, moved with vector loads and stores.
+struct __align__(16) Elt7 {
   uint32_t pos;
   uint32_t r[3];
   uint32_t c[6];
+  uint32_t pad[2];
 };
-static_assert(sizeof(Elt7) == 40, "Elt7 layout");
+static_assert(sizeof(Elt7) == 48, "Elt7 layout");
+constexpr uint32_t ELT7_WORDS = sizeof(Elt7) / 16;
 
-__global__ void k_dc7_elts(const uint32_t *__restrict__ t, const uint32_t *__restrict__ R,
-                           uint32_t n, uint32_t c0, uint32_t c1, const uint32_t *__restrict__ cls,
-                           Elt7 *__restrict__ E) {
+// dst[0, count) = src[0, count) by 16-byte words, the block's threads
+// striding through them.
+__device__ __forceinline__ void copy_elts(Elt7 *dst, const Elt7 *src, uint32_t count) {
+  const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+  uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+  for (uint32_t x = threadIdx.x; x < count * ELT7_WORDS; x += blockDim.x) d4[x] = s4[x];
+}
+
+// One element per thread, staged in shared memory and written out in
+// 16-byte words by consecutive threads.
+__global__ void __launch_bounds__(DC_BLOCK) k_dc7_elts(const uint32_t *__restrict__ t,
+                                                       const uint32_t *__restrict__ R,
+                                                       uint32_t n, uint32_t c0, uint32_t c1,
+                                                       const uint32_t *__restrict__ cls,
+                                                       Elt7 *__restrict__ E) {
+  __shared__ Elt7 buf[DC_BLOCK];
   const uint32_t m = c0 + c1 + class_samples(n, 3);
-  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
-       x += (uint64_t)gridDim.x * blockDim.x) {
+  const uint64_t base = (uint64_t)blockIdx.x * DC_BLOCK;
+  const uint64_t x = base + threadIdx.x;
+  Elt7 e{};
+  if (x < n) {
     const uint32_t i = cls[x];
-    Elt7 e{};
     e.pos = i;
-    if (i >= n) {  // never taken unless a class list is incomplete
-      E[x] = e;
-      continue;
-    }
-    const uint32_t j = i % 7;
+    if (i < n) {  // else a class list is incomplete (never taken)
+      const uint32_t j = i % 7;
 #pragma unroll
-    for (uint32_t d = 0; d < 3; ++d) {
-      const uint32_t target = d == 0 ? 0u : (d == 1 ? 1u : 3u);
-      const uint64_t p = (uint64_t)i + (target + 7 - j) % 7;
-      const uint32_t k = dc7_sample_idx(p, n, c0, c1);
-      e.r[d] = k < m ? R[k] : 0u;
-    }
+      for (uint32_t d = 0; d < 3; ++d) {
+        const uint32_t target = d == 0 ? 0u : (d == 1 ? 1u : 3u);
+        const uint64_t p = (uint64_t)i + (target + 7 - j) % 7;
+        const uint32_t k = dc7_sample_idx(p, n, c0, c1);
+        e.r[d] = k < m ? R[k] : 0u;
+      }
 #pragma unroll
-    for (int c = 0; c < 6; ++c) e.c[c] = t[(uint64_t)i + c];
-    E[x] = e;
+      for (int c = 0; c < 6; ++c) e.c[c] = t[(uint64_t)i + c];
+    }
   }
+  buf[threadIdx.x] = e;
+  __syncthreads();
+  const uint32_t cnt = (uint32_t)min((uint64_t)DC_BLOCK, n > base ? n - base : 0);
+  const uint4 *b4 = reinterpret_cast<const uint4 *>(buf);
+  uint4 *o4 = reinterpret_cast<uint4 *>(E + base);
+  for (uint32_t w = threadIdx.x; w < cnt * ELT7_WORDS; w += DC_BLOCK) o4[w] = b4[w];
 }
 
 // The lookup table of CompareDC7 for classes a, b: l = l(a, b) in bits
@@ -224,7 +251,7 @@ __device__ __forceinline__ bool less7(const Elt7 &x, const Elt7 &y, const uint8_
   return x.r[(e >> 3) & 3u] < y.r[(e >> 5) & 3u];
 }
 
-constexpr int MG7_ITEMS = 4;
+constexpr int MG7_ITEMS = 2;
 constexpr int MG7_TILE = DC_BLOCK * MG7_ITEMS;
 
 __device__ __forceinline__ void load_lut(uint8_t *lut) {
@@ -272,8 +299,8 @@ __global__ void __launch_bounds__(DC_BLOCK) k_dc7_merge(const Elt7 *ea, uint32_t
   const uint32_t b0 = d0 - a0, b1 = d1 - a1;
   const uint32_t sa = a1 - a0, sb = b1 - b0, len = d1 - d0;
   if (a1 < a0 || sa > len || sb > len || a1 > na) return;  // never taken unless unsorted
-  for (uint32_t x = threadIdx.x; x < sa; x += DC_BLOCK) e[x] = ea[a0 + x];
-  for (uint32_t x = threadIdx.x; x < sb; x += DC_BLOCK) e[sa + x] = eb[b0 + x];
+  copy_elts(e, ea + a0, sa);
+  copy_elts(e + sa, eb + b0, sb);
   __syncthreads();
   const uint32_t dt = min((uint32_t)threadIdx.x * MG7_ITEMS, len);
   uint32_t lo = dt > sb ? dt - sb : 0u, hi = dt < sa ? dt : sa;
@@ -293,11 +320,13 @@ __global__ void __launch_bounds__(DC_BLOCK) k_dc7_merge(const Elt7 *ea, uint32_t
     }
   }
   __syncthreads();
-  for (uint32_t x = threadIdx.x; x < len; x += DC_BLOCK) {
-    if (POS)
-      out_pos[d0 + x] = e[pick[x]].pos;
-    else
-      out_e[d0 + x] = e[pick[x]];
+  if (POS) {
+    for (uint32_t x = threadIdx.x; x < len; x += DC_BLOCK) out_pos[d0 + x] = e[pick[x]].pos;
+  } else {
+    uint4 *o4 = reinterpret_cast<uint4 *>(out_e + d0);
+    const uint4 *e4 = reinterpret_cast<const uint4 *>(e);
+    for (uint32_t x = threadIdx.x; x < len * ELT7_WORDS; x += DC_BLOCK)
+      o4[x] = e4[pick[x / ELT7_WORDS] * ELT7_WORDS + x % ELT7_WORDS];
   }
 }
 
@@ -415,7 +444,7 @@ struct Dc7 : DcxRun {
       k_dc7_keys<<<grid(m), DC_BLOCK, 0, st>>>(t, m, c0, c1, b, lo, 7, keys, vals);
       if ((s = ok()) != SA_OK) return s;
       if ((s = sort_chars(t, keys, vals, m, b, 0, 7, true)) != SA_OK) return s;
-      k_dc7_flags<<<grid(m), DC_BLOCK, 0, st>>>(t, m, vals, tmp);
+      k_dc7_flags<<<grid(m), DC_BLOCK, 0, st>>>(t, m, per >= 7 ? keys : nullptr, vals, tmp);
       if ((s = ok()) != SA_OK || (s = scan(tmp, tmp, m, sums)) != SA_OK) return s;
       if (cudaMemsetAsync(R, 0, ((size_t)m + PAD7) * 4, st) != cudaSuccess) return SA_ERR_CUDA;
       k_dc7_scatter_names<<<grid(m), DC_BLOCK, 0, st>>>(m, n, c0, c1, vals, tmp, R);
@@ -479,7 +508,8 @@ struct Dc7 : DcxRun {
     uint32_t *sp;
     if ((s = sc.get(&E, n)) != SA_OK || (s = sc.get(&E2, n)) != SA_OK) return s;
     if ((s = sc.get(&sp, (uint64_t)n / MG7_TILE + 2)) != SA_OK) return s;
-    k_dc7_elts<<<grid(n), DC_BLOCK, 0, st>>>(t, R, n, c0, c1, cls, E);
+    k_dc7_elts<<<(unsigned)(((uint64_t)n + DC_BLOCK - 1) / DC_BLOCK), DC_BLOCK, 0, st>>>(
+        t, R, n, c0, c1, cls, E);
     if ((s = ok()) != SA_OK) return s;
     if ((s = merge(E + off[0], size[0], E + off[1], size[1], E2 + off[0], nullptr, sp)) != SA_OK ||
         (s = merge(E + off[2], size[2], E + off[3], size[3], E2 + off[2], nullptr, sp)) != SA_OK ||
