@@ -288,7 +288,7 @@ def run_plain(args):
     clocks = sampler.stop()
     stats = st
 
-    bwt_ms = lcp_ms = dc3_ms = dc7_ms = None
+    bwt_ms = lcp_ms = dc3_ms = dc7_ms = pds_ms = None
     mult = None
     if not args.build_only:
         # BWT of the built SA through sa_bwt, timed alone on the same stream
@@ -364,6 +364,20 @@ def run_plain(args):
         b1.record(stream)
         torch.cuda.synchronize()
         dc7_ms = b0.elapsed_time(b1) / 2
+
+        # ... and by prefix doubling using sorting (no discarding).
+        def pds_call():
+            rc = lib.sa_build_pd_sort(text.data_ptr(), n, dc3_sa.data_ptr(), None, 0, None,
+                                      stream.cuda_stream)
+            if rc != 0:
+                raise RuntimeError(f"sa_build_pd_sort failed: {rc}")
+
+        pds_call()
+        b0.record(stream)
+        pds_call()
+        b1.record(stream)
+        torch.cuda.synchronize()
+        pds_ms = b0.elapsed_time(b1)
         del dc3_sa
 
         # The same build with a-fold rounds (prefix tripling and quadrupling):
@@ -453,6 +467,9 @@ def run_plain(args):
             "dc7": {"ms": dc7_ms, "value": n / (dc7_ms * 1e-3) / 1e6, "unit": "MB/s",
                     "note": "the same text by sa_build_dc7 (difference cover mod 7), outside "
                             "the timed step"},
+            "pd_sort": {"ms": pds_ms, "value": n / (pds_ms * 1e-3) / 1e6, "unit": "MB/s",
+                        "note": "the same text by sa_build_pd_sort (prefix doubling using "
+                                "sorting, no discarding), outside the timed step"},
             "multiplier": {"by_a": mult, "unit": "MB/s",
                            "note": "the same text with sa_options.multiplier a (a-fold rounds, "
                                    "Prefix Quadrupling); a = 3, 4 outside the timed step"},
@@ -657,7 +674,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--no-tune", action="store_true", help="use the default tile parameters")
     ap.add_argument("--build-only", action="store_true",
-                    help="plain workload: skip the BWT, LCP, DC3, DC7 and multiplier calls "
+                    help="plain workload: skip the BWT, LCP, DC3, DC7, sorting-variant and multiplier calls "
                          "(a launch list of the builds alone)")
     args = ap.parse_args()
     if args.impl == "reference":

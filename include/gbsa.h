@@ -385,6 +385,30 @@ sa_status sa_build_dc3(const uint8_t *text, uint64_t n, uint32_t *sa_out, uint32
 sa_status sa_build_dc7(const uint8_t *text, uint64_t n, uint32_t *sa_out, uint32_t *trace_names,
                        gbsa_stream_t stream);
 
+/* ---- Prefix doubling using sorting -------------------------------------
+ * The suffix array by prefix doubling without discarding, with the partner
+ * names fetched by sorting instead of through the inverse suffix array
+ * (Section 2.1, Algorithms 1, 2 and 3): every round sorts all n suffixes
+ * by their name pair, names them by CmpName and PrefixSum(max) (head
+ * ranks), and unless all names differ sorts the (position, name) items by
+ * the comparator of Eq. 1, (i mod 2^k, i div 2^k), so that each name's
+ * partner i + 2^k is its successor. The initial names are the character
+ * pairs (T[i], T[i+1]) with T[n] = $. Same result as sa_build.
+ * text        : DEVICE, n bytes, read only.
+ * sa_out      : DEVICE, n uint32, written with SA.
+ * trace_names : DEVICE or NULL; if set, trace_cap * n uint32: row r holds
+ *               every position's name after the r-th naming (row 0: the
+ *               character pairs), for r < trace_cap.
+ * rounds      : HOST or NULL; receives the number of namings.
+ * Memory comes from the library's stream-ordered pool; the call
+ * synchronises `stream` once per round and before returning. Returns
+ * SA_ERR_INVALID_ARG for a NULL text or sa_out with n > 0,
+ * SA_ERR_TOO_LARGE for n > SA_MAX_N, SA_ERR_OOM if memory runs out.
+ * n = 0 writes nothing. */
+sa_status sa_build_pd_sort(const uint8_t *text, uint64_t n, uint32_t *sa_out,
+                           uint32_t *trace_names, uint32_t trace_cap, uint32_t *rounds,
+                           gbsa_stream_t stream);
+
 /* Human-readable name of a status code (static string). */
 const char *sa_status_string(sa_status s);
 

@@ -31,7 +31,8 @@ EXPORTED = ("sa_build", "sa_workspace_bytes", "sa_build_ex", "sa_build_batched",
             "sa_sort_pairs", "sa_sort_workspace_bytes", "sa_status_string",
             "sa_build_noalloc", "sa_request_footprint", "sa_server_create", "sa_server_submit",
             "sa_server_poll", "sa_server_wait", "sa_server_get_stats", "sa_server_destroy",
-            "sa_bwt", "sa_lcp", "sa_lcp_workspace_bytes", "sa_build_dc3", "sa_build_dc7")
+            "sa_bwt", "sa_lcp", "sa_lcp_workspace_bytes", "sa_build_dc3", "sa_build_dc7",
+            "sa_build_pd_sort")
 
 
 class SAError(RuntimeError):
@@ -136,6 +137,7 @@ def load(path: str | None = None):
     lib.sa_bwt.argtypes = [vp, u64, vp, vp, vp, vp]
     lib.sa_build_dc3.argtypes = [vp, u64, vp, vp, vp]
     lib.sa_build_dc7.argtypes = [vp, u64, vp, vp, vp]
+    lib.sa_build_pd_sort.argtypes = [vp, u64, vp, vp, u32, vp, vp]
     lib.sa_lcp.argtypes = [vp, u64, vp, vp, vp, sz, vp]
     lib.sa_lcp_workspace_bytes.argtypes = [u64]
     lib.sa_lcp_workspace_bytes.restype = sz
@@ -354,6 +356,25 @@ def sa_build_dc7(text, trace=False, stream=None):
                             tr.data_ptr() if tr is not None else None, _stream(stream)),
            "sa_build_dc7")
     return (sa, tr) if trace else sa
+
+
+def sa_build_pd_sort(text, trace_cap=0, stream=None):
+    """Suffix array by prefix doubling using sorting (no discarding; the
+    partner names by a sort with Eq. 1's comparator). Returns (sa, trace,
+    rounds): trace[r] holds every position's name after the r-th naming
+    (None when trace_cap = 0), rounds the number of namings."""
+    torch = _torch()
+    lib = load()
+    t = _dev_u8(text)
+    n = t.numel()
+    sa = torch.empty(n, dtype=torch.int32, device=t.device)
+    tr = torch.zeros((trace_cap, n), dtype=torch.int32, device=t.device) if trace_cap else None
+    rounds = ctypes.c_uint32(0)
+    _check(lib.sa_build_pd_sort(t.data_ptr() if n else None, n, sa.data_ptr() if n else None,
+                                tr.data_ptr() if tr is not None and n else None, trace_cap,
+                                ctypes.byref(rounds), _stream(stream)),
+           "sa_build_pd_sort")
+    return sa, tr, int(rounds.value)
 
 
 def sa_lcp(text, sa, workspace=None, stream=None):

@@ -80,6 +80,10 @@ def test_host_side_argument_checks(lib):
     assert lib.sa_build_dc7(None, 5, None, None, None) == 1
     assert lib.sa_build_dc7(8, (1 << 31) + 1, 8, None, None) == 2
     assert lib.sa_build_dc7(None, 0, None, None, None) == 0
+    # prefix doubling using sorting: the same argument checks
+    assert lib.sa_build_pd_sort(None, 5, None, None, 0, None, None) == 1
+    assert lib.sa_build_pd_sort(8, (1 << 31) + 1, 8, None, 0, None, None) == 2
+    assert lib.sa_build_pd_sort(None, 0, None, None, 0, None, None) == 0
 
 
 def test_workspace_model(lib):
