@@ -659,13 +659,81 @@ def run_serving(args):
     return line
 
 
+EXTRA_CALLS = ("bwt", "lcp", "dc3", "dc7", "pd_sort", "quad")
+
+
+def run_extra(args):
+    """One of the paths beside the hot path, alone, on the configuration-2
+    text (or --n characters of its recipe): W untimed calls, K calls timed
+    with CUDA events on the launching stream. bwt and lcp take the SA from
+    one sa_build outside the timed calls; quad is sa_build_ex with
+    multiplier 4."""
+    import torch
+
+    import gen
+    import paper_1610_03007_gb300 as gbsa
+    from paper_1610_03007_gb300 import _build
+
+    _build.build()
+    lib = gbsa.load()
+    n = args.n or PLAIN_N
+    dev = torch.device("cuda", 0)
+    text = torch.from_numpy(gen.text("zipf_repeats", PLAIN_SEED, n)).to(dev)
+    stream = torch.cuda.current_stream()
+    out = torch.empty(n + 1, dtype=torch.int32, device=dev)
+    st = stream.cuda_stream
+    kind = args.workload
+    if kind in ("bwt", "lcp"):
+        sa = gbsa.sa_build(text)
+        prim = torch.zeros(1, dtype=torch.int64, device=dev)
+        lws = torch.empty(int(lib.sa_lcp_workspace_bytes(n)), dtype=torch.uint8, device=dev)
+
+    def call():
+        if kind == "bwt":
+            rc = lib.sa_bwt(text.data_ptr(), n, sa.data_ptr(), out.data_ptr(), prim.data_ptr(), st)
+        elif kind == "lcp":
+            rc = lib.sa_lcp(text.data_ptr(), n, sa.data_ptr(), out.data_ptr(), lws.data_ptr(),
+                            lws.numel(), st)
+        elif kind == "dc3":
+            rc = lib.sa_build_dc3(text.data_ptr(), n, out.data_ptr(), None, st)
+        elif kind == "dc7":
+            rc = lib.sa_build_dc7(text.data_ptr(), n, out.data_ptr(), None, st)
+        elif kind == "pd_sort":
+            rc = lib.sa_build_pd_sort(text.data_ptr(), n, out.data_ptr(), None, 0, None, st)
+        else:
+            gbsa.sa_build_ex(text, multiplier=4)
+            rc = 0
+        if rc != 0:
+            raise RuntimeError(f"{kind} failed: {rc}")
+
+    for _ in range(max(args.warmup, 0)):
+        call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    line = {"metric": "input MB/s", "value": n / (ms * 1e-3) / 1e6, "unit": "MB/s",
+            "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": f"{kind} on the repeated-Zipf recipe (Zipf(1.1) base over "
+                                   f"bytes 1..255 x256 copies, 0.1% substitutions), n={n}",
+                       "seed": PLAIN_SEED}}
+    print(json.dumps(line), flush=True)
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving"])
+    ap.add_argument("--workload", default="plain",
+                    choices=["plain", "batched", "serving"] + list(EXTRA_CALLS))
     ap.add_argument("--requests", type=int, default=0, help="requests per rate (serving)")
     ap.add_argument("--rates", default="", help="comma-separated offered rates (serving)")
     ap.add_argument("--slots", type=int, default=16, help="server slots (serving)")
@@ -683,6 +751,8 @@ def main():
         run_batched(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload in EXTRA_CALLS:
+        run_extra(args)
     else:
         run_plain(args)
 
