@@ -288,6 +288,21 @@ def run_plain(args):
     clocks = sampler.stop()
     stats = st
 
+    # End to end through the host entry point: pinned host text in, host SA
+    # out, copies inside the timed region (right after the timed steps, before
+    # the other paths below fill the library's memory pool).
+    h_text = torch.from_numpy(t_host).pin_memory()
+    h_sa = torch.empty(n, dtype=torch.int32).pin_memory()
+    gbsa.sa_build_host_ptr(h_text.data_ptr(), n, h_sa.data_ptr())
+    torch.cuda.synchronize()
+    e_steps = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(e_steps):
+        gbsa.sa_build_host_ptr(h_text.data_ptr(), n, h_sa.data_ptr())
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) / e_steps * 1e3
+    del h_text, h_sa
+
     bwt_ms = lcp_ms = dc3_ms = dc7_ms = pds_ms = None
     mult = None
     if not args.build_only:
@@ -394,20 +409,8 @@ def run_plain(args):
         for v in mult.values():
             v["value"] = n / (v["ms"] * 1e-3) / 1e6
 
-    # End to end through the host entry point: pinned host text in, host SA
-    # out, copies inside the timed region.
-    h_text = torch.from_numpy(t_host).pin_memory()
-    h_sa = torch.empty(n, dtype=torch.int32).pin_memory()
     del ws
     torch.cuda.empty_cache()
-    gbsa.sa_build_host_ptr(h_text.data_ptr(), n, h_sa.data_ptr())
-    torch.cuda.synchronize()
-    e_steps = max(1, min(args.steps, 5))
-    t0 = time.perf_counter()
-    for _ in range(e_steps):
-        gbsa.sa_build_host_ptr(h_text.data_ptr(), n, h_sa.data_ptr())
-    torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t0) / e_steps * 1e3
 
     if rank != 0:
         if pg:
