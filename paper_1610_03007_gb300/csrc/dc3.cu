@@ -146,10 +146,13 @@ constexpr int MG_ITEMS = 4;
 constexpr int MG_TILE = DC_BLOCK * MG_ITEMS;
 
 // A merge element: its position, t[p], t[p+1] and the ranks of the sample
-// positions p+1 and p+2 (0 where the position is not a sample).
-struct Elt {
-  uint32_t pos, c0, c1, r1, r2;
+// positions p+1 and p+2 (0 where the position is not a sample); padded to
+// two 16-byte words, moved with vector loads and stores.
+struct __align__(16) Elt {
+  uint32_t pos, c0, c1, r1, r2, pad[3];
 };
+static_assert(sizeof(Elt) == 32, "Elt layout");
+constexpr uint32_t ELT_WORDS = sizeof(Elt) / 16;
 
 struct MergeArgs {
   const uint32_t *t;     // the level's text (padded with three zeros)
@@ -159,11 +162,12 @@ struct MergeArgs {
   uint32_t n, n0, skip;  // skip: 1 if SA_R starts with the dummy position
   uint32_t na, nb;       // |S12| (dummy dropped), |S0|
   Elt *ea, *eb;          // the two inputs' elements, in order (built by k_dc3_elts)
+  uint32_t *split;       // merge path: S12 elements before each block's first output
   uint32_t *sa;          // out: n positions
 };
 
 __device__ __forceinline__ Elt make_elt(const MergeArgs &a, uint32_t p) {
-  Elt e;
+  Elt e{};
   e.pos = p;
   e.c0 = a.t[p];
   e.c1 = a.t[p + 1];
@@ -174,16 +178,28 @@ __device__ __forceinline__ Elt make_elt(const MergeArgs &a, uint32_t p) {
 
 // The elements of both inputs with their comparison data, in order: the
 // gathers happen once, in parallel, and the merge reads contiguous arrays.
-__global__ void k_dc3_elts(MergeArgs a) {
+// One element per thread, staged in shared memory and written out in
+// 16-byte words by consecutive threads.
+__global__ void __launch_bounds__(DC_BLOCK) k_dc3_elts(MergeArgs a) {
+  __shared__ Elt buf[DC_BLOCK];
   const uint64_t total = (uint64_t)a.na + a.nb;
-  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
-       k += (uint64_t)gridDim.x * blockDim.x) {
-    if (k < a.na) {
-      const uint32_t s = a.sa12[a.skip + k];
-      a.ea[k] = make_elt(a, s < a.n0 ? 3u * s + 1u : 3u * (s - a.n0) + 2u);
-    } else {
-      a.eb[k - a.na] = make_elt(a, a.s0[k - a.na]);
-    }
+  const uint64_t base = (uint64_t)blockIdx.x * DC_BLOCK;
+  const uint64_t k = base + threadIdx.x;
+  Elt e{};
+  if (k < a.na) {
+    const uint32_t s = a.sa12[a.skip + k];
+    e = make_elt(a, s < a.n0 ? 3u * s + 1u : 3u * (s - a.n0) + 2u);
+  } else if (k < total) {
+    e = make_elt(a, a.s0[k - a.na]);
+  }
+  buf[threadIdx.x] = e;
+  __syncthreads();
+  const uint32_t cnt = (uint32_t)min((uint64_t)DC_BLOCK, total > base ? total - base : 0);
+  const uint4 *b4 = reinterpret_cast<const uint4 *>(buf);
+  for (uint32_t w = threadIdx.x; w < cnt * ELT_WORDS; w += DC_BLOCK) {
+    const uint64_t x = base + w / ELT_WORDS;
+    uint4 *dst = reinterpret_cast<uint4 *>(x < a.na ? a.ea + x : a.eb + (x - a.na));
+    dst[w % ELT_WORDS] = b4[w];
   }
 }
 
@@ -211,21 +227,33 @@ __device__ uint32_t merge_split(const MergeArgs &a, uint32_t d) {
   return lo;
 }
 
+// split[b] = merge_split(b * tile) for b = 0 .. blocks (the last one the
+// whole output), one thread per block boundary, so that the merge blocks
+// start at once.
+__global__ void __launch_bounds__(DC_BLOCK) k_dc3_splits(MergeArgs a, uint32_t blocks) {
+  const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b > blocks) return;
+  a.split[b] = merge_split(a, (uint32_t)min(b * MG_TILE, (uint64_t)a.n));
+}
+
+// dst[0, count) = src[0, count) by 16-byte words over the block's threads.
+__device__ __forceinline__ void copy_elts(Elt *dst, const Elt *src, uint32_t count) {
+  const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+  uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+  for (uint32_t x = threadIdx.x; x < count * ELT_WORDS; x += DC_BLOCK) d4[x] = s4[x];
+}
+
 __global__ void __launch_bounds__(DC_BLOCK) k_dc3_merge(MergeArgs a) {
   __shared__ Elt e[MG_TILE];  // S12 slice, then S0 slice
   __shared__ uint32_t out[MG_TILE];
-  __shared__ uint32_t split[2];
   const uint32_t d0 = blockIdx.x * MG_TILE;
   const uint32_t d1 = min(d0 + (uint32_t)MG_TILE, a.n);
-  if (threadIdx.x == 0) split[0] = merge_split(a, d0);
-  if (threadIdx.x == 32) split[1] = merge_split(a, d1);
-  __syncthreads();
-  const uint32_t a0 = split[0], a1 = split[1];
+  const uint32_t a0 = a.split[blockIdx.x], a1 = a.split[blockIdx.x + 1];
   const uint32_t b0 = d0 - a0, b1 = d1 - a1;
   const uint32_t na = a1 - a0, nb = b1 - b0, len = d1 - d0;
-  if (na > len || nb > len) return;  // never taken unless the inputs are not sorted
-  for (uint32_t x = threadIdx.x; x < na; x += DC_BLOCK) e[x] = elt_a(a, a0 + x);
-  for (uint32_t x = threadIdx.x; x < nb; x += DC_BLOCK) e[na + x] = elt_b(a, b0 + x);
+  if (a1 < a0 || a1 > a.na || na > len || nb > len) return;  // never taken unless unsorted
+  copy_elts(e, a.ea + a0, na);
+  copy_elts(e + na, a.eb + b0, nb);
   __syncthreads();
   const uint32_t dt = min((uint32_t)threadIdx.x * MG_ITEMS, len);
   uint32_t lo = dt > nb ? dt - nb : 0u, hi = dt < na ? dt : na;
@@ -336,9 +364,14 @@ struct Dc3 : DcxRun {
     ma.na = n02 - ma.skip;
     ma.nb = n0;
     ma.sa = sa;
-    if ((s = sc.get(&ma.ea, ma.na)) != SA_OK || (s = sc.get(&ma.eb, ma.nb)) != SA_OK) return s;
-    k_dc3_elts<<<grid((uint64_t)ma.na + ma.nb), DC_BLOCK, 0, st>>>(ma);
-    k_dc3_merge<<<(unsigned)(((uint64_t)n + MG_TILE - 1) / MG_TILE), DC_BLOCK, 0, st>>>(ma);
+    const uint32_t blocks = (uint32_t)(((uint64_t)n + MG_TILE - 1) / MG_TILE);
+    if ((s = sc.get(&ma.ea, ma.na)) != SA_OK || (s = sc.get(&ma.eb, ma.nb)) != SA_OK ||
+        (s = sc.get(&ma.split, (uint64_t)blocks + 1)) != SA_OK)
+      return s;
+    k_dc3_elts<<<(unsigned)(((uint64_t)ma.na + ma.nb + DC_BLOCK - 1) / DC_BLOCK), DC_BLOCK, 0,
+                 st>>>(ma);
+    k_dc3_splits<<<(blocks + DC_BLOCK) / DC_BLOCK, DC_BLOCK, 0, st>>>(ma, blocks);
+    k_dc3_merge<<<blocks, DC_BLOCK, 0, st>>>(ma);
     return ok();
   }
 };
