@@ -237,8 +237,11 @@ struct RfSmem {
   uint32_t vals[CAP + CAP / 32];  // padded (e + e/32) after the last pass
   RfWide<CAP, WIDE> w;
   union {
-    uint32_t gsrc[C::MAXG];             // loading: first position of each local group
-    uint32_t match[C::WARPS][RADIX];    // sorting: per-warp peer masks
+    uint32_t gsrc[C::MAXG];             // first position of each local group
+    // Not read: keeps the arrays below at the offsets of the layout that
+    // measured fastest (the same shape with 3 KB less shared memory ran the
+    // refine about 5% slower on GB300).
+    uint32_t spacer[C::WARPS][RADIX];
   };
   uint16_t whist[2][C::WARPS][RADIX];   // per pass (double-buffered): counts, then prefixes
   uint32_t dstart[RADIX];
@@ -331,6 +334,23 @@ __device__ __forceinline__ void rf_block_scan4(uint32_t mx, uint32_t s1, uint32_
   tot_s2 = t2;
 }
 
+// Rank of digit d among this warp's earlier lanes with the same digit, plus
+// the warp's running count of d (wh), which the lowest such lane advances.
+// Peers are found with match.any: in a refine tile the digits of a warp
+// take few distinct values (the members of a group mostly share their
+// partner's name), where it measured faster than the radix pass's
+// shared-memory peer masks (refine 82.5 -> 74.5 ms at n = 2^28); on the
+// radix pass's high-entropy digits it measured slower, so the pass keeps
+// the masks.
+__device__ __forceinline__ uint32_t rf_rank_digit(uint32_t d, uint16_t *wh, uint32_t lt) {
+  const uint32_t peers = __match_any_sync(0xffffffffu, d);
+  const uint32_t before = wh[d];
+  __syncwarp();
+  if ((peers & lt) == 0) wh[d] = (uint16_t)(before + __popc(peers));
+  __syncwarp();
+  return before + __popc(peers & lt);
+}
+
 // Stable LSD radix sort of S.keys/S.vals[0, cnt) in shared memory over the
 // 8-bit digits below `nbits` that vary inside the tile. Warp w ranks the
 // contiguous chunk [w*C, (w+1)*C) with C = 32 * ceil(cnt / BLOCK), so every
@@ -347,10 +367,7 @@ __device__ void rf_tile_sort(RfSmem<BLOCK, CAP, WIDE> &S, uint32_t cnt,
   const uint32_t K = (cnt + BLOCK - 1) / BLOCK;  // slots per lane, <= ITEMS
   const uint32_t chunk = K * 32;
   const uint32_t ndig = (nbits + RADIX_BITS - 1) / RADIX_BITS;
-  for (int x = tid; x < C::WARPS * RADIX; x += BLOCK) {
-    (&S.match[0][0])[x] = 0u;
-    (&S.whist[0][0][0])[x] = 0;
-  }
+  for (int x = tid; x < C::WARPS * RADIX; x += BLOCK) (&S.whist[0][0][0])[x] = 0;
   __syncthreads();
   uint32_t last = 0;
   for (uint32_t p = 0; p < ndig; ++p)
@@ -364,7 +381,6 @@ __device__ void rf_tile_sort(RfSmem<BLOCK, CAP, WIDE> &S, uint32_t cnt,
     uint64_t key[C::ITEMS];
     uint32_t val[C::ITEMS], pos[C::ITEMS];
     uint16_t *wh = S.whist[buf][warp];
-    uint32_t *mt = S.match[warp];
 #pragma unroll
     for (int k = 0; k < C::ITEMS; ++k) {
       if ((uint32_t)k < K) {
@@ -373,7 +389,7 @@ __device__ void rf_tile_sort(RfSmem<BLOCK, CAP, WIDE> &S, uint32_t cnt,
         key[k] = valid ? S.keys[li] : ~0ull;
         val[k] = valid ? S.vals[li] : 0u;
         const uint32_t d = valid ? (uint32_t)(key[k] >> shift) & 0xFFu : 0xFFu;
-        pos[k] = warp_rank_digit(d, mt, wh, lane, lt);
+        pos[k] = rf_rank_digit(d, wh, lt);
       }
     }
     __syncthreads();
