@@ -65,6 +65,7 @@ struct SortPlan {
   uint32_t final_idx;  // 0: result in buffer A, 1: in buffer B
   const uint64_t *kfinal;
   const uint32_t *vfinal;
+  uint32_t match_mask;  // bit p: pass p ranks with match.any (low-entropy digit)
 };
 
 // Digit positions of one sort: pass p covers key bits [shift[p], shift[p]+bits[p]).
@@ -344,6 +345,18 @@ __device__ __forceinline__ uint32_t warp_rank_digit(uint32_t d, uint32_t *match,
   }
   __syncwarp();
   return before + __popc(lower);
+}
+
+// The same rank with the peers found by match.any: faster than the masks
+// when a warp's digits take few distinct values (their atomics then
+// serialise on a few words), slower when they take many.
+__device__ __forceinline__ uint32_t warp_rank_digit_match(uint32_t d, uint16_t *wh, uint32_t lt) {
+  const uint32_t peers = __match_any_sync(0xffffffffu, d);
+  const uint32_t before = wh[d];
+  __syncwarp();
+  if ((peers & lt) == 0) wh[d] = (uint16_t)(before + __popc(peers));
+  __syncwarp();
+  return before + __popc(peers & lt);
 }
 
 // Local index of gapped position ip: text s occupies the gapped positions

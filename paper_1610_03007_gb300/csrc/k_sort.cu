@@ -74,13 +74,21 @@ cudaError_t launch_digit_histogram(const uint64_t *keys, uint32_t m, const Digit
 
 // ---- 2. plan ---------------------------------------------------------------
 
+// Passes whose digits a 32-key warp is expected to spread over at most this
+// many values rank with match.any (repeated Zipf bytes: about 20; uniform
+// DNA or bytes: 28 to 30, where the masks measured faster).
+constexpr float MATCH_RANK_MAX_DISTINCT = 24.f;
+
 __global__ void __launch_bounds__(RADIX)
 k_sort_plan(const uint32_t *__restrict__ hist, uint32_t *__restrict__ digit_base, DigitSpec spec,
             uint32_t m, uint64_t *ka, uint64_t *kb, uint32_t *va, uint32_t *vb,
             SortPlan *plan, Ctrl *ctrl) {
   __shared__ uint32_t s_tmp[RADIX / 32 + 1];
   __shared__ uint32_t s_active[MAX_PASSES];
+  __shared__ float s_e[RADIX / 32];
+  __shared__ uint32_t s_match;
   const uint32_t d = threadIdx.x;
+  if (d == 0) s_match = 0u;
   for (uint32_t p = 0; p < spec.P; ++p) {
     const uint32_t c = hist[p * RADIX + d];
     uint32_t total;
@@ -89,6 +97,26 @@ k_sort_plan(const uint32_t *__restrict__ hist, uint32_t *__restrict__ digit_base
     // A digit position is constant iff one bin holds every key.
     const int constant = __syncthreads_or(c == m);
     if (d == 0) s_active[p] = constant ? 0u : 1u;
+    // Expected distinct digits among 32 keys drawn from this histogram:
+    // sum over d of 1 - (1 - p_d)^32. Few (a skewed alphabet) -> the pass
+    // ranks with match.any, else with the shared-memory masks.
+    float q = m ? 1.f - (float)c / (float)m : 1.f;
+    q *= q;
+    q *= q;
+    q *= q;
+    q *= q;
+    q *= q;
+    float e = 1.f - q;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if ((d & 31) == 0) s_e[d >> 5] = e;
+    __syncthreads();
+    if (d == 0) {
+      float all = 0.f;
+      for (int w = 0; w < RADIX / 32; ++w) all += s_e[w];
+      if (all <= MATCH_RANK_MAX_DISTINCT) s_match |= 1u << p;
+    }
+    __syncthreads();
   }
   __syncthreads();
   if (d == 0) {
@@ -109,6 +137,7 @@ k_sort_plan(const uint32_t *__restrict__ hist, uint32_t *__restrict__ digit_base
       }
     }
     plan->n_active = kept;
+    plan->match_mask = s_match;
     plan->final_idx = cur;
     plan->kfinal = k[cur];
     plan->vfinal = v[cur];
@@ -234,13 +263,20 @@ __global__ void __launch_bounds__(OS_BLOCK, OS_ITEMS >= 16 ? 3 : (OS_ITEMS >= 12
     status_store(st, status_word(a.epoch, tile == 0 ? ST_INC : ST_AGG, mine));
   }
 
-  // Rank within the tile: stable, by per-warp peer masks and counts.
+  // Rank within the tile: stable, by per-warp peers and counts (peers by
+  // match.any on the plan's low-entropy passes, else by the masks).
   uint16_t *wh = S.whist[warp];
   uint32_t *mt = S.match[warp];
   const uint32_t lt = lanemask_lt();
+  if ((a.plan->match_mask >> a.p) & 1u) {
 #pragma unroll
-  for (int k = 0; k < OS_ITEMS; ++k)
-    pos[k] = warp_rank_digit(digit_of(key[k], a.shift, a.bits), mt, wh, lane, lt);
+    for (int k = 0; k < OS_ITEMS; ++k)
+      pos[k] = warp_rank_digit_match(digit_of(key[k], a.shift, a.bits), wh, lt);
+  } else {
+#pragma unroll
+    for (int k = 0; k < OS_ITEMS; ++k)
+      pos[k] = warp_rank_digit(digit_of(key[k], a.shift, a.bits), mt, wh, lane, lt);
+  }
   __syncthreads();
 
   // Thread d: counts of digit d per warp -> per-warp exclusive prefixes.
