@@ -1,6 +1,6 @@
 """GPU unit tests of the building blocks through the C-ABI: the one-sweep
-radix sort (stability, ragged sizes, skipped digits, bit ranges), the
-batched build, and the bounded-wait failure path."""
+radix sort (stability, ragged sizes, skipped digits, bit ranges, both
+ranking methods), the batched build, and the bounded-wait failure path."""
 import numpy as np
 import pytest
 
@@ -53,6 +53,25 @@ def test_sort_bit_ranges_are_stable(gb, lo, hi):
     vals = rng.integers(0, 2**32, m, dtype=np.uint64).astype(np.uint32)
     gk, gv = sort_on_gpu(gb, keys, vals, lo, hi)
     rk, rv = reference_sort(keys, vals, lo, hi)
+    assert np.array_equal(gk, rk) and np.array_equal(gv, rv)
+
+
+@pytest.mark.parametrize("m", [4097, 300007])
+def test_sort_mixed_digit_entropy(gb, m):
+    """Passes ranked both ways in one sort: the plan ranks a pass with
+    match.any when its histogram predicts few distinct digits per warp
+    (bits 8-15 Zipf-skewed, bits 24-31 two values, bits 40-47 one value in
+    ninety) and with the shared-memory masks otherwise (bits 0-7 and 32-39
+    uniform); bits 16-23 are constant (skipped). Stable, element-wise."""
+    rng = np.random.default_rng(m + 5)
+    u = lambda lo_, hi_: rng.integers(lo_, hi_, m, dtype=np.uint64)
+    zipf = np.minimum(rng.zipf(1.3, m), 255).astype(np.uint64)
+    rare = np.where(rng.random(m) < 1 / 90, np.uint64(7), np.uint64(3))
+    keys = (u(0, 256) | (zipf << np.uint64(8)) | (np.uint64(0x5A) << np.uint64(16))
+            | (u(0, 2) << np.uint64(24)) | (u(0, 256) << np.uint64(32)) | (rare << np.uint64(40)))
+    vals = np.arange(m, dtype=np.uint32)
+    gk, gv = sort_on_gpu(gb, keys, vals, 0, 48)
+    rk, rv = reference_sort(keys, vals, 0, 48)
     assert np.array_equal(gk, rk) and np.array_equal(gv, rv)
 
 
