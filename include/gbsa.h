@@ -327,7 +327,9 @@ sa_status sa_bwt(const uint8_t *text, uint64_t n, const uint32_t *sa, uint8_t *b
  * text      : DEVICE, n bytes, read only.
  * sa        : DEVICE, n uint32, the suffix array of text (sa_build).
  * lcp_out   : DEVICE, n uint32, written.
- * workspace : DEVICE, ws_bytes >= sa_lcp_workspace_bytes(n), 256-byte
+ * workspace : DEVICE, ws_bytes >= sa_lcp_workspace_bytes(n) (about 20 bytes
+ *             per character plus 1 MiB: Phi, PLCP and, from 2^20
+ *             characters on, the Phi writes grouped by position), 256-byte
  *             aligned; NULL to have it allocated and freed stream-ordered
  *             on `stream` (cudaMallocAsync).
  * Stream-ordered on `stream`. Returns SA_ERR_INVALID_ARG for a NULL text,
