@@ -94,3 +94,32 @@ def test_workspace_model(lib):
     for n in (1 << 20, 1 << 28, 1 << 31):
         b = lib.sa_workspace_bytes(n)
         assert 66 * n < b < 68 * n + (2 << 20)
+
+
+def test_multiplier_option_is_checked_on_the_host(lib):
+    """sa_options.multiplier outside {0, 2, 3, 4} is refused before any GPU
+    work, on the single and the batched entry points; n = 0 with a valid
+    multiplier returns at once."""
+    import paper_1610_03007_gb300 as gbsa
+    for bad in (1, 5, 64):
+        opt = gbsa.Options(multiplier=bad)
+        assert lib.sa_build_ex(8, 100, 8, None, None, 0, ctypes.byref(opt), None, None) == 1
+        off = np.array([0, 100], dtype=np.uint64)
+        assert lib.sa_build_batched_ex(8, off.ctypes.data, 1, 8, None, 0, ctypes.byref(opt),
+                                       None, None) == 1
+    for good in (0, 2, 3, 4):
+        opt = gbsa.Options(multiplier=good)
+        assert lib.sa_build_ex(None, 0, None, None, None, 0, ctypes.byref(opt), None, None) == 0
+
+
+def test_binding_fails_loudly_without_the_library_or_a_gpu_tensor():
+    """No CPU fallback: a missing library and a host tensor both raise."""
+    import torch
+
+    import paper_1610_03007_gb300 as gbsa
+    with pytest.raises(RuntimeError, match="not built"):
+        gbsa.load(os.path.join(ROOT, "no_such_dir", "libgbsa.so"))
+    with pytest.raises(TypeError):
+        gbsa.sa_build(torch.zeros(16, dtype=torch.uint8))
+    with pytest.raises(TypeError):
+        gbsa.sa_build_dc7(torch.zeros(16, dtype=torch.uint8))
