@@ -41,7 +41,7 @@ def build(mutant: int = 0, force: bool = False) -> str:
     return out
 
 
-MUTANTS = (1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13)
+MUTANTS = (1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16)
 
 
 class Oracle:

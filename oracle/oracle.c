@@ -330,8 +330,25 @@ int64_t oracle_check_adjacent(const uint8_t *T, int64_t n, const uint32_t *sa,
   int64_t bad = 0;
   for (int64_t k = 0; k < count; ++k) {
     int64_t j = idx[k];
-    if (j < 0 || j + 1 >= n) continue;
-    if (sa[j] >= n || sa[j + 1] >= n || cmp_suffix(T, n, sa[j], sa[j + 1]) >= 0) ++bad;
+#if ORACLE_MUTANT == 15
+    if (j <= 0 || j + 1 >= n) continue; /* mutant: the first pair never checked */
+#else
+    if (j < 0 || j + 1 >= n) continue; /* no pair (j, j+1) inside SA */
+#endif
+    if (sa[j] >= n || sa[j + 1] >= n) {
+      ++bad;
+      continue;
+    }
+#if ORACLE_MUTANT == 14
+    const int c = cmp_suffix(T, n, sa[j + 1], sa[j]); /* mutant: operands swapped */
+#else
+    const int c = cmp_suffix(T, n, sa[j], sa[j + 1]);
+#endif
+#if ORACLE_MUTANT == 16
+    if (c > 0) ++bad; /* mutant: equal suffixes (a repeated entry) pass */
+#else
+    if (c >= 0) ++bad; /* SA[j]'s suffix must be strictly smaller */
+#endif
   }
   return bad;
 }

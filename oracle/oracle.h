@@ -97,9 +97,12 @@ int oracle_check_sa(const uint8_t *T, int64_t n, const uint32_t *sa, int64_t *ba
  * *bad. Linear time, n / 8 bytes of memory. */
 int oracle_check_permutation(const uint32_t *sa, int64_t n, int64_t *bad);
 
-/* Direct lexicographic check of sampled adjacent pairs:
- * T[SA[j],n) < T[SA[j+1],n) for j in idx[0..count). Returns the number of
- * violations. */
+/* Direct lexicographic check of sampled adjacent pairs (Section 2: SA lists
+ * the suffixes in increasing lexicographic order, all distinct):
+ * T[SA[j],n) < T[SA[j+1],n), strictly, for each j in idx[0..count).
+ * Returns the number of sampled j that violate it; an entry SA[j] or
+ * SA[j+1] >= n counts as a violation, a j with no pair (j < 0 or
+ * j + 1 >= n) is skipped, and a j listed twice counts twice. */
 int64_t oracle_check_adjacent(const uint8_t *T, int64_t n, const uint32_t *sa,
                               const int64_t *idx, int64_t count);
 

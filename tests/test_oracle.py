@@ -146,6 +146,73 @@ def pin_checker(o):
     return bad
 
 
+def py_adjacent_violations(t: bytes, sa, idx):
+    """Violations of SA order at the sampled j, by Python's bytes order (no
+    oracle code): j with a pair (j, j+1) whose entries are not both < n or
+    whose suffixes are not strictly increasing."""
+    n = len(t)
+    bad = 0
+    for j in idx:
+        j = int(j)
+        if j < 0 or j + 1 >= n:
+            continue
+        a, b = int(sa[j]), int(sa[j + 1])
+        if a >= n or b >= n or not t[a:] < t[b:]:
+            bad += 1
+    return bad
+
+
+def pin_adjacent(o):
+    """The sampled adjacent-suffix check, on SAs that are right and on SAs
+    with one planted error, against counts fixed by construction or by
+    Python's bytes order."""
+    bad = []
+    for recipe, seed, n in (("dna", 41, 700), ("zipf_repeats", 42, 900), ("bytes", 43, 257)):
+        t = gen.text(recipe, seed, n).tobytes()
+        good = np.array(py_sa(t), dtype=np.uint32)
+        every = np.arange(-2, n + 2)
+        if o.check_adjacent(t, good, every) != 0:
+            bad.append(f"{recipe}: counts violations in a correct SA")
+        for j in (0, 1, n // 2, n - 2):  # an adjacent swap breaks exactly pair j
+            s = good.copy()
+            s[j], s[j + 1] = s[j + 1], s[j]
+            if o.check_adjacent(t, s, [j]) != 1:
+                bad.append(f"{recipe}: swap at {j} not counted once")
+            if o.check_adjacent(t, s, [j, j]) != 2:
+                bad.append(f"{recipe}: a repeated sample not counted twice")
+            # Pairs away from the swap stay in order: a sample that misses
+            # j - 1, j, j + 1 counts nothing.
+            others = [k for k in range(n - 1) if abs(k - j) > 1]
+            if o.check_adjacent(t, s, others) != 0:
+                bad.append(f"{recipe}: swap at {j} counted outside the sample")
+        s = good.copy()
+        s[n // 3] = n  # out of range: breaks the pairs on both sides
+        if o.check_adjacent(t, s, [n // 3 - 1, n // 3, n // 3 + 1]) != 2:
+            bad.append(f"{recipe}: out-of-range entry")
+        s = good.copy()
+        s[5] = s[4]  # a repeated entry: equal suffixes are not increasing
+        if o.check_adjacent(t, s, [4]) != 1:
+            bad.append(f"{recipe}: repeated entry accepted")
+        rng = np.random.default_rng(seed)
+        for _ in range(3):  # random wrong orders against Python's count
+            s = good.copy()
+            k = rng.integers(0, n, 40)
+            s[k] = s[rng.permutation(k)]
+            idx = rng.integers(-1, n + 1, 300)
+            if o.check_adjacent(t, s, idx) != py_adjacent_violations(t, s, idx):
+                bad.append(f"{recipe}: shuffled SA count")
+    for n in (2, 3, 17, 64):  # a^n in text order: every pair is decreasing
+        t = b"a" * n
+        inc = np.arange(n, dtype=np.uint32)
+        if o.check_adjacent(t, inc, np.arange(n - 1)) != n - 1:
+            bad.append(f"a^{n} in text order")
+        if o.check_adjacent(t, inc[::-1].copy(), np.arange(n - 1)) != 0:
+            bad.append(f"a^{n} in SA order")
+    if o.check_adjacent(b"ab", np.array([0, 1], dtype=np.uint32), [-1, 1, 2, 9]) != 0:
+        bad.append("indices without a pair are not skipped")
+    return bad
+
+
 def pin_bwt(o):
     bad = []
     t = b"banana"  # textbook: BWT(banana$) = annb$aa
@@ -295,7 +362,7 @@ def pin_dc7_names(o):
 
 
 PINS = [pin_examples, pin_closed_forms, pin_bruteforce, pin_random, pin_checker,
-        pin_bwt, pin_rank, pin_lcp, pin_multiplier, pin_dc7_names]
+        pin_adjacent, pin_bwt, pin_rank, pin_lcp, pin_multiplier, pin_dc7_names]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
