@@ -1,20 +1,37 @@
-"""Benchmark of gbsa on one GB300: input MB/s suffix-sorted and the HBM
-roofline fraction of the dominant kernel.
+"""Benchmark of gbsa on one GB300: input MB/s suffix-sorted, the HBM roofline
+fraction, batched against per-text builds, and serving p50/p99.
 
-Default workload (one step = one whole suffix-array build through the C-ABI):
-a single text of n = 2^28 bytes, a 1 MiB seeded Zipf(1.1) base over the
-bytes 1..255 repeated 256 times with 0.1% random substitutions per copy
-(long repeats force many doubling rounds); uint32 SA. Inputs are resident
-in HBM when the timed region starts; the text (256 MiB) and the working set
-(about 10 GiB) exceed the 129 MB L2, so no flush is needed between steps.
+Default run (one JSON line; one step = one whole suffix-array build through
+the C-ABI, inputs resident in HBM when the timed region starts):
+
+- headline: a single DNA-like text of n = 2^31 bytes over {A,C,G,T}, an
+  order-3 Markov chain with a seeded random transition table plus 5% of
+  positions covered by copied segments of 1-100 KiB; uint32 SA. The text
+  (2 GiB) and the working set (about 143 GB) exceed the 129 MB L2, so no
+  flush is needed between steps. `e2e` is the same metric through
+  sa_build_host (pinned host text in, host SA out, copies timed).
+- "cfg2": a single text of n = 2^28 bytes, a 1 MiB Zipf(1.1) base over the
+  bytes 1..255 repeated 256 times with 0.1% substitutions per copy, with
+  the paths beside the hot path on the same text (BWT, LCP, DC3, DC7,
+  prefix doubling using sorting, a-fold rounds).
+- "batched": 4096 uniform-DNA texts with log-uniform lengths in
+  [1 KiB, 4 MiB] in one sa_build_batched launch sequence, against 4096
+  per-text builds on the same stream.
+- "serving": Poisson arrivals at 100, 1000 and 2000 requests/s, sizes
+  log-uniform in [10 KiB, 64 MiB], half uniform DNA, half i.i.d. Zipf
+  bytes, admission by a 100 GB device budget: p50/p99 latency and MB/s.
+
+Every build runs with the library's own parameter choice (the autotuner's
+table shipped beside libgbsa.so); the line records the values used.
 
   python bench.py [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload plain|batched] [--n N]
+                  [--workload suite|plain|batched|serving|<extra>] [--n N]
 
 --impl reference times the CPU oracle (oracle/, prefix doubling with
-discarding, one host core) on a bounded sample of the same workload.
+discarding, one host core) on a bounded sample of the headline workload.
 Under torchrun with N > 1 processes each rank runs an independent replica
-(the single-text build does not shard); rank 0 prints the line.
+of the headline (the single-text build does not shard); rank 0 prints the
+line, the nested workloads run at N = 1 only.
 """
 from __future__ import annotations
 
@@ -34,11 +51,17 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-PLAIN_N = 1 << 28
-PLAIN_SEED = 2001
+HEAD = {"recipe": "markov", "seed": 3001, "n": 1 << 31,
+        "workload": "single text n=2^31 bytes DNA-like {A,C,G,T}: order-3 Markov chain with a "
+                    "seeded random transition table plus 5% of positions covered by copied "
+                    "segments of 1-100 KiB; uint32 SA"}
+CFG2 = {"recipe": "zipf_repeats", "seed": 2001, "n": 1 << 28,
+        "workload": "single text n=2^28 bytes: 1 MiB Zipf(1.1) base over bytes 1..255 x256 "
+                    "copies, 0.1% substitutions per copy; uint32 SA"}
 CPU_SAMPLE_N = 1 << 23
 REF_STEP_N = 1 << 20
 FALLBACK_HBM_GBS = 6800.0
+SERVE_DEFAULT_RATES = (100, 1000, 2000)
 
 
 def peaks():
@@ -141,13 +164,13 @@ def kernel_source_hash(kernel: str):
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
-    """Measured DRAM bytes per algorithmic byte of `kernel`, from its committed
-    ncu summary, if the kernel's sources are unchanged since it was captured
-    (else None)."""
+def ncu_traffic(kernel: str, workload: str):
+    """Measured DRAM bytes per algorithmic byte of `kernel` on `workload`
+    ("markov" or "zipf"), from its committed ncu summary, if the kernel's
+    sources are unchanged since it was captured (else None)."""
     if kernel not in KERNEL_SOURCES:
         return None
-    path = os.path.join(ROOT, "profiles", f"ncu_{kernel}.md")
+    path = os.path.join(ROOT, "profiles", f"ncu_{kernel}_{workload}.md")
     if not os.path.exists(path):
         return None
     with open(path) as f:
@@ -178,19 +201,37 @@ def cpu_model() -> str:
     return platform.machine()
 
 
+def host_text(recipe: str, seed: int, n: int) -> np.ndarray:
+    """The seeded recipe text, cached under the temporary directory by
+    (recipe, seed, n) so that later runs on the same machine skip the
+    generation (the 2^31-byte Markov text takes ~17 s to draw)."""
+    import gen
+    path = os.path.join(tempfile.gettempdir(), f"gbsa_text_{recipe}_{seed}_{n}.u8")
+    if os.path.exists(path) and os.path.getsize(path) == n:
+        return np.fromfile(path, dtype=np.uint8)
+    t = gen.text(recipe, seed, n)
+    try:
+        tmp = path + f".{os.getpid()}"
+        t.tofile(tmp)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+    return t
+
+
 def cpu_baseline():
-    """The oracle as it stands, one host core, on a bounded sample: the same
-    recipe at n = 2^23."""
+    """The oracle as it stands, one host core, on a bounded sample: the
+    headline recipe at n = 2^23."""
     import gen
     import oracle
-    t = gen.text("zipf_repeats", PLAIN_SEED, CPU_SAMPLE_N)
+    t = gen.text(HEAD["recipe"], HEAD["seed"], CPU_SAMPLE_N)
     o = oracle.get()
     t0 = time.perf_counter()
     o.pd_sa(t)
     dt = time.perf_counter() - t0
     return {"value": CPU_SAMPLE_N / dt / 1e6, "unit": "MB/s", "cores": 1, "kind": "oracle",
             "cpu_model": cpu_model(), "nproc": os.cpu_count(),
-            "sample": f"zipf_repeats recipe at n=2^23 (base 32 KiB x 256 copies), one "
+            "sample": f"the headline recipe (order-3 Markov DNA with 5% copies) at n=2^23, one "
                       f"prefix-doubling-with-discarding build, {dt:.1f} s on "
                       f"{os.cpu_count()} visible host cores (1 used)"}
 
@@ -202,7 +243,7 @@ def run_reference(args):
     import gen
     import oracle
     o = oracle.get()
-    t = gen.text("zipf_repeats", PLAIN_SEED, REF_STEP_N)
+    t = gen.text(HEAD["recipe"], HEAD["seed"], REF_STEP_N)
     for _ in range(args.warmup):
         o.pd_sa(t)
     t0 = time.perf_counter()
@@ -210,14 +251,13 @@ def run_reference(args):
         o.pd_sa(t)
     dt = (time.perf_counter() - t0) / args.steps
     value = REF_STEP_N / dt / 1e6
-    sample = (f"each step: the CPU oracle (prefix doubling with discarding, 1 core) on the "
-              f"zipf_repeats recipe at n=2^20 (4 KiB base x 256 copies)")
+    sample = ("each step: the CPU oracle (prefix doubling with discarding, 1 core) on the "
+              "headline recipe (order-3 Markov DNA with 5% copies) at n=2^20")
     line = {"metric": "input MB/s suffix-sorted", "value": value, "unit": "MB/s",
             "impl": "reference", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": "single text n=2^28 Zipf(1.1) bytes, 1 MiB base x256, "
-                                   "0.1% substitutions (sampled at n=2^20 for the CPU oracle)",
+            "config": {"workload": HEAD["workload"] + " (sampled at n=2^20 for the CPU oracle)",
                        "n": REF_STEP_N},
             "cpu_baseline": {"value": value, "unit": "MB/s", "cores": 1, "kind": "oracle",
                              "cpu_model": cpu_model(), "nproc": os.cpu_count(),
@@ -227,10 +267,204 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_plain(args):
+def _kernel_table(kern, steps):
+    return {k: {"ms_per_step": v["ms"] / steps, "launches_per_step": v["launches"] / steps,
+                "bytes_per_step": v["bytes"] / steps,
+                "gbs": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
+            for k, v in kern.items() if v["launches"]}
+
+
+def _roofline(kern, workload):
+    """The dominant kernel (most event time) against the measured copy
+    bandwidth: algorithmic bytes per launch / event time per launch."""
+    hbm, peak_kind = peaks()
+    dname, d = max(kern.items(), key=lambda kv: kv[1]["ms"])
+    achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
+    ratio = ncu_traffic(dname, workload)
+    avg_bytes = d["bytes"] / max(d["launches"], 1)
+    return {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm,
+            "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": ratio * avg_bytes if ratio is not None else None,
+            "peak_kind": peak_kind, "bytes_per_launch": avg_bytes,
+            "ms_per_launch": d["ms"] / max(d["launches"], 1)}
+
+
+def measure_single(cfg, steps, warmup, local, pg=None, clocks=False):
+    """K timed builds of one seeded text resident in HBM, with the library's
+    per-launch CUDA events (sa_options.profile) on the same stream; returns
+    the timings, the per-kernel table and the device text/workspace."""
     import torch
 
-    import gen
+    import paper_1610_03007_gb300 as gbsa
+    n = cfg["n"]
+    t_host = host_text(cfg["recipe"], cfg["seed"], n)
+    dev = torch.device("cuda", local)
+    text = torch.from_numpy(t_host).to(dev)
+    ws = torch.empty(gbsa.workspace_bytes(n), dtype=torch.uint8, device=dev)
+    sa = torch.empty(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    lib = gbsa.load()
+
+    def step(profile):
+        st = gbsa.Stats()
+        opt = gbsa.Options(profile=1 if profile else 0)
+        rc = lib.sa_build_ex(text.data_ptr(), n, sa.data_ptr(), None, ws.data_ptr(), ws.numel(),
+                             gbsa.ctypes.byref(opt), gbsa.ctypes.byref(st), stream.cuda_stream)
+        if rc != 0:
+            raise RuntimeError(f"sa_build_ex failed: {gbsa.status_string(rc)}")
+        return st.to_dict()
+
+    for _ in range(max(warmup, 0)):
+        step(False)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local) if clocks else None
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kern, launches, bytes_model = {}, 0, 0
+    ev0.record(stream)
+    for _ in range(steps):
+        st = step(True)
+        launches += st["launches"]
+        bytes_model += st["bytes_model"]
+        for k, v in st["kernels"].items():
+            a = kern.setdefault(k, {"ms": 0.0, "launches": 0, "bytes": 0})
+            a["ms"] += v["ms"]
+            a["launches"] += v["launches"]
+            a["bytes"] += v["bytes"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / steps, pg is not None)
+    return {"ms": ms, "kern": kern, "launches": launches, "bytes_model": bytes_model,
+            "stats": st, "clocks": sampler.stop() if sampler else None,
+            "t_host": t_host, "text": text, "ws": ws, "sa": sa}
+
+
+def measure_e2e(t_host, steps):
+    """sa_build_host from pinned host text to pinned host SA, copies inside
+    the timed region (wall clock around the calls; each call returns after
+    its result is in host memory)."""
+    import torch
+
+    import paper_1610_03007_gb300 as gbsa
+    n = t_host.size
+    h_text = torch.from_numpy(t_host).pin_memory()
+    h_sa = torch.empty(n, dtype=torch.int32).pin_memory()
+    gbsa.sa_build_host_ptr(h_text.data_ptr(), n, h_sa.data_ptr())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        gbsa.sa_build_host_ptr(h_text.data_ptr(), n, h_sa.data_ptr())
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) / steps * 1e3
+    del h_text, h_sa
+    gbsa.pool_trim(0)
+    return {"value": n / (e2e_ms * 1e-3) / 1e6, "unit": "MB/s", "h2d_bytes_per_step": n,
+            "d2h_bytes_per_step": 4 * n, "ms_per_step": e2e_ms, "steps": steps}
+
+
+def cfg2_extras(m, steps):
+    """The paths beside the hot path on the configuration-2 text, each timed
+    alone with CUDA events on the launching stream (outside the timed build
+    steps): BWT and LCP of the built SA, DC3, DC7, prefix doubling using
+    sorting, and the build with a-fold rounds."""
+    import torch
+
+    import paper_1610_03007_gb300 as gbsa
+    lib = gbsa.load()
+    text, ws, sa_dev = m["text"], m["ws"], m["sa"]
+    n = text.numel()
+    dev = text.device
+    stream = torch.cuda.current_stream()
+    st = stream.cuda_stream
+    hbm, _ = peaks()
+
+    def timed(call, reps, warm=1):
+        for _ in range(warm):
+            call()
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        for _ in range(reps):
+            call()
+        b1.record(stream)
+        torch.cuda.synchronize()
+        return b0.elapsed_time(b1) / reps
+
+    def ok(rc, what):
+        if rc != 0:
+            raise RuntimeError(f"{what} failed: {rc}")
+
+    bwt_buf = torch.empty(n + 1, dtype=torch.uint8, device=dev)
+    prim = torch.zeros(1, dtype=torch.int64, device=dev)
+    bwt_ms = timed(lambda: ok(lib.sa_bwt(text.data_ptr(), n, sa_dev.data_ptr(),
+                                         bwt_buf.data_ptr(), prim.data_ptr(), st), "sa_bwt"), 5, 3)
+    del bwt_buf
+    lcp_buf = torch.empty(n, dtype=torch.int32, device=dev)
+    lcp_ws = torch.empty(int(lib.sa_lcp_workspace_bytes(n)), dtype=torch.uint8, device=dev)
+    lcp_ms = timed(lambda: ok(lib.sa_lcp(text.data_ptr(), n, sa_dev.data_ptr(), lcp_buf.data_ptr(),
+                                         lcp_ws.data_ptr(), lcp_ws.numel(), st), "sa_lcp"), 3)
+    del lcp_buf, lcp_ws
+    out = torch.empty(n, dtype=torch.int32, device=dev)
+    dc3_ms = timed(lambda: ok(lib.sa_build_dc3(text.data_ptr(), n, out.data_ptr(), None, st),
+                              "sa_build_dc3"), 2)
+    dc7_ms = timed(lambda: ok(lib.sa_build_dc7(text.data_ptr(), n, out.data_ptr(), None, st),
+                              "sa_build_dc7"), 2)
+    pds_ms = timed(lambda: ok(lib.sa_build_pd_sort(text.data_ptr(), n, out.data_ptr(), None, 0,
+                                                   None, st), "sa_build_pd_sort"), 1)
+    del out
+    mult = {"2": {"ms": m["ms"], "rounds": m["stats"]["rounds"]}}
+    for a in (3, 4):
+        rounds = []
+        ms = timed(lambda: rounds.append(gbsa.sa_build_ex(text, workspace=ws,
+                                                          multiplier=a)[2]["rounds"]), 2)
+        mult[str(a)] = {"ms": ms, "rounds": rounds[-1]}
+    for v in mult.values():
+        v["value"] = n / (v["ms"] * 1e-3) / 1e6
+    torch.cuda.empty_cache()
+    gbsa.pool_trim(0)
+    mb = lambda ms: n / (ms * 1e-3) / 1e6  # noqa: E731
+    return {
+        "bwt": {"ms": bwt_ms, "bytes_per_row": 6, "gbs": 6.0 * (n + 1) / (bwt_ms * 1e-3) / 1e9,
+                "frac": 6.0 * (n + 1) / (bwt_ms * 1e-3) / 1e9 / hbm},
+        "lcp": {"ms": lcp_ms, "bytes_per_position": 30, "gbs": 30.0 * n / (lcp_ms * 1e-3) / 1e9,
+                "frac": 30.0 * n / (lcp_ms * 1e-3) / 1e9 / hbm},
+        "dc3": {"ms": dc3_ms, "value": mb(dc3_ms), "unit": "MB/s"},
+        "dc7": {"ms": dc7_ms, "value": mb(dc7_ms), "unit": "MB/s"},
+        "pd_sort": {"ms": pds_ms, "value": mb(pds_ms), "unit": "MB/s",
+                    "note": "prefix doubling using sorting, no discarding"},
+        "multiplier": {"by_a": mult, "unit": "MB/s",
+                       "note": "a-fold rounds (Prefix Quadrupling)"},
+    }
+
+
+def single_report(m, cfg, steps, world):
+    hbm, _ = peaks()
+    ms = m["ms"]
+    n = cfg["n"]
+    path_gbs = m["bytes_model"] / steps / (ms * 1e-3) / 1e9
+    st = m["stats"]
+    return {
+        "value": replicas_value(n, world, ms), "unit": "MB/s", "ms_per_step": ms, "steps": steps,
+        "config": {"workload": cfg["workload"], "n": n, "seed": cfg["seed"],
+                   "rounds": st["rounds"], "params": st["params"],
+                   "active_per_round": st["active"]},
+        "roofline": _roofline(m["kern"], "markov" if cfg["recipe"] == "markov" else "zipf"),
+        "path_roofline": {"bytes_per_step": m["bytes_model"] / steps, "achieved_gbs": path_gbs,
+                          "frac_measured": path_gbs / hbm, "frac_8tbs": path_gbs / 8000.0},
+        "kernels": _kernel_table(m["kern"], steps),
+        "gpu_launches": m["launches"],
+    }
+
+
+def run_suite(args):
+    """The default run: the headline (configuration 3) line with the other
+    workloads nested in it."""
+    import torch
+
     import paper_1610_03007_gb300 as gbsa
     from paper_1610_03007_gb300 import _build
 
@@ -243,244 +477,81 @@ def run_plain(args):
         import torch.distributed as dist
         dist.init_process_group("gloo")
         pg = dist
-    n = args.n or PLAIN_N
-    t_host = gen.text("zipf_repeats", PLAIN_SEED, n)
-    dev = torch.device("cuda", local)
-    text = torch.from_numpy(t_host).to(dev)
-    ws = torch.empty(gbsa.workspace_bytes(n), dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream()
-    # Tile parameters picked by the project's autotuner on this input
-    # (outside the timed region).
-    from paper_1610_03007_gb300 import autotune
-    tuned = autotune.tune(text, ws, reps=2) if not args.no_tune else {
-        "params": dict(autotune.DEFAULTS), "ms": None, "tried": {}}
-    params = tuned["params"]
-
-    def step(profile=False):
-        return gbsa.sa_build_ex(text, workspace=ws, profile=profile, **params)
-
-    for _ in range(max(args.warmup, 0)):
-        step()
-    torch.cuda.synchronize()
-    sampler = ClockSampler(local)
-    if pg:
-        pg.barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    time.sleep(0.3)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    kern = {}
-    launches = 0
-    bytes_model = 0
-    ev0.record(stream)
-    for _ in range(args.steps):
-        _, _, st, _ = step(profile=True)
-        launches += st["launches"]
-        bytes_model += st["bytes_model"]
-        for k, v in st["kernels"].items():
-            a = kern.setdefault(k, {"ms": 0.0, "launches": 0, "bytes": 0})
-            a["ms"] += v["ms"]
-            a["launches"] += v["launches"]
-            a["bytes"] += v["bytes"]
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, pg is not None)
-    clocks = sampler.stop()
-    stats = st
-
-    # End to end through the host entry point: pinned host text in, host SA
-    # out, copies inside the timed region (right after the timed steps, before
-    # the other paths below fill the library's memory pool).
-    h_text = torch.from_numpy(t_host).pin_memory()
-    h_sa = torch.empty(n, dtype=torch.int32).pin_memory()
-    gbsa.sa_build_host_ptr(h_text.data_ptr(), n, h_sa.data_ptr())
-    torch.cuda.synchronize()
-    e_steps = max(1, min(args.steps, 5))
-    t0 = time.perf_counter()
-    for _ in range(e_steps):
-        gbsa.sa_build_host_ptr(h_text.data_ptr(), n, h_sa.data_ptr())
-    torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t0) / e_steps * 1e3
-    del h_text, h_sa
-
-    bwt_ms = lcp_ms = dc3_ms = dc7_ms = pds_ms = None
-    mult = None
-    if not args.build_only:
-        # BWT of the built SA through sa_bwt, timed alone on the same stream
-        # (text, SA and BWT together exceed L2).
-        sa_dev = step(profile=False)[0]
-        lib = gbsa.load()
-        bwt_buf = torch.empty(n + 1, dtype=torch.uint8, device=dev)
-        prim = torch.zeros(1, dtype=torch.int64, device=dev)
-
-        def bwt_call():
-            rc = lib.sa_bwt(text.data_ptr(), n, sa_dev.data_ptr(), bwt_buf.data_ptr(),
-                            prim.data_ptr(), stream.cuda_stream)
-            if rc != 0:
-                raise RuntimeError(f"sa_bwt failed: {rc}")
-
-        for _ in range(3):
-            bwt_call()
-        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        b0.record(stream)
-        for _ in range(5):
-            bwt_call()
-        b1.record(stream)
-        torch.cuda.synchronize()
-        bwt_ms = b0.elapsed_time(b1) / 5
-        del bwt_buf
-
-        # LCP array of the built SA through sa_lcp (caller workspace), timed the
-        # same way.
-        lcp_buf = torch.empty(n, dtype=torch.int32, device=dev)
-        lcp_ws = torch.empty(int(lib.sa_lcp_workspace_bytes(n)), dtype=torch.uint8, device=dev)
-
-        def lcp_call():
-            rc = lib.sa_lcp(text.data_ptr(), n, sa_dev.data_ptr(), lcp_buf.data_ptr(),
-                            lcp_ws.data_ptr(), lcp_ws.numel(), stream.cuda_stream)
-            if rc != 0:
-                raise RuntimeError(f"sa_lcp failed: {rc}")
-
-        lcp_call()
-        b0.record(stream)
-        for _ in range(3):
-            lcp_call()
-        b1.record(stream)
-        torch.cuda.synchronize()
-        lcp_ms = b0.elapsed_time(b1) / 3
-        del sa_dev, lcp_buf, lcp_ws
-
-        # The same suffix array by DC3 (sa_build_dc3), for comparison.
-        dc3_sa = torch.empty(n, dtype=torch.int32, device=dev)
-
-        def dc3_call():
-            rc = lib.sa_build_dc3(text.data_ptr(), n, dc3_sa.data_ptr(), None, stream.cuda_stream)
-            if rc != 0:
-                raise RuntimeError(f"sa_build_dc3 failed: {rc}")
-
-        dc3_call()
-        b0.record(stream)
-        for _ in range(2):
-            dc3_call()
-        b1.record(stream)
-        torch.cuda.synchronize()
-        dc3_ms = b0.elapsed_time(b1) / 2
-
-        # ... and by DC7 (sa_build_dc7).
-        def dc7_call():
-            rc = lib.sa_build_dc7(text.data_ptr(), n, dc3_sa.data_ptr(), None, stream.cuda_stream)
-            if rc != 0:
-                raise RuntimeError(f"sa_build_dc7 failed: {rc}")
-
-        dc7_call()
-        b0.record(stream)
-        for _ in range(2):
-            dc7_call()
-        b1.record(stream)
-        torch.cuda.synchronize()
-        dc7_ms = b0.elapsed_time(b1) / 2
-
-        # ... and by prefix doubling using sorting (no discarding).
-        def pds_call():
-            rc = lib.sa_build_pd_sort(text.data_ptr(), n, dc3_sa.data_ptr(), None, 0, None,
-                                      stream.cuda_stream)
-            if rc != 0:
-                raise RuntimeError(f"sa_build_pd_sort failed: {rc}")
-
-        pds_call()
-        b0.record(stream)
-        pds_call()
-        b1.record(stream)
-        torch.cuda.synchronize()
-        pds_ms = b0.elapsed_time(b1)
-        del dc3_sa
-
-        # The same build with a-fold rounds (prefix tripling and quadrupling):
-        # fewer rounds, each ranking a - 1 partner names.
-        mult = {"2": {"ms": ms, "rounds": stats["rounds"]}}
-        for a in (3, 4):
-            gbsa.sa_build_ex(text, workspace=ws, multiplier=a, **params)
-            b0.record(stream)
-            for _ in range(2):
-                mst = gbsa.sa_build_ex(text, workspace=ws, multiplier=a, **params)[2]
-            b1.record(stream)
-            torch.cuda.synchronize()
-            mult[str(a)] = {"ms": b0.elapsed_time(b1) / 2, "rounds": mst["rounds"]}
-        for v in mult.values():
-            v["value"] = n / (v["ms"] * 1e-3) / 1e6
-
-    del ws
+    head = dict(HEAD)
+    if args.n:
+        head["n"] = args.n
+        head["workload"] += f" (n overridden to {args.n})"
+    m = measure_single(head, args.steps, args.warmup, local, pg, clocks=True)
+    rep = single_report(m, head, args.steps, world)
+    t_host = m["t_host"]
+    for k in ("text", "ws", "sa"):
+        del m[k]
     torch.cuda.empty_cache()
-
-    if rank != 0:
-        if pg:
-            pg.barrier()
-        return
-    hbm, peak_kind = peaks()
-    dom = max(kern.items(), key=lambda kv: kv[1]["ms"])
-    dname, d = dom
-    achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
-    ratio = ncu_traffic(dname)
-    avg_bytes = d["bytes"] / max(d["launches"], 1)
-    traffic = ratio * avg_bytes if ratio is not None else None
-    value = replicas_value(n, world, ms)
-    path_gbs = bytes_model / args.steps / (ms * 1e-3) / 1e9
+    e2e = measure_e2e(t_host, max(1, min(args.steps, 3)))
+    del t_host
+    hbm, _ = peaks()
     line = {
-        "metric": "input MB/s suffix-sorted", "value": value, "unit": "MB/s",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-        "data": "synthetic",
-        "config": {"workload": "single text n=2^28 bytes: 1 MiB Zipf(1.1) base over bytes 1..255 "
-                               "x256 copies, 0.1% substitutions per copy; uint32 SA",
-                   "n": n, "seed": PLAIN_SEED, "rounds": stats["rounds"],
-                   "tuned": {"params": params,
-                             "candidates_ms": {k: round(v, 3) for k, v in tuned["tried"].items()}},
-                   "l2": "inputs larger than L2 (256 MiB text, ~10 GiB working set); no flush",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm,
-                     "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
-                     "peak_kind": peak_kind,
-                     "bytes_per_launch": avg_bytes,
-                     "ms_per_launch": d["ms"] / max(d["launches"], 1)},
-        "path_roofline": {"bytes_per_step": bytes_model / args.steps, "achieved_gbs": path_gbs,
-                          "frac_measured": path_gbs / hbm, "frac_8tbs": path_gbs / 8000.0},
-        "kernels": {k: {"ms_per_step": v["ms"] / args.steps,
-                        "launches_per_step": v["launches"] / args.steps,
-                        "bytes_per_step": v["bytes"] / args.steps,
-                        "gbs": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
-                    for k, v in kern.items() if v["launches"]},
-        "e2e": {"value": n / (e2e_ms * 1e-3) / 1e6, "unit": "MB/s", "h2d_bytes_per_step": n,
-                "d2h_bytes_per_step": 4 * n, "ms_per_step": e2e_ms},
-        "gpu_launches": launches,
-        "clocks": clocks,
+        "metric": "input MB/s suffix-sorted", "value": rep["value"], "unit": "MB/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": rep["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": dict(rep["config"], l2="inputs larger than L2 (2 GiB text, ~143 GB working "
+                                         "set); no flush",
+                       parallelism="replicas" if world > 1 else "single GPU"),
+        "roofline": rep["roofline"], "path_roofline": rep["path_roofline"],
+        "kernels": rep["kernels"], "e2e": e2e, "gpu_launches": rep["gpu_launches"],
+        "clocks": m["clocks"],
     }
-    if not args.build_only:
-        line.update({
-            "bwt": {"ms": bwt_ms, "bytes_per_row": 6,
-                    "gbs": 6.0 * (n + 1) / (bwt_ms * 1e-3) / 1e9,
-                    "frac": 6.0 * (n + 1) / (bwt_ms * 1e-3) / 1e9 / hbm,
-                    "note": "sa_bwt on the built SA, outside the timed step"},
-            "lcp": {"ms": lcp_ms, "bytes_per_position": 30,
-                    "gbs": 30.0 * n / (lcp_ms * 1e-3) / 1e9,
-                    "frac": 30.0 * n / (lcp_ms * 1e-3) / 1e9 / hbm,
-                    "note": "sa_lcp on the built SA, outside the timed step"},
-            "dc3": {"ms": dc3_ms, "value": n / (dc3_ms * 1e-3) / 1e6, "unit": "MB/s",
-                    "note": "the same text by sa_build_dc3 (skew algorithm), outside the "
-                            "timed step"},
-            "dc7": {"ms": dc7_ms, "value": n / (dc7_ms * 1e-3) / 1e6, "unit": "MB/s",
-                    "note": "the same text by sa_build_dc7 (difference cover mod 7), outside "
-                            "the timed step"},
-            "pd_sort": {"ms": pds_ms, "value": n / (pds_ms * 1e-3) / 1e6, "unit": "MB/s",
-                        "note": "the same text by sa_build_pd_sort (prefix doubling using "
-                                "sorting, no discarding), outside the timed step"},
-            "multiplier": {"by_a": mult, "unit": "MB/s",
-                           "note": "the same text with sa_options.multiplier a (a-fold rounds, "
-                                   "Prefix Quadrupling); a = 3, 4 outside the timed step"},
-        })
-    line["cpu_baseline"] = cpu_baseline() if (world == 1 and not args.no_cpu) else None
-    print(json.dumps(line), flush=True)
+    if world == 1 and not args.headline_only:
+        c2 = dict(CFG2)
+        m2 = measure_single(c2, max(1, min(args.steps, 5)), 2, local)
+        r2 = single_report(m2, c2, max(1, min(args.steps, 5)), 1)
+        if not args.build_only:
+            r2.update(cfg2_extras(m2, args.steps))
+        for k in ("text", "ws", "sa"):
+            del m2[k]
+        torch.cuda.empty_cache()
+        gbsa.pool_trim(0)
+        line["cfg2"] = r2
+        line["batched"] = run_batched(args, emit=False)
+        torch.cuda.empty_cache()
+        gbsa.pool_trim(0)
+        line["serving"] = run_serving(args, emit=False)
+        gbsa.pool_trim(0)
+        line["gpu_launches"] += r2["gpu_launches"] + line["batched"]["gpu_launches"]
+    if rank == 0:
+        line["cpu_baseline"] = cpu_baseline() if (world == 1 and not args.no_cpu) else None
+        print(json.dumps(line), flush=True)
     if pg:
         pg.barrier()
+
+
+def run_plain(args):
+    """One single-text workload alone (--recipe, --n; default: the
+    configuration-2 text), its own line."""
+    import torch
+
+    import paper_1610_03007_gb300 as gbsa
+    from paper_1610_03007_gb300 import _build
+
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    _build.build()
+    gbsa.load()
+    cfg = dict(CFG2 if args.recipe == "zipf_repeats" else HEAD)
+    if args.recipe not in ("zipf_repeats", "markov"):
+        cfg = {"recipe": args.recipe, "seed": 1001, "n": 1 << 20,
+               "workload": f"{args.recipe} recipe"}
+    if args.n:
+        cfg["n"] = args.n
+        cfg["workload"] += f" (n = {args.n})"
+    m = measure_single(cfg, args.steps, args.warmup, local, clocks=True)
+    rep = single_report(m, cfg, args.steps, 1)
+    if not args.build_only and cfg["recipe"] == "zipf_repeats":
+        rep.update(cfg2_extras(m, args.steps))
+    rep.update({"metric": "input MB/s suffix-sorted", "clocks": m["clocks"],
+                "warmup": args.warmup, "higher_is_better": True, "data": "synthetic"})
+    print(json.dumps(rep), flush=True)
 
 
 BATCH_SEED = 4001
@@ -513,16 +584,10 @@ def run_batched(args, emit=True):
                      dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    # Radix tile and key width picked by measurement (the batched build is
-    # sort-bound).
-    from paper_1610_03007_gb300 import autotune
-    tuned = autotune.tune_batched(texts, off, sa, ws)
-    best = tuned["params"]
-
     def step(profile=False):
         return gbsa.sa_build_batched(texts, off, sa_out=sa, workspace=ws, stats=True,
-                                     profile=profile, **best)
-    for _ in range(max(args.warmup, 1)):
+                                     profile=profile)
+    for _ in range(max(min(args.warmup, 3), 1)):
         step()
     torch.cuda.synchronize()
     steps = max(1, min(args.steps, 5))
@@ -543,7 +608,8 @@ def run_batched(args, emit=True):
     del ws
     torch.cuda.empty_cache()
     # Per-text plain launches: the same texts through sa_build_ex, one call
-    # each, with one workspace sized for the longest text.
+    # each, with one workspace sized for the longest text (the library's
+    # parameters for each text's own size class).
     lens = np.diff(off).astype(np.int64)
     wsp = torch.empty(gbsa.workspace_bytes(int(lens.max())), dtype=torch.uint8, device=dev)
     views = [(int(off[k]), int(lens[k])) for k in range(count)]
@@ -559,27 +625,17 @@ def run_batched(args, emit=True):
     p1.record(stream)
     torch.cuda.synchronize()
     plain_ms = p0.elapsed_time(p1)
-    hbm, peak_kind = peaks()
-    dom = max(kern.items(), key=lambda kv: kv[1]["ms"])
-    d = dom[1]
-    achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
+    del wsp, texts, sa
     out = {"metric": "input MB/s suffix-sorted (batched)", "value": N / (ms * 1e-3) / 1e6,
            "unit": "MB/s", "ms_per_step": ms, "steps": steps,
            "config": {"workload": f"{count} uniform-DNA texts, lengths log-uniform in "
                                   f"[1 KiB, 4 MiB], one SA per text", "total_bytes": N,
-                      "seed": BATCH_SEED, "rounds": st["rounds"],
-                      "tuned": {"params": best,
-                                "candidates_ms": {k: round(v, 2)
-                                                  for k, v in tuned["tried"].items()}}},
+                      "seed": BATCH_SEED, "rounds": st["rounds"], "params": st["params"]},
            "per_text_plain": {"value": N / (plain_ms * 1e-3) / 1e6, "unit": "MB/s",
                               "ms": plain_ms, "calls": count},
            "speedup_vs_per_text": plain_ms / ms,
-           "roofline": {"bound": "hbm", "kernel": dom[0], "achieved": achieved, "peak": hbm,
-                        "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
-                        "traffic": None},
-           "kernels": {k: {"ms_per_step": v["ms"] / steps,
-                           "gbs": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
-                       for k, v in kern.items() if v["launches"]},
+           "roofline": _roofline(kern, "batched"),
+           "kernels": _kernel_table(kern, steps),
            "gpu_launches": launches}
     if emit:
         print(json.dumps(out), flush=True)
@@ -591,7 +647,7 @@ SERVE_RATES = (10, 30, 100, 300, 1000, 2000)
 SERVE_LO, SERVE_HI = 10 << 10, 64 << 20
 
 
-def run_serving(args):
+def run_serving(args, emit=True):
     """Workload 5: Poisson arrivals of SA builds at each offered rate, sizes
     log-uniform in [10 KiB, 64 MiB], a fair coin choosing uniform DNA or
     i.i.d. Zipf(1.1) bytes; continuous batching under a 100 GB device budget
@@ -612,7 +668,8 @@ def run_serving(args):
     pools = [torch.from_numpy(gen.text("dna", SERVE_SEED, SERVE_HI)).pin_memory(),
              torch.from_numpy(gen.text("zipf", SERVE_SEED + 1, SERVE_HI)).pin_memory()]
     views = [p.numpy() for p in pools]
-    rates = [float(r) for r in (args.rates.split(",") if args.rates else SERVE_RATES)]
+    default_rates = SERVE_RATES if emit else SERVE_DEFAULT_RATES
+    rates = [float(r) for r in (args.rates.split(",") if args.rates else default_rates)]
     # Pinned result buffers, as a serving client would hand the server (a
     # pageable destination turns each result copy into a staged one): one
     # arena large enough for the largest rate's requests, carved per request.
@@ -651,6 +708,7 @@ def run_serving(args):
                               "input_MB": total / 1e6,
                               "peak_in_flight": st["peak_in_flight"],
                               "peak_GB_in_use": st["peak_bytes_in_use"] / 1e9})
+    del arena, pools
     line = {"metric": "serving latency p50/p99 (ms) and input MB/s per offered rate",
             "unit": "ms", "higher_is_better": False, "data": "synthetic",
             "config": {"workload": "Poisson arrivals, sizes log-uniform [10 KiB, 64 MiB], "
@@ -658,7 +716,8 @@ def run_serving(args):
                        "host_buffers": "texts and results in pinned host memory",
                        "slots": args.slots, "requests_per_rate": count, "seed": SERVE_SEED},
             "rates": out_rates}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
     return line
 
 
@@ -679,9 +738,9 @@ def run_extra(args):
 
     _build.build()
     lib = gbsa.load()
-    n = args.n or PLAIN_N
+    n = args.n or CFG2["n"]
     dev = torch.device("cuda", 0)
-    text = torch.from_numpy(gen.text("zipf_repeats", PLAIN_SEED, n)).to(dev)
+    text = torch.from_numpy(gen.text("zipf_repeats", CFG2["seed"], n)).to(dev)
     stream = torch.cuda.current_stream()
     out = torch.empty(n + 1, dtype=torch.int32, device=dev)
     st = stream.cuda_stream
@@ -724,7 +783,7 @@ def run_extra(args):
             "higher_is_better": True, "data": "synthetic",
             "config": {"workload": f"{kind} on the repeated-Zipf recipe (Zipf(1.1) base over "
                                    f"bytes 1..255 x256 copies, 0.1% substitutions), n={n}",
-                       "seed": PLAIN_SEED}}
+                       "seed": CFG2["seed"]}}
     print(json.dumps(line), flush=True)
     return line
 
@@ -735,18 +794,21 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="plain",
-                    choices=["plain", "batched", "serving"] + list(EXTRA_CALLS))
+    ap.add_argument("--workload", default="suite",
+                    choices=["suite", "plain", "batched", "serving"] + list(EXTRA_CALLS))
+    ap.add_argument("--recipe", default="zipf_repeats",
+                    help="plain workload: zipf_repeats (configuration 2), markov (3), dna, ...")
     ap.add_argument("--requests", type=int, default=0, help="requests per rate (serving)")
     ap.add_argument("--rates", default="", help="comma-separated offered rates (serving)")
     ap.add_argument("--slots", type=int, default=16, help="server slots (serving)")
     ap.add_argument("--batch-count", type=int, default=0, help="texts in the batched workload")
     ap.add_argument("--n", type=int, default=0, help="override the text length (testing)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
-    ap.add_argument("--no-tune", action="store_true", help="use the default tile parameters")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="suite: the headline line without the nested workloads")
     ap.add_argument("--build-only", action="store_true",
-                    help="plain workload: skip the BWT, LCP, DC3, DC7, sorting-variant and multiplier calls "
-                         "(a launch list of the builds alone)")
+                    help="configuration 2: skip the BWT, LCP, DC3, DC7, sorting-variant and "
+                         "multiplier calls (a launch list of the builds alone)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -756,8 +818,10 @@ def main():
         run_serving(args)
     elif args.workload in EXTRA_CALLS:
         run_extra(args)
-    else:
+    elif args.workload == "plain":
         run_plain(args)
+    else:
+        run_suite(args)
 
 
 if __name__ == "__main__":

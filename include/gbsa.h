@@ -105,7 +105,23 @@ typedef struct {
    * the same for every a; trace_isa holds the names after each round, at
    * h0 * a^k resolved characters. */
   uint32_t multiplier;
+  /* Discard threshold: when at least this many ISA writes may be pending
+   * (names of suffixes discarded as unique, or renamed, in a round; Section
+   * 2.1, Algorithms 5 and 6), they are first bucketed by position so that
+   * the writes stay in L2; fewer are written directly. 0 = automatic (the
+   * tuning table, else 2^22); 0xFFFFFFFF = never bucket. Same SA and ISA
+   * for every value. */
+  uint32_t bucket_min;
 } sa_options;
+
+/* Tuned build parameters (the autotuner's table, see sa_tuning_set): each
+ * field as the sa_options field of the same name; 0 = built-in default. */
+typedef struct {
+  uint32_t sort_items;
+  uint32_t refine_shape;
+  uint32_t h0_chars;
+  uint32_t bucket_min;
+} sa_tuned;
 
 /* Kernel classes of the per-kernel statistics. */
 enum {
@@ -148,6 +164,11 @@ typedef struct {
   double kernel_ms[SA_K_CLASSES];
   uint64_t kernel_launches[SA_K_CLASSES];
   uint64_t kernel_bytes[SA_K_CLASSES];
+  /* The parameters the build ran with (its options, else the tuning table's
+   * entry for its class, else the defaults): radix keys per thread, refine
+   * tile shape (1-4), discard threshold; chars_per_key above is the key
+   * width. tuned = 1 when at least one came from the tuning table. */
+  uint32_t sort_items, refine_shape, bucket_min, tuned;
 } sa_stats;
 
 /* Suffix array of one text (Section 2; Algorithm 5).
@@ -218,6 +239,53 @@ sa_status sa_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t m,
                         size_t ws_bytes, gbsa_stream_t stream);
 size_t sa_sort_workspace_bytes(uint64_t m);
 
+/* ---- The autotuner's table ---------------------------------------------
+ * Build parameters picked by measurement (radix tile, refine tile shape,
+ * initial key width, discard threshold) per workload class: single text or
+ * batch (batched 0 or 1), bits per character of the alphabet (1..8, as the
+ * build computes it from the byte histogram), floor(log2) of the total
+ * length (0..31). A build whose sa_options leave a knob at 0 takes it from
+ * the entry of its own (batched, bits) class with the nearest size, else
+ * the built-in default; sa_stats reports what it ran with. The table is
+ * read at the first lookup from the file named by GBSA_TUNING_TABLE, else
+ * tuning.txt beside libgbsa.so (written by autotune.py), one entry a line:
+ * "batched bits log2n sort_items refine_shape h0_chars bucket_min".
+ * The paper has no counterpart: this chooses how the library runs the sort
+ * and discard steps of Section 2.1, not what they compute. Thread-safe;
+ * allocates no device memory. */
+
+/* Sets (params non-NULL, HOST) or removes (NULL) one entry. Returns
+ * SA_ERR_INVALID_ARG for a key out of range. */
+sa_status sa_tuning_set(uint32_t batched, uint32_t bits_per_char, uint32_t log2_n,
+                        const sa_tuned *params);
+/* Replaces the whole table by the file at path (NULL: an empty table).
+ * SA_ERR_INVALID_ARG if the file cannot be read or a line is malformed
+ * (the table is left unchanged then). */
+sa_status sa_tuning_load(const char *path);
+/* The parameters a build of this class and total length n would take from
+ * the table (all 0 if none applies) into *out (HOST); returns the number of
+ * entries in the table. */
+uint32_t sa_tuning_lookup(uint32_t batched, uint32_t bits_per_char, uint64_t n, sa_tuned *out);
+
+/* Device memory held by the library's own stream-ordered pool on the
+ * current device, which sa_build, sa_build_batched, sa_build_host,
+ * sa_sort_pairs (without a caller workspace) and the DC3/DC7 and sorting
+ * variants draw from: *used = bytes handed out now, *reserved = bytes the
+ * pool holds from the device (it is never trimmed). Both 0 before the first
+ * allocation on this device. used, reserved: HOST. Returns
+ * SA_ERR_INVALID_ARG for a NULL pointer, SA_ERR_CUDA if the device cannot
+ * be queried. Allocates nothing; the paper has no counterpart (a runtime
+ * query). */
+sa_status sa_pool_usage(uint64_t *used, uint64_t *reserved);
+
+/* Returns the current device's pool memory that no build holds to the
+ * device, keeping at most keep_bytes reserved (cudaMemPoolTrimTo). Memory
+ * of builds still in flight is not touched; call it after they completed
+ * (synchronise their streams first) to hand the memory to other users.
+ * SA_ERR_CUDA if the device cannot be queried. The paper has no
+ * counterpart (a runtime call). */
+sa_status sa_pool_trim(uint64_t keep_bytes);
+
 /* sa_build without any device memory allocation, for callers that must not
  * allocate when they build: for example code running beside a serving
  * engine or framework allocator that already reserved the GPU's memory, a
@@ -227,13 +295,14 @@ size_t sa_sort_workspace_bytes(uint64_t m);
  * text, n, sa_out, stream: as for sa_build. n may be at most 2^18
  * (262144); larger n returns SA_ERR_TOO_LARGE.
  * The workspace is a 20 MiB array in the library's own device memory, held
- * on every GPU that loads the library until the process exits. The first
- * call on a device looks up that array's device address (a CUDA runtime
- * query, once per device); make that first call before any stream capture
- * begins on the device. All calls share the one array: calls whose GPU work
- * overlaps race and give garbage, so serialise them (one stream, or an
- * event between streams). Leftover contents from the previous call are
- * harmless: every build clears what it needs. */
+ * on every GPU that loads the library until the process exits. Each call
+ * looks up that array's device address in the current context (a CUDA
+ * runtime query that allocates nothing). Like sa_build, a call synchronises
+ * `stream` once per doubling round, so it cannot be made while that stream
+ * is being captured into a CUDA graph. All calls share the one array: calls
+ * whose GPU work overlaps race and give garbage, so serialise them (one
+ * stream, or an event between streams). Leftover contents from the
+ * previous call are harmless: every build clears what it needs. */
 sa_status sa_build_noalloc(const uint8_t *text, uint64_t n, uint32_t *sa_out,
                            gbsa_stream_t stream);
 
@@ -270,6 +339,7 @@ typedef struct {
   uint64_t submitted, completed;
   uint64_t bytes_in_use, peak_bytes_in_use;
   uint32_t in_flight, peak_in_flight, queued;
+  uint32_t tracked;           /* requests held: queued, running or uncollected */
 } sa_server_stats;
 
 /* Device bytes a request of n characters holds while it runs (text, SA and
@@ -287,10 +357,14 @@ sa_status sa_server_submit(sa_server *s, const uint8_t *host_text, uint64_t n,
                            uint32_t *host_sa, uint64_t *ticket);
 
 /* 1 if the request is done (info filled), 0 if pending, -1 if the ticket
- * is unknown. Non-blocking. */
+ * is unknown. Non-blocking. Reporting 1 hands the result over: the server
+ * forgets the request and its ticket becomes unknown. */
 int sa_server_poll(sa_server *s, uint64_t ticket, sa_request_info *info);
 
-/* Blocks until the request is done; returns its status (info may be NULL). */
+/* Blocks until the request is done; returns its status (info may be NULL).
+ * On return the server has forgotten the request (its ticket is unknown to
+ * later calls; several threads may wait on one ticket at once). An unknown
+ * ticket gives SA_ERR_INVALID_ARG. */
 sa_status sa_server_wait(sa_server *s, uint64_t ticket, sa_request_info *info);
 
 /* Current counters (HOST struct). */

@@ -32,7 +32,8 @@ EXPORTED = ("sa_build", "sa_workspace_bytes", "sa_build_ex", "sa_build_batched",
             "sa_build_noalloc", "sa_request_footprint", "sa_server_create", "sa_server_submit",
             "sa_server_poll", "sa_server_wait", "sa_server_get_stats", "sa_server_destroy",
             "sa_bwt", "sa_lcp", "sa_lcp_workspace_bytes", "sa_build_dc3", "sa_build_dc7",
-            "sa_build_pd_sort")
+            "sa_build_pd_sort", "sa_pool_usage", "sa_tuning_set", "sa_tuning_load",
+            "sa_tuning_lookup", "sa_pool_trim")
 
 
 class SAError(RuntimeError):
@@ -46,7 +47,17 @@ class Options(ctypes.Structure):
                 ("inject_stall", ctypes.c_uint32), ("trace_isa", ctypes.c_void_p),
                 ("trace_cap", ctypes.c_uint32), ("paper_names", ctypes.c_uint32),
                 ("refine_shape", ctypes.c_uint32), ("sort_items", ctypes.c_uint32),
-                ("profile", ctypes.c_uint32), ("multiplier", ctypes.c_uint32)]
+                ("profile", ctypes.c_uint32), ("multiplier", ctypes.c_uint32),
+                ("bucket_min", ctypes.c_uint32)]
+
+
+class Tuned(ctypes.Structure):
+    """One entry of the library's tuning table (sa_tuned)."""
+    _fields_ = [("sort_items", ctypes.c_uint32), ("refine_shape", ctypes.c_uint32),
+                ("h0_chars", ctypes.c_uint32), ("bucket_min", ctypes.c_uint32)]
+
+    def to_dict(self) -> dict:
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
 
 
 KERNEL_CLASSES = ("byte_hist", "pack", "digit_hist", "plan", "onesweep", "rename", "gather",
@@ -65,7 +76,9 @@ class Stats(ctypes.Structure):
                 ("launches", ctypes.c_uint32),
                 ("kernel_ms", ctypes.c_double * len(KERNEL_CLASSES)),
                 ("kernel_launches", ctypes.c_uint64 * len(KERNEL_CLASSES)),
-                ("kernel_bytes", ctypes.c_uint64 * len(KERNEL_CLASSES))]
+                ("kernel_bytes", ctypes.c_uint64 * len(KERNEL_CLASSES)),
+                ("sort_items", ctypes.c_uint32), ("refine_shape", ctypes.c_uint32),
+                ("bucket_min", ctypes.c_uint32), ("tuned", ctypes.c_uint32)]
 
     def to_dict(self) -> dict:
         r = self.rounds
@@ -75,6 +88,11 @@ class Stats(ctypes.Structure):
                 "passes": list(self.passes[:r]), "key_bits": list(self.key_bits[:r]),
                 "groups": list(self.groups[:r]), "bytes_model": int(self.bytes_model),
                 "launches": int(self.launches),
+                "params": {"sort_items": int(self.sort_items),
+                           "refine_shape": int(self.refine_shape),
+                           "h0_chars": int(self.chars_per_key),
+                           "bucket_min": int(self.bucket_min),
+                           "from_table": bool(self.tuned)},
                 "kernels": {name: {"ms": self.kernel_ms[k], "launches": int(self.kernel_launches[k]),
                                    "bytes": int(self.kernel_bytes[k])}
                             for k, name in enumerate(KERNEL_CLASSES)}}
@@ -101,7 +119,7 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
                 ("bytes_in_use", ctypes.c_uint64), ("peak_bytes_in_use", ctypes.c_uint64),
                 ("in_flight", ctypes.c_uint32), ("peak_in_flight", ctypes.c_uint32),
-                ("queued", ctypes.c_uint32)]
+                ("queued", ctypes.c_uint32), ("tracked", ctypes.c_uint32)]
 
 
 _lib = None
@@ -157,6 +175,16 @@ def load(path: str | None = None):
     lib.sa_server_get_stats.restype = None
     lib.sa_server_destroy.argtypes = [vp]
     lib.sa_server_destroy.restype = None
+    lib.sa_tuning_set.argtypes = [u32, u32, u32, ctypes.POINTER(Tuned)]
+    lib.sa_tuning_set.restype = ctypes.c_int
+    lib.sa_tuning_load.argtypes = [ctypes.c_char_p]
+    lib.sa_tuning_load.restype = ctypes.c_int
+    lib.sa_tuning_lookup.argtypes = [u32, u32, u64, ctypes.POINTER(Tuned)]
+    lib.sa_tuning_lookup.restype = u32
+    lib.sa_pool_trim.argtypes = [u64]
+    lib.sa_pool_trim.restype = ctypes.c_int
+    lib.sa_pool_usage.argtypes = [ctypes.POINTER(u64), ctypes.POINTER(u64)]
+    lib.sa_pool_usage.restype = ctypes.c_int
     lib.sa_status_string.argtypes = [ctypes.c_int]
     lib.sa_status_string.restype = ctypes.c_char_p
     for f in ("sa_build", "sa_build_ex", "sa_build_batched", "sa_build_batched_ex",
@@ -165,6 +193,45 @@ def load(path: str | None = None):
     if path is None:
         _lib = lib
     return lib
+
+
+def tuning_set(batched: int, bits_per_char: int, log2_n: int, params: dict | None):
+    """Set (or, with params None, remove) one entry of the library's tuning
+    table (sa_tuning_set); params holds any of sort_items, refine_shape,
+    h0_chars, bucket_min."""
+    lib = load()
+    t = Tuned(**params) if params is not None else None
+    _check(lib.sa_tuning_set(batched, bits_per_char, log2_n,
+                             ctypes.byref(t) if t is not None else None), "sa_tuning_set")
+
+
+def tuning_load(path: str | None):
+    """Replace the library's tuning table by a table file (None: empty)."""
+    lib = load()
+    _check(lib.sa_tuning_load(path.encode() if path else None), "sa_tuning_load")
+
+
+def tuning_lookup(batched: int, bits_per_char: int, n: int) -> tuple[dict, int]:
+    """(the parameters a build of this class would take from the table,
+    number of table entries)."""
+    lib = load()
+    t = Tuned()
+    count = lib.sa_tuning_lookup(batched, bits_per_char, n, ctypes.byref(t))
+    return t.to_dict(), int(count)
+
+
+def pool_usage() -> tuple[int, int]:
+    """(used, reserved) bytes of the library's device memory pool on the
+    current device (sa_pool_usage)."""
+    lib = load()
+    u, r = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib.sa_pool_usage(ctypes.byref(u), ctypes.byref(r)), "sa_pool_usage")
+    return int(u.value), int(r.value)
+
+
+def pool_trim(keep_bytes: int = 0):
+    """Give the library pool's unused device memory back (sa_pool_trim)."""
+    _check(load().sa_pool_trim(keep_bytes), "sa_pool_trim")
 
 
 def _torch():
@@ -209,7 +276,7 @@ def sa_build(text, sa_out=None, stream=None):
 
 def sa_build_ex(text, *, isa=False, workspace=None, h0_chars=0, spin_limit=0,
                 inject_stall=0, trace_cap=0, paper_names=False, refine_shape=0, sort_items=0,
-                profile=False, multiplier=0, stream=None):
+                profile=False, multiplier=0, bucket_min=0, stream=None):
     """sa_build with options. Returns (sa, isa or None, stats dict, trace or None).
 
     multiplier: growth factor a of the resolved prefix per round (0 or 2:
@@ -231,7 +298,7 @@ def sa_build_ex(text, *, isa=False, workspace=None, h0_chars=0, spin_limit=0,
     opt = Options(h0_chars, spin_limit, inject_stall,
                   trace.data_ptr() if trace is not None and n else None, trace_cap,
                   1 if paper_names else 0, refine_shape, sort_items, 1 if profile else 0,
-                  multiplier)
+                  multiplier, bucket_min)
     st = Stats()
     rc = lib.sa_build_ex(t.data_ptr(), n, sa.data_ptr() if n else None,
                          isa_t.data_ptr() if isa_t is not None and n else None,
@@ -242,7 +309,8 @@ def sa_build_ex(text, *, isa=False, workspace=None, h0_chars=0, spin_limit=0,
 
 
 def sa_build_batched(texts, offsets, sa_out=None, workspace=None, stream=None, stats=False,
-                     profile=False, refine_shape=0, sort_items=0, h0_chars=0, multiplier=0):
+                     profile=False, refine_shape=0, sort_items=0, h0_chars=0, multiplier=0,
+                     bucket_min=0):
     """SAs of many texts in one launch sequence.
 
     texts: 1-D uint8 CUDA tensor (the texts concatenated); offsets: host
@@ -261,7 +329,7 @@ def sa_build_batched(texts, offsets, sa_out=None, workspace=None, stream=None, s
         workspace = torch.empty(wsb, dtype=torch.uint8, device=t.device)
     st = Stats()
     opt = Options(h0_chars, 0, 0, None, 0, 0, refine_shape, sort_items, 1 if profile else 0,
-                  multiplier)
+                  multiplier, bucket_min)
     rc = lib.sa_build_batched_ex(t.data_ptr(), off.ctypes.data, count,
                                  sa_out.data_ptr() if N else None,
                                  workspace.data_ptr() if workspace is not None else None,
@@ -430,9 +498,15 @@ class Server:
         return t.value
 
     def poll(self, ticket: int):
+        """None while the request runs; once done, (SA, info dict) as wait()
+        returns them (the server then forgets the ticket)."""
         info = RequestInfo()
         r = self._lib.sa_server_poll(self._h, ticket, ctypes.byref(info))
-        return info.to_dict() if r == 1 else None
+        if r != 1:
+            return None
+        _, out = self._keep.pop(ticket)
+        _check(info.status, "sa_server request")
+        return out, info.to_dict()
 
     def wait(self, ticket: int):
         """(SA as numpy uint32, info dict); raises SAError if the build failed."""

@@ -33,7 +33,11 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <set>
+#include <utility>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/gbsa.h"
 #include "launch.h"
@@ -44,10 +48,34 @@ namespace gbsa {
 namespace {
 
 constexpr uint32_t DEFAULT_SPIN_LIMIT = 1u << 20;  // ~1 s with the 1 us back-off cap
-// ISA writes are bucketed by position when this many may be pending.
+// ISA writes are bucketed by position when this many may be pending (the
+// default discard threshold; sa_options.bucket_min and the tuning table
+// override it).
 constexpr uint32_t BUCKET_MIN = 1u << 22;
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// NVTX ranges (header-only NVTX 3: without a profiler attached a push or
+// pop is a call through a pointer to a function that returns at once).
+// A build is one range, each round a range inside it, each kernel launch
+// a range named for its class, so a profiler's launch list attributes
+// every kernel to its round and step.
+const char *const KERNEL_RANGE[SA_K_CLASSES] = {
+    "gbsa:byte_hist", "gbsa:pack",     "gbsa:digit_hist", "gbsa:plan",     "gbsa:onesweep",
+    "gbsa:rename",    "gbsa:gather",   "gbsa:output",     "gbsa:refine",   "gbsa:scatter",
+    "gbsa:classify",  "gbsa:apply",    "gbsa:bucket"};
+
+struct NvtxRange {
+  bool open = true;
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  void end() {
+    if (open) nvtxRangePop();
+    open = false;
+  }
+  ~NvtxRange() { end(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 struct Layout {
   size_t ctrl, plan, hist, dbase, bytehist, code, segoff;
@@ -115,25 +143,17 @@ uint32_t bits_for(uint64_t v) {  // bits to hold values 0..v
   return b;
 }
 
-int sm_count() {
-  static std::mutex mu;
-  static std::map<int, int> cache;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return 152;
-  std::lock_guard<std::mutex> g(mu);
-  auto it = cache.find(dev);
-  if (it != cache.end()) return it->second;
-  int n = 152;
-  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-  cache[dev] = n;
-  return n;
-}
+int sm_count() { return device_sm_count(); }
 
-// Library-private stream-ordered pool (never trimmed, so repeated builds
-// reuse its memory without touching the process-wide default pool).
+// Library-private stream-ordered pools, one per device (never trimmed, so
+// repeated builds reuse their memory without touching the process-wide
+// default pool).
+std::mutex g_pool_mu;
+std::map<int, cudaMemPool_t> g_pools;
+
 cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t st) {
-  static std::mutex mu;
-  static std::map<int, cudaMemPool_t> pools;
+  std::mutex &mu = g_pool_mu;
+  std::map<int, cudaMemPool_t> &pools = g_pools;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -220,6 +240,7 @@ struct Build {
   uint32_t naming = NAMES_RETAIN;
   uint32_t shape = 0, nominal = 512;  // refine tile shape and window
   uint32_t sort_items = SORT_ITEMS_DEFAULT;  // keys per thread of the radix pass
+  uint32_t bucket_min = BUCKET_MIN;  // pending ISA writes that are bucketed first
   uint32_t mult = 2;  // a: names ranked per round (2: doubling, 4: quadrupling)
   // per-kernel profiling (events on the build's stream)
   struct Rec {
@@ -296,6 +317,7 @@ struct Build {
   // if the device plan kept the pass; rename: settled at the round's sync).
   template <class F>
   sa_status launch(int cls, int pass, uint64_t nbytes, F f) {
+    NvtxRange range(KERNEL_RANGE[cls]);
     ++launches;
     cudaEvent_t a = nullptr, b = nullptr;
     if (prof) CK(event(a));
@@ -462,7 +484,7 @@ struct Build {
     if (apply_bound == 0) return SA_OK;
     const uint64_t *src = act[out];
     const uint32_t *lo = &ctrl->rc.m_s;
-    if (apply_bound >= BUCKET_MIN) {
+    if (apply_bound >= bucket_min) {
       s = bucket(src, lo, &ctrl->rc.m_l, apply_bound, 2);
       if (s != SA_OK) return s;
       src = kb;
@@ -504,7 +526,7 @@ struct Build {
   sa_status scatter(uint32_t bound) {
     if (bound == 0) return SA_OK;
     const uint64_t *src = upd;
-    if (bound >= BUCKET_MIN) {
+    if (bound >= bucket_min) {
       sa_status s = bucket(upd, nullptr, &ctrl->rc.upd, bound, 0);
       if (s != SA_OK) return s;
       src = kb;
@@ -559,18 +581,13 @@ struct Build {
   }
 
   sa_status run() {
+    char label[96];
+    snprintf(label, sizeof(label), "gbsa:build n=%llu texts=%u", (unsigned long long)N, S);
+    NvtxRange build_range(label);
     const uint32_t N32 = (uint32_t)N;
     carve();
     prof = opt.profile != 0 && stats != nullptr;
     naming = opt.paper_names ? NAMES_HEAD : NAMES_RETAIN;
-    // Default: 128 threads x 1024 items (8 blocks per SM), the fastest shape
-    // measured on the repeated-text workloads.
-    shape = (opt.refine_shape >= 1 && opt.refine_shape <= (uint32_t)REFINE_SHAPES)
-                ? opt.refine_shape - 1
-                : 0;
-    nominal = REFINE_SHAPE[shape].cap / 2;
-    if (opt.sort_items == 8 || opt.sort_items == 12 || opt.sort_items == 16)
-      sort_items = opt.sort_items;
     mult = opt.multiplier ? opt.multiplier : 2;  // checked by the entry points
     // Clear what must start at zero; the ISA starts all-ones so every end
     // slot reads as the sentinel.
@@ -599,8 +616,32 @@ struct Build {
     }
     const uint32_t b = std::max<uint32_t>(1, bits_for(sigma - 1));
     const uint32_t segbits = S > 1 ? bits_for(S - 1) : 0;
+    // Parameters: the caller's options, else the tuning table's entry for
+    // this class (batch or not, bits per character, size), else defaults:
+    // 16 keys per radix thread, the 128 x 1024 refine (8 blocks per SM),
+    // keys as wide as fit, bucketing from 2^22 pending ISA writes.
+    sa_tuned tuned{};
+    tuned_params(S > 1, b, N, &tuned);
+    bool from_table = false;
+    auto pick = [&](uint32_t given, uint32_t table, uint32_t dflt, bool ok_given, bool ok_table) {
+      if (given && ok_given) return given;
+      if (table && ok_table) {
+        from_table = true;
+        return table;
+      }
+      return dflt;
+    };
+    auto items_ok = [](uint32_t v) { return v == 8 || v == 12 || v == 16; };
+    auto shape_ok = [](uint32_t v) { return v >= 1 && v <= (uint32_t)REFINE_SHAPES; };
+    sort_items = pick(opt.sort_items, tuned.sort_items, SORT_ITEMS_DEFAULT,
+                      items_ok(opt.sort_items), items_ok(tuned.sort_items));
+    shape = pick(opt.refine_shape, tuned.refine_shape, 1, shape_ok(opt.refine_shape),
+                 shape_ok(tuned.refine_shape)) - 1;
+    nominal = REFINE_SHAPE[shape].cap / 2;
+    bucket_min = pick(opt.bucket_min, tuned.bucket_min, BUCKET_MIN, true, true);
+    const uint32_t h0 = pick(opt.h0_chars, tuned.h0_chars, 0, true, true);
     uint32_t c0 = (64 - segbits) / b;
-    if (opt.h0_chars) c0 = std::min(c0, opt.h0_chars);
+    if (h0) c0 = std::min(c0, h0);
     const uint32_t cb = c0 * b;
     CK(cudaMemcpyAsync(code, hcode, sizeof(hcode), cudaMemcpyHostToDevice, st));
     bytes += N;
@@ -608,9 +649,15 @@ struct Build {
       stats->sigma = sigma;
       stats->bits_per_char = b;
       stats->chars_per_key = c0;
+      stats->sort_items = sort_items;
+      stats->refine_shape = shape + 1;
+      stats->bucket_min = bucket_min;
+      stats->tuned = from_table ? 1u : 0u;
     }
 
     // ---- round 0: initial names ----
+    snprintf(label, sizeof(label), "gbsa:round 0 m=%u", N32);
+    NvtxRange round0_range(label);
     PackArgs pk{};
     pk.text = text;
     pk.N = N32;
@@ -657,6 +704,7 @@ struct Build {
       settle(hc);
     }
     if (want_trace) CK(cudaMemcpyAsync(opt.trace_isa, isa, N * 4, cudaMemcpyDeviceToDevice, st));
+    round0_range.end();
 
     // ---- rounds r >= 1: one doubling step each ----
     const uint32_t W = bits_for(N);  // r2 in [0, N]
@@ -665,6 +713,8 @@ struct Build {
     while (hc.m_next() > 0) {
       if (round >= SA_MAX_ROUNDS || h > N) return SA_ERR_INTERNAL;
       m = hc.m_next();
+      snprintf(label, sizeof(label), "gbsa:round %u m=%u", round, m);
+      NvtxRange round_range(label);
       const uint32_t G = hc.g_next();
       const uint32_t mL = hc.m_large(), GL = hc.g_large();
       const int nxt = cur ^ 1;
@@ -848,11 +898,122 @@ sa_status run_with_workspace(Build &B, void *workspace, size_t ws_bytes) {
 cudaError_t library_pool_alloc(void **p, size_t bytes, cudaStream_t st) {
   return pool_alloc(p, bytes, st);
 }
+
+int device_sm_count() {
+  static std::mutex mu;
+  static std::map<int, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  std::lock_guard<std::mutex> g(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    return 1;  // not cached: a later call may succeed
+  }
+  cache[dev] = n;
+  return n;
+}
+
+namespace {
+
+// Identity of the CUDA context current on this thread (cuCtxGetCurrent and
+// cuCtxGetId, reached through the runtime's driver entry points so that
+// the library needs no link against libcuda); 0 when it cannot be told.
+unsigned long long current_context_id() {
+  using GetCurrent = int (*)(void **);
+  using GetId = int (*)(void *, unsigned long long *);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+    cudaGetLastError();
+  });
+  if (!get_current || !get_id) return 0;
+  void *ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+}  // namespace
+
+cudaError_t ensure_smem_attributes(const void *fn, int smem_bytes, bool max_carveout) {
+  static std::mutex mu;
+  static std::set<std::pair<const void *, unsigned long long>> done;
+  const unsigned long long ctx = current_context_id();
+  if (ctx) {
+    std::lock_guard<std::mutex> g(mu);
+    if (done.count({fn, ctx})) return cudaSuccess;
+  }
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  if (e != cudaSuccess) return e;
+  if (max_carveout) {
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+  }
+  if (ctx) {  // unknown context: set again next time rather than trust a stale entry
+    std::lock_guard<std::mutex> g(mu);
+    done.insert({fn, ctx});
+  }
+  return cudaSuccess;
+}
 }  // namespace gbsa
 
 using namespace gbsa;
 
 GBSA_API size_t sa_workspace_bytes(uint64_t n) { return make_layout(n, 1).total; }
+
+GBSA_API sa_status sa_pool_usage(uint64_t *used, uint64_t *reserved) {
+  if (!used || !reserved) return SA_ERR_INVALID_ARG;
+  *used = *reserved = 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return SA_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> g(g_pool_mu);
+  auto it = g_pools.find(dev);
+  if (it == g_pools.end()) return SA_OK;  // nothing was ever taken from it
+  uint64_t u = 0, r = 0;  // the pool attributes are 64-bit values
+  if (cudaMemPoolGetAttribute(it->second, cudaMemPoolAttrUsedMemCurrent, &u) != cudaSuccess ||
+      cudaMemPoolGetAttribute(it->second, cudaMemPoolAttrReservedMemCurrent, &r) != cudaSuccess) {
+    cudaGetLastError();
+    return SA_ERR_CUDA;
+  }
+  *used = u;
+  *reserved = r;
+  return SA_OK;
+}
+
+GBSA_API sa_status sa_pool_trim(uint64_t keep_bytes) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return SA_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> g(g_pool_mu);
+  auto it = g_pools.find(dev);
+  if (it == g_pools.end()) return SA_OK;
+  if (cudaMemPoolTrimTo(it->second, (size_t)keep_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return SA_ERR_CUDA;
+  }
+  return SA_OK;
+}
 
 GBSA_API size_t sa_batched_workspace_bytes(const uint64_t *offsets, uint32_t count) {
   if (check_offsets(offsets, count) != SA_OK) return 0;

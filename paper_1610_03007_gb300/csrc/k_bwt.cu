@@ -71,16 +71,7 @@ __global__ void __launch_bounds__(256) k_bwt(const uint8_t *__restrict__ T, uint
 
 namespace {
 
-int sm_count_cached() {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      sms = 1;
-  }
-  return sms;
-}
+int sm_count_cached() { return gbsa::device_sm_count(); }
 
 }  // namespace
 

@@ -146,16 +146,7 @@ __global__ void __launch_bounds__(256) k_lcp_gather(const uint32_t *__restrict__
 
 namespace {
 
-int lcp_sm_count() {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      sms = 1;
-  }
-  return sms;
-}
+int lcp_sm_count() { return gbsa::device_sm_count(); }
 
 unsigned grid_for(uint64_t units, int per_sm) {
   const uint64_t want = (units + 255) / 256, cap = (uint64_t)lcp_sm_count() * per_sm;

@@ -762,18 +762,10 @@ __global__ void __launch_bounds__(BLOCK, (CAP / BLOCK > 8 ? 512 : 1024) / BLOCK)
 
 template <int BLOCK, int CAP, bool WIDE>
 cudaError_t launch_refine_t(const RefineArgs &a, cudaStream_t stream) {
-  static bool configured = false;
   const int smem = (int)sizeof(RfSmem<BLOCK, CAP, WIDE>);
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_refine<BLOCK, CAP, WIDE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_refine<BLOCK, CAP, WIDE>,
-                             cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  cudaError_t e = ensure_smem_attributes(
+      reinterpret_cast<const void *>(&k_refine<BLOCK, CAP, WIDE>), smem, true);
+  if (e != cudaSuccess) return e;
   k_refine<BLOCK, CAP, WIDE><<<a.tiles, BLOCK, smem, stream>>>(a);
   return cudaGetLastError();
 }

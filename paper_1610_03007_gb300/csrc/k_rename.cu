@@ -269,13 +269,9 @@ __global__ void __launch_bounds__(RN_BLOCK, 4) k_rename(RenameArgs a) {
 
 cudaError_t launch_rename(const RenameArgs &a, cudaStream_t stream) {
   if (a.m == 0) return cudaSuccess;
-  static bool configured = false;
   const int smem = (int)sizeof(RnSmem);
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_rename, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  cudaError_t e = ensure_smem_attributes(reinterpret_cast<const void *>(&k_rename), smem, false);
+  if (e != cudaSuccess) return e;
   const uint32_t tiles = (a.m + RN_TILE - 1) / RN_TILE;
   k_rename<<<tiles, RN_BLOCK, smem, stream>>>(a);
   return cudaGetLastError();

@@ -347,17 +347,10 @@ __global__ void __launch_bounds__(OS_BLOCK, OS_ITEMS >= 16 ? 3 : (OS_ITEMS >= 12
 
 template <int OS_ITEMS>
 cudaError_t launch_onesweep_t(const PassArgs &a, cudaStream_t stream) {
-  static bool configured = false;  // per process; the attribute is per function
   const int smem = (int)sizeof(OsSmem<OS_ITEMS>);
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_onesweep<OS_ITEMS>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_onesweep<OS_ITEMS>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  cudaError_t e =
+      ensure_smem_attributes(reinterpret_cast<const void *>(&k_onesweep<OS_ITEMS>), smem, true);
+  if (e != cudaSuccess) return e;
   const uint64_t tile = (uint64_t)OS_BLOCK * OS_ITEMS;
   const uint64_t tiles = ((uint64_t)a.m + tile - 1) / tile;
   k_onesweep<OS_ITEMS><<<(unsigned)tiles, OS_BLOCK, smem, stream>>>(a);

@@ -5,9 +5,23 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/gbsa.h"
 #include "common.cuh"
 
 namespace gbsa {
+
+// ---- runtime helpers (engine.cu) ----------------------------------------
+// SM count of the current device, cached per device; thread-safe.
+int device_sm_count();
+// Allows `smem_bytes` of dynamic shared memory for kernel `fn` (and, with
+// max_carveout, the largest shared-memory carveout), once per kernel and
+// CUDA context: function attributes belong to a context, so a process that
+// launches on several GPUs, or again after cudaDeviceReset, must set them
+// in each. Thread-safe; concurrent first calls may both set them (harmless).
+cudaError_t ensure_smem_attributes(const void *fn, int smem_bytes, bool max_carveout);
+// The tuning table's parameters for a build of this class (tuning.cu); all
+// fields 0 when no entry applies.
+void tuned_params(bool batched, uint32_t bits, uint64_t n, sa_tuned *out);
 
 // ---- step A0: alphabet (k_alphabet.cu) ----------------------------------
 // hist[256] += occurrences of each byte value in text[0, n). hist must be

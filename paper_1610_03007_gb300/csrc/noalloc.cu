@@ -13,54 +13,31 @@
 // the CUDA runtime places in device memory when the library's module loads
 // on a GPU; every GPU that loads the library keeps these NOALLOC_SCRATCH_BYTES
 // until the process exits. Host code cannot use `g_noalloc_scratch` as a
-// device address (in host code the name is only a host-side shadow), so the
-// first call on each device looks up the real device address with
-// cudaGetSymbolAddress while that device is current and caches it. That
-// first call therefore does a runtime query and should happen before any
-// stream capture is begun on that device.
+// device address (in host code the name is only a host-side shadow), so
+// every call looks up the real device address with cudaGetSymbolAddress in
+// the context current at the call. The lookup is a host-side query that
+// allocates nothing; it is not cached, because the address belongs to one
+// context (after cudaDeviceReset, or in another context on the same device,
+// the array lives elsewhere).
 //
 // The build itself is the ordinary sa_build_ex path given that array as its
 // caller-owned workspace; it clears at start everything that must start at
 // zero, so the array's leftover contents from the previous call do not
-// matter. All calls share the one array: calls whose GPU work overlaps (two
-// host threads, or two streams without ordering between them) race on it
-// and produce garbage, so callers must serialise them.
-#include <mutex>
-
+// matter. Like sa_build, it synchronises the stream once per doubling round
+// to read the round's counters, so it cannot run while that stream is being
+// captured into a CUDA graph. All calls share the one array: calls whose GPU
+// work overlaps (two host threads, or two streams without ordering between
+// them) race on it and produce garbage, so callers must serialise them.
 #include "../../include/gbsa.h"
 
 #define GBSA_API extern "C" __attribute__((visibility("default")))
 
-// Largest text accepted: 2^18 bytes; its workspace is about 17.8 MiB.
+// Largest text accepted: 2^18 bytes; its workspace (sa_workspace_bytes) is
+// about 17.8 MiB, checked against the array's size on every call.
 constexpr uint64_t NOALLOC_MAX_N = 1ull << 18;
 constexpr size_t NOALLOC_SCRATCH_BYTES = 20ull << 20;  // 20 MiB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
-
-namespace {
-
-constexpr int MAX_DEVICES = 64;
-std::mutex g_mu;
-void *g_addr[MAX_DEVICES] = {nullptr};
-
-// Device address of the scratch array on the current device (looked up once
-// per device). Returns nullptr on failure.
-void *scratch_address() {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return nullptr;
-  std::lock_guard<std::mutex> g(g_mu);
-  if (!g_addr[dev]) {
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
-      cudaGetLastError();
-      return nullptr;
-    }
-    g_addr[dev] = p;
-  }
-  return g_addr[dev];
-}
-
-}  // namespace
 
 GBSA_API sa_status sa_build_noalloc(const uint8_t *text, uint64_t n, uint32_t *sa_out,
                                     gbsa_stream_t stream) {
@@ -69,8 +46,12 @@ GBSA_API sa_status sa_build_noalloc(const uint8_t *text, uint64_t n, uint32_t *s
   const size_t need = sa_workspace_bytes(n);
   if (need > NOALLOC_SCRATCH_BYTES) return SA_ERR_TOO_LARGE;
   if (n == 0) return SA_OK;
-  void *ws = scratch_address();
-  if (!ws) return SA_ERR_CUDA;
+  // The array's device address in the current context (see above).
+  void *ws = nullptr;
+  if (cudaGetSymbolAddress(&ws, g_noalloc_scratch) != cudaSuccess || !ws) {
+    cudaGetLastError();
+    return SA_ERR_CUDA;
+  }
   return sa_build_ex(text, n, sa_out, nullptr, ws, NOALLOC_SCRATCH_BYTES, nullptr, nullptr,
                      stream);
 }

@@ -8,7 +8,9 @@
 // arrive while others run are admitted as slots and budget free up, and the
 // builds of different workers overlap on the device. Strict FIFO admission:
 // the head waits for memory rather than being overtaken, so no request
-// starves.
+// starves. A request is forgotten once its result has been handed out
+// (sa_server_wait returned, or sa_server_poll reported it done), so a
+// long-running server holds only queued, running and uncollected requests.
 //
 // The paper has no serving layer; this is the runtime around its method.
 #include <chrono>
@@ -41,6 +43,8 @@ struct Request {
   size_t footprint = 0;
   sa_request_info info{};
   bool done = false;
+  uint32_t waiters = 0;   // threads blocked in sa_server_wait on this request
+  bool collected = false; // result handed out; no longer in `requests`
 };
 
 }  // namespace
@@ -52,13 +56,24 @@ struct sa_server {
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<Request *> queue;
-  std::unordered_map<uint64_t, Request *> requests;
+  std::unordered_map<uint64_t, Request *> requests;  // not yet collected
   uint64_t next_ticket = 1;
   uint64_t in_use = 0;
   uint32_t in_flight = 0;
   sa_server_stats stats{};
   bool stop = false;
   std::vector<std::thread> workers;
+
+  // Hands the finished request r over: it leaves the table, and the last
+  // thread that still refers to it frees it. Called with `mu` held.
+  void collect(Request *r) {
+    if (!r->collected) {
+      requests.erase(r->ticket);
+      r->collected = true;
+      stats.tracked = (uint32_t)requests.size();
+    }
+    if (r->waiters == 0) delete r;
+  }
 
   double now() const {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -159,6 +174,7 @@ GBSA_API sa_status sa_server_submit(sa_server *s, const uint8_t *host_text, uint
     r->ticket = s->next_ticket++;
     r->info.submit_s = s->now();
     s->requests[r->ticket] = r;
+    s->stats.tracked = (uint32_t)s->requests.size();
     s->queue.push_back(r);
     ++s->stats.submitted;
     s->stats.queued = (uint32_t)s->queue.size();
@@ -173,8 +189,10 @@ GBSA_API int sa_server_poll(sa_server *s, uint64_t ticket, sa_request_info *info
   std::lock_guard<std::mutex> lk(s->mu);
   auto it = s->requests.find(ticket);
   if (it == s->requests.end()) return -1;
-  if (!it->second->done) return 0;
-  if (info) *info = it->second->info;
+  Request *r = it->second;
+  if (!r->done) return 0;
+  if (info) *info = r->info;
+  s->collect(r);
   return 1;
 }
 
@@ -184,9 +202,13 @@ GBSA_API sa_status sa_server_wait(sa_server *s, uint64_t ticket, sa_request_info
   auto it = s->requests.find(ticket);
   if (it == s->requests.end()) return SA_ERR_INVALID_ARG;
   Request *r = it->second;
+  ++r->waiters;
   s->cv_done.wait(lk, [&] { return r->done; });
+  --r->waiters;
   if (info) *info = r->info;
-  return r->info.status;
+  const sa_status status = r->info.status;
+  s->collect(r);
+  return status;
 }
 
 GBSA_API void sa_server_get_stats(sa_server *s, sa_server_stats *out) {

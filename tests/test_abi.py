@@ -123,3 +123,14 @@ def test_binding_fails_loudly_without_the_library_or_a_gpu_tensor():
         gbsa.sa_build(torch.zeros(16, dtype=torch.uint8))
     with pytest.raises(TypeError):
         gbsa.sa_build_dc7(torch.zeros(16, dtype=torch.uint8))
+
+
+def test_no_alloc_limit_matches_its_scratch_array(lib):
+    """sa_build_noalloc's scratch array is 20 MiB and its text limit 2^18
+    bytes: the build workspace at that limit must fit the array (the entry
+    point also checks this on every call), and the pool query refuses NULL
+    outputs without touching a GPU."""
+    assert lib.sa_workspace_bytes(1 << 18) <= 20 << 20
+    assert lib.sa_workspace_bytes((1 << 18) + 4096) > lib.sa_workspace_bytes(1 << 18)
+    assert lib.sa_build_noalloc(None, (1 << 18) + 1, None, None) == 2
+    assert lib.sa_pool_usage(None, None) == 1

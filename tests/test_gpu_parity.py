@@ -255,11 +255,15 @@ def test_every_radix_tile_size(gb, orc, items):
     assert list(sa.cpu().numpy()) == list(range(299999, -1, -1))
 
 
-def test_workload_3_full_size_properties(gb, orc):
+def test_workload_3_full_size_complete(gb, orc):
     """n = 2^31 order-3 Markov DNA with 5% copied segments (the largest
-    input, about 154 GB on the device): SA is a permutation (bitmap), 200000
-    sampled adjacent suffixes compare strictly increasing, and the oracle's
-    one-by-one rank of two sampled suffixes equals their SA positions."""
+    input and the benchmark's headline, about 153 GB on the device), in the
+    benchmark's launch configuration (the library's tuned parameters, a
+    caller workspace): the whole SA through the linear-time checker of
+    Burkhardt and Kaerkkaeinen (a permutation, and every adjacent pair in
+    order through the ranks: the SA of Section 2's definition), plus 200000
+    sampled adjacent suffixes compared directly and the oracle's rank of one
+    suffix computed one by one."""
     import torch
     n = 1 << 31
     t = gen.text("markov", 3001, n)
@@ -272,8 +276,8 @@ def test_workload_3_full_size_properties(gb, orc):
     del sa, d
     torch.cuda.empty_cache()
     assert stats["rounds"] > 3
-    assert orc.check_permutation(s) == 0
+    assert orc.check_sa(t, s) == (0, -1)
     rng = np.random.default_rng(31)
     assert orc.check_adjacent(t, s, rng.integers(0, n - 1, 200000)) == 0
-    for j in rng.integers(0, n, 2):
-        assert orc.suffix_rank(t, int(s[j])) == int(j)
+    j = int(rng.integers(0, n))
+    assert orc.suffix_rank(t, int(s[j])) == j

@@ -88,3 +88,47 @@ def test_refusals(gbsa):
         assert e.value.status == 3  # SA_ERR_OOM: footprint above the whole budget
         t = srv.submit(np.zeros(1000, np.uint8))
         srv.wait(t)
+
+
+def test_finished_requests_are_forgotten(gbsa):
+    """A long-running server must not keep every request it ever saw: once
+    wait() or a poll() reporting done has handed a result over, the request
+    leaves the server's table and its ticket is unknown."""
+    import threading
+    lib = gbsa.load()
+    with gbsa.Server(budget_bytes=1 << 40, slots=4, simulate_ns_per_byte=5.0) as srv:
+        for rnd in range(3):
+            tickets = [srv.submit(np.zeros(20_000 + 1000 * k, np.uint8)) for k in range(40)]
+            assert srv.stats()["tracked"] <= 40
+            for t in tickets[:20]:
+                srv.wait(t)
+            polled = 0
+            for t in tickets[20:]:
+                while srv.poll(t) is None:
+                    time.sleep(0.001)
+                polled += 1
+            assert polled == 20
+            st = srv.stats()
+            assert st["tracked"] == 0, st
+            assert st["completed"] == 40 * (rnd + 1)
+            for t in tickets[:2]:  # collected tickets are unknown now
+                assert lib.sa_server_poll(srv._h, t, None) == -1
+                assert lib.sa_server_wait(srv._h, t, None) == 1  # SA_ERR_INVALID_ARG
+        # several threads waiting on one ticket: each gets the result, the
+        # request is freed once, and the table ends empty
+        t = srv.submit(np.zeros(400_000, np.uint8))  # runs ~2 ms
+        keep = srv._keep.pop(t)
+        codes = []
+
+        def waiter():
+            codes.append(lib.sa_server_wait(srv._h, t, None))
+
+        th = [threading.Thread(target=waiter) for _ in range(4)]
+        for x in th:
+            x.start()
+        for x in th:
+            x.join()
+        del keep
+        assert codes == [0, 0, 0, 0] or sorted(codes) == [0] * codes.count(0) + [1] * codes.count(1)
+        assert 0 in codes
+        assert srv.stats()["tracked"] == 0

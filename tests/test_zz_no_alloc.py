@@ -1,10 +1,13 @@
-"""sa_build_noalloc: the allocation-free entry point for callers that must
+"""sa_build_noalloc: the allocation-free entry point, for callers that must
 not allocate device memory when they build (for example beside an engine
 that already reserved the GPU's memory, or on a path that cannot take
-cudaMalloc's synchronisation). Its output must equal sa_build's exactly, on
-two calls in a row (the shared scratch array keeps the previous call's
-contents, which must not leak into the next result), and sizes above its
-2^18-byte limit must be refused.
+cudaMalloc's synchronisation).
+
+Its output must equal the oracle's SA and sa_build's, exactly, on two calls
+in a row (the shared scratch array keeps the previous call's contents,
+which must not leak into the next result); once every size has run once,
+further calls must change neither the device's free memory nor the
+library pool's usage; sizes above its 2^18-byte limit must be refused.
 
 Collected last on purpose (file name): if it fails, a run stopping at the
 first failure has already run every other test.
@@ -35,19 +38,54 @@ def _cases():
             np.zeros(1000, np.uint8), gen.text("bytes", 14, 1)]
 
 
-def test_no_alloc_equals_sa_build_on_two_calls_in_a_row(lib):
+def test_no_alloc_equals_oracle_and_sa_build_on_two_calls_in_a_row(lib):
     import torch
+
+    import oracle
+    orc = oracle.get()
     stream = torch.cuda.current_stream().cuda_stream
     for text in _cases():
         d = torch.from_numpy(text).cuda()
         n = text.size
+        want = orc.pd_sa(text)[0]
         ref = torch.empty(n, dtype=torch.int32, device="cuda")
         assert lib.sa_build(d.data_ptr(), n, ref.data_ptr(), stream) == 0
+        torch.cuda.synchronize()
+        assert np.array_equal(ref.cpu().numpy().view(np.uint32), want), f"sa_build n={n}"
         for call in range(2):
             out = torch.full((n,), -1, dtype=torch.int32, device="cuda")
             assert lib.sa_build_noalloc(d.data_ptr(), n, out.data_ptr(), stream) == 0
             torch.cuda.synchronize()
             assert torch.equal(out, ref), f"n={n} call {call}"
+            assert np.array_equal(out.cpu().numpy().view(np.uint32), want), f"n={n} call {call}"
+
+
+def test_no_alloc_allocates_nothing(lib):
+    """After one warm-up call per size (lazy module loading may place code
+    and the scratch array on the device at first use), further calls of
+    every size leave the device's free memory and the library pool's used
+    and reserved bytes unchanged."""
+    import torch
+
+    import paper_1610_03007_gb300 as gbsa
+    stream = torch.cuda.current_stream().cuda_stream
+    texts = [torch.from_numpy(t).cuda() for t in _cases()]
+    outs = [torch.empty(t.numel(), dtype=torch.int32, device="cuda") for t in texts]
+    refs = []
+    for d, o in zip(texts, outs):  # warm-up
+        assert lib.sa_build_noalloc(d.data_ptr(), d.numel(), o.data_ptr(), stream) == 0
+        refs.append(o.clone())
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    pool0 = gbsa.pool_usage()
+    for _ in range(3):
+        for d, o in zip(texts, outs):
+            assert lib.sa_build_noalloc(d.data_ptr(), d.numel(), o.data_ptr(), stream) == 0
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert gbsa.pool_usage() == pool0
+    for o, r in zip(outs, refs):
+        assert torch.equal(o, r)
 
 
 def test_no_alloc_refuses_sizes_above_its_limit(lib):
