@@ -679,8 +679,14 @@ def run_serving(args, emit=True):
     arena = torch.empty(arena_n, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
     out_rates = []
     with gbsa.Server(budget_bytes=100 * 10**9, slots=args.slots) as srv:
+        # Warm-up: module, streams, and the library's memory pool grown to
+        # one largest request per slot, as a server that has been running a
+        # while holds it (growing the pool inside a timed rate would charge
+        # one-time device allocations to the requests then in flight).
         for t in [srv.submit(views[k % 2][: 1 << 20]) for k in range(8)]:
-            srv.wait(t)  # warm-up: pool, module, streams
+            srv.wait(t)
+        for t in [srv.submit(views[k % 2]) for k in range(args.slots)]:
+            srv.wait(t)
         for lam in rates:
             arr, sizes, kinds = streams[lam]
             outs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)

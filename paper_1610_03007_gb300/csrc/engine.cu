@@ -672,6 +672,7 @@ struct Build {
     const uint32_t bits0 = cb + segbits;
     pk.spec = spec_for(bits0);
     pk.hist = hist;
+    pk.top_only = (S == 1 && 8 % b == 0 && cb % 8 == 0 && c0 <= 64 && pk.spec.P * 8 == cb) ? 1u : 0u;
     CK(cudaMemsetAsync(hist, 0, (size_t)pk.spec.P * RADIX * 4, st));
     s = launch(SA_K_PACK, 0, 13ull * N, [&] { return launch_pack(pk, st); });
     if (s != SA_OK) return s;

@@ -33,10 +33,12 @@ constexpr int PACK_SPAN = PACK_BLOCK * PACK_ITEMS;
 constexpr uint32_t PACK_SLIDE_MIN = 16;
 
 // Digit histograms of one key (warp-aggregated when a warp shares a digit).
+// With top_only, only the most significant digit's (the others follow from
+// it, k_pack_hist_fixup).
 __device__ __forceinline__ void pack_hist(uint32_t (*s_hist)[RADIX], const DigitSpec &spec,
-                                          uint64_t key, bool valid, int lane) {
+                                          uint64_t key, bool valid, int lane, bool top_only) {
   const uint32_t nvalid = __popc(__ballot_sync(0xffffffffu, valid));
-  for (uint32_t p = 0; p < spec.P; ++p) {
+  for (uint32_t p = top_only ? spec.P - 1 : 0; p < spec.P; ++p) {
     const uint32_t d = digit_of(key, spec.shift[p], spec.bits[p]);
     const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
     if (__all_sync(0xffffffffu, !valid || d == d0)) {
@@ -64,6 +66,9 @@ __global__ void __launch_bounds__(PACK_BLOCK) k_pack(PackArgs a) {
   __shared__ uint32_t s_hist[MAX_PASSES][RADIX];
   __shared__ uint32_t s_seg[2];
   __shared__ uint8_t s_txt[PACK_SPAN + 64];
+  // Fast path: the block's keys, key x at x + x/8 (a thread's 8 consecutive
+  // keys fall in distinct banks), written out with consecutive addresses.
+  __shared__ uint64_t s_keys[PACK_SPAN + PACK_SPAN / 8];
   const int tid = threadIdx.x, lane = tid & 31;
   s_code[tid] = a.code[tid];
   for (int x = tid; x < MAX_PASSES * RADIX; x += PACK_BLOCK) (&s_hist[0][0])[x] = 0;
@@ -102,10 +107,18 @@ __global__ void __launch_bounds__(PACK_BLOCK) k_pack(PackArgs a) {
       if (valid) {
         key = ((key << a.b) | s_txt[x + a.c0 - 1]) & mask;
         out = key | segbits;
-        a.keys[j0 + x] = out;
+        s_keys[x + (x >> 3)] = out;
+      }
+      pack_hist(s_hist, a.spec, out, valid, lane, a.top_only != 0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PACK_ITEMS; ++k) {
+      const uint32_t x = (uint32_t)k * PACK_BLOCK + tid;
+      if (x < span) {
+        a.keys[j0 + x] = s_keys[x + (x >> 3)];
         a.vals[j0 + x] = (uint32_t)(pos0 + x) + s_lo;
       }
-      pack_hist(s_hist, a.spec, out, valid, lane);
     }
   } else {
 #pragma unroll
@@ -141,13 +154,47 @@ __global__ void __launch_bounds__(PACK_BLOCK) k_pack(PackArgs a) {
         a.keys[j] = key;
         a.vals[j] = off + irel + s;
       }
-      pack_hist(s_hist, a.spec, key, valid, lane);
+      pack_hist(s_hist, a.spec, key, valid, lane, a.top_only != 0);
     }
   }
   __syncthreads();
-  for (uint32_t x = tid; x < a.spec.P * RADIX; x += PACK_BLOCK) {
+  for (uint32_t x = a.top_only ? (a.spec.P - 1) * RADIX + tid : tid; x < a.spec.P * RADIX;
+       x += PACK_BLOCK) {
     const uint32_t v = (&s_hist[0][0])[x];
     if (v) atomicAdd(&a.hist[x], v);
+  }
+}
+
+// The digit histograms of a single text's keys from the top digit's alone,
+// when every digit covers g = 8 / b whole characters (b divides 8 and c0 * b
+// is a multiple of 8): digit p of the key at position i is the g-character
+// gram at i + q_p, q_p = (c0 * b - 8 (p + 1)) / b, with code 0 past the end
+// of the text. Over i in [0, n) those grams are the grams at [q_p, n + q_p):
+// the top digit's histogram (q = 0, grams at [0, n)) minus the grams at
+// [0, q_p) plus q_p all-padding grams (digit 0). One block; q_p < 64.
+__global__ void __launch_bounds__(RADIX) k_pack_hist_fixup(PackArgs a) {
+  __shared__ uint8_t s_code[RADIX];
+  __shared__ uint32_t s_gram[64];
+  const uint32_t d = threadIdx.x;
+  s_code[d] = a.code[d];
+  const uint32_t P = a.spec.P, g = 8 / a.b;
+  const uint32_t top = a.hist[(P - 1) * RADIX + d];
+  __syncthreads();
+  // grams at positions 0 .. 63 (all q_p are below c0 <= 64)
+  if (d < 64) {
+    uint32_t v = 0;
+    for (uint32_t c = 0; c < g; ++c) {
+      const uint64_t x = (uint64_t)d + c;
+      v = (v << a.b) | (x < a.N ? s_code[a.text[x]] : 0u);
+    }
+    s_gram[d] = v;
+  }
+  __syncthreads();
+  for (uint32_t p = 0; p + 1 < P; ++p) {
+    const uint32_t qp = (a.cb - 8 * (p + 1)) / a.b;
+    uint32_t below = 0;
+    for (uint32_t x = 0; x < qp; ++x) below += s_gram[x] == d ? 1u : 0u;
+    a.hist[p * RADIX + d] = top - below + (d == 0 ? qp : 0u);
   }
 }
 
@@ -155,6 +202,9 @@ cudaError_t launch_pack(const PackArgs &a, cudaStream_t stream) {
   if (a.N == 0) return cudaSuccess;
   const uint64_t grid = ((uint64_t)a.N + PACK_SPAN - 1) / PACK_SPAN;
   k_pack<<<(unsigned)grid, PACK_BLOCK, 0, stream>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !a.top_only) return e;
+  k_pack_hist_fixup<<<1, RADIX, 0, stream>>>(a);
   return cudaGetLastError();
 }
 

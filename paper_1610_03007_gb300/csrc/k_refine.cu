@@ -206,6 +206,19 @@ cudaError_t launch_wide_finish(const WideArgs &a, cudaStream_t stream) {
 
 // ---- small groups: one tile per block ---------------------------------------
 
+// Tiles whose small groups have at most RF_RANK_GMAX members and whose
+// items would make at most RF_RANK_AVG comparisons each on average (sum of
+// squared group sizes <= RF_RANK_AVG x items) are ordered by counting
+// instead of the in-tile radix sort.
+#ifndef GBSA_RF_RANK_GMAX
+#define GBSA_RF_RANK_GMAX 64
+#endif
+#ifndef GBSA_RF_RANK_AVG
+#define GBSA_RF_RANK_AVG 16
+#endif
+constexpr uint32_t RF_RANK_GMAX = GBSA_RF_RANK_GMAX;
+constexpr uint32_t RF_RANK_AVG = GBSA_RF_RANK_AVG;
+
 template <int BLOCK, int CAP>
 struct RfCfg {
   static constexpr int WARPS = BLOCK / 32;
@@ -250,6 +263,7 @@ struct RfSmem {
   uint32_t goff[C::MAXG + 1];           // start of the local group in the tile
   uint32_t tmp[2][4 * C::WARPS];        // scan scratch (double-buffered)
   uint32_t flag, all_small, upd_local, upd_base, surv_base, grp_base;
+  uint32_t gmax, gsq;  // largest small group, sum of squared small-group sizes
   unsigned long long orv, orv2;
 };
 
@@ -448,6 +462,8 @@ __global__ void __launch_bounds__(BLOCK, (CAP / BLOCK > 8 ? 512 : 1024) / BLOCK)
     S.orv = 0ull;
     S.orv2 = 0ull;
     S.upd_local = 0u;
+    S.gmax = 0u;
+    S.gsq = 0u;
     S.flag = has_error(a.ctrl) ? 1u : 0u;
   }
   __syncthreads();
@@ -464,7 +480,7 @@ __global__ void __launch_bounds__(BLOCK, (CAP / BLOCK > 8 ? 512 : 1024) / BLOCK)
   // Local group table: source position, name, head rank, size (0 for a
   // large group), then exclusive offsets inside the tile.
   uint32_t sz[C::GPT];
-  uint32_t mysum = 0, mybig = 0;
+  uint32_t mysum = 0, mybig = 0, mymax = 0, mysq = 0;
 #pragma unroll
   for (int r = 0; r < C::GPT; ++r) {
     const uint32_t lg = tid * C::GPT + r;
@@ -481,6 +497,16 @@ __global__ void __launch_bounds__(BLOCK, (CAP / BLOCK > 8 ? 512 : 1024) / BLOCK)
       else
         mybig = 1;
       mysum += sz[r];
+      mysq += sz[r] * sz[r];
+      mymax = sz[r] > mymax ? sz[r] : mymax;
+    }
+  }
+  {
+    const uint32_t wsq = __reduce_add_sync(0xffffffffu, mysq);
+    const uint32_t wmax = __reduce_max_sync(0xffffffffu, mymax);
+    if ((tid & 31) == 0 && wsq) {
+      atomicAdd(&S.gsq, wsq);
+      atomicMax(&S.gmax, wmax);
     }
   }
   uint32_t nitems;
@@ -582,10 +608,51 @@ __global__ void __launch_bounds__(BLOCK, (CAP / BLOCK > 8 ? 512 : 1024) / BLOCK)
       }
     }
   }
+  __syncthreads();
+  // Tiles of small groups only (the pairs left by long repeats, for
+  // example): each item's place is its group's start plus the number of
+  // members with a smaller partner name, or an equal one earlier in the
+  // list, which is the stable sort's order, at about (sum of squared group
+  // sizes) / items comparisons per item instead of the radix passes.
+  if constexpr (!WIDE) {
+    if (S.gmax <= RF_RANK_GMAX && S.gsq <= RF_RANK_AVG * cnt) {
+      uint32_t dst[C::ITEMS];
+#pragma unroll
+      for (int k = 0; k < C::ITEMS; ++k) {
+        const uint32_t q = k * BLOCK + tid;
+        dst[k] = 0;
+        if ((uint32_t)k < K && q < cnt) {
+          const uint32_t lgq = (uint32_t)(ent[k] >> 32) - g0;
+          const uint32_t lo = S.goff[lgq], hi = S.goff[lgq + 1];
+          // Members share the group bits, so whole keys compare as names.
+          const uint64_t kq = ((uint64_t)lgq << a.W) | r2v[k];
+          uint32_t before = 0;
+          for (uint32_t x = lo; x < hi; ++x) {
+            const uint64_t o = S.keys[x];
+            before += (o < kq || (o == kq && x < q)) ? 1u : 0u;
+          }
+          dst[k] = lo + before;
+        }
+      }
+      __syncthreads();  // every read of the input order is done
+#pragma unroll
+      for (int k = 0; k < C::ITEMS; ++k) {
+        const uint32_t q = k * BLOCK + tid;
+        if ((uint32_t)k < K && q < cnt) {
+          const uint32_t lgq = (uint32_t)(ent[k] >> 32) - g0;
+          const uint32_t e = dst[k];
+          S.keys[e + (e >> 4)] = ((uint64_t)lgq << a.W) | r2v[k];
+          S.vals[e + (e >> 5)] = (uint32_t)ent[k];
+        }
+      }
+      __syncthreads();
+      goto renamed_order;
+    }
+  }
+  {
   // Bits that vary inside the tile: OR of (key ^ first key). Every key
   // shares the first key's local group 0 bits only when ng == 1, so the
-  // reference key is the tile's first key, read after the barrier.
-  __syncthreads();
+  // reference key is the tile's first key.
   if constexpr (WIDE) {
     const uint64_t key0 = S.w.key1[0], sec0 = S.w.sec[0];
 #pragma unroll
@@ -625,6 +692,8 @@ __global__ void __launch_bounds__(BLOCK, (CAP / BLOCK > 8 ? 512 : 1024) / BLOCK)
     __syncthreads();
   }
   rf_tile_sort<BLOCK, CAP, WIDE>(S, cnt, S.orv, a.W + gbits, true);
+  }
+renamed_order:
 
   // Rename in blocked layout: items tid*K .. tid*K+K-1 of the sorted tile.
   const uint32_t l0 = tid * K;

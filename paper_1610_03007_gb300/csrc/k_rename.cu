@@ -36,7 +36,7 @@
 namespace gbsa {
 
 constexpr int RN_BLOCK = 256;
-constexpr int RN_ITEMS = 8;
+constexpr int RN_ITEMS = GBSA_RN_ITEMS;
 constexpr int RN_TILE = RN_BLOCK * RN_ITEMS;
 constexpr int RN_WARPS = RN_BLOCK / 32;
 static_assert(RN_TILE == RENAME_TILE, "tile size mismatch");
@@ -57,8 +57,9 @@ struct RnSmem {
 __device__ __forceinline__ uint32_t kidx(uint32_t e) { return e + (e >> 4); }
 __device__ __forceinline__ uint32_t vidx(uint32_t e) { return e + (e >> 5); }
 
-// 64 registers: 4 blocks of 256 threads per SM (42 KB of shared memory each).
-__global__ void __launch_bounds__(RN_BLOCK, 4) k_rename(RenameArgs a) {
+// 8 items: 64 registers, 4 blocks of 256 threads per SM (42 KB of shared
+// memory each); 4 items: 6 blocks.
+__global__ void __launch_bounds__(RN_BLOCK, RN_ITEMS <= 4 ? 6 : 4) k_rename(RenameArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   RnSmem &S = *reinterpret_cast<RnSmem *>(smem_raw);
   const int tid = threadIdx.x;

@@ -43,6 +43,10 @@ struct PackArgs {
   uint32_t *vals;          // out: N gapped positions
   DigitSpec spec;          // digits of the following radix sort
   uint32_t *hist;          // out: += their histograms (P * 256, zeroed by the caller)
+  // 1: one text whose digits hold whole characters (b divides 8, cb a
+  // multiple of 8, P = cb / 8): only the top digit is counted per key and
+  // the other histograms are derived from it (k_pack_hist_fixup).
+  uint32_t top_only;
 };
 cudaError_t launch_pack(const PackArgs &a, cudaStream_t stream);
 
@@ -109,7 +113,10 @@ struct RenameArgs {
   Ctrl *ctrl;
   uint32_t spin_limit;
 };
-constexpr int RENAME_TILE = 256 * 8;
+#ifndef GBSA_RN_ITEMS
+#define GBSA_RN_ITEMS 8
+#endif
+constexpr int RENAME_TILE = 256 * GBSA_RN_ITEMS;
 cudaError_t launch_rename(const RenameArgs &a, cudaStream_t stream);
 
 // ---- rounds >= 1: small-group refine and large-group path (k_refine.cu) --
