@@ -165,12 +165,20 @@ static_assert(OS_BLOCK == RADIX, "one thread per digit");
 // per digit thread).
 constexpr int LB_WINDOW = GBSA_LB_WINDOW;
 
+// GBSA_OS_ALIAS = 1: the per-warp peer masks live in the first 8 KB of the
+// key buffer while the tile is ranked (its keys are in registers then), so
+// a 16-key tile needs 55 KB instead of 63 and four blocks fit per SM.
+#ifndef GBSA_OS_ALIAS
+#define GBSA_OS_ALIAS 0
+#endif
+constexpr bool OS_ALIAS = GBSA_OS_ALIAS != 0;
+
 template <int OS_ITEMS>
 struct OsSmem {
   static constexpr int OS_TILE = OS_BLOCK * OS_ITEMS;
   uint64_t keys[OS_TILE];           // tile in input order, then in digit order
   uint32_t vals[OS_TILE];
-  uint32_t match[OS_WARPS][RADIX];  // per-warp peer masks (zero between uses)
+  uint32_t match[OS_ALIAS ? 1 : OS_WARPS][RADIX];  // per-warp peer masks (zero between uses)
   uint16_t whist[OS_WARPS][RADIX];  // per-warp counts, then per-warp prefixes
   uint32_t start[RADIX];            // tile-local start of each digit run
   uint32_t count[RADIX];            // the tile's count of each digit (early, by atomics)
@@ -185,7 +193,8 @@ struct OsSmem {
 // blocks per SM (~62 KB of shared memory each), 12 four, 8 five; registers
 // are capped to match.
 template <int OS_ITEMS>
-__global__ void __launch_bounds__(OS_BLOCK, OS_ITEMS >= 16 ? 3 : (OS_ITEMS >= 12 ? 4 : 5))
+__global__ void __launch_bounds__(OS_BLOCK, OS_ITEMS >= 16 ? (OS_ALIAS ? 4 : 3)
+                                                      : (OS_ITEMS >= 12 ? 4 : 5))
     k_onesweep(PassArgs a) {
   constexpr int OS_TILE = OS_BLOCK * OS_ITEMS;
   extern __shared__ __align__(128) uint8_t smem_raw[];
@@ -199,7 +208,7 @@ __global__ void __launch_bounds__(OS_BLOCK, OS_ITEMS >= 16 ? 3 : (OS_ITEMS >= 12
   }
   for (int x = tid; x < OS_WARPS * RADIX; x += OS_BLOCK) {
     (&S.whist[0][0])[x] = 0;
-    (&S.match[0][0])[x] = 0u;
+    if (!OS_ALIAS) (&S.match[0][0])[x] = 0u;
   }
   S.count[tid] = 0u;
   __syncthreads();
@@ -266,7 +275,11 @@ __global__ void __launch_bounds__(OS_BLOCK, OS_ITEMS >= 16 ? 3 : (OS_ITEMS >= 12
   // Rank within the tile: stable, by per-warp peers and counts (peers by
   // match.any on the plan's low-entropy passes, else by the masks).
   uint16_t *wh = S.whist[warp];
-  uint32_t *mt = S.match[warp];
+  uint32_t *mt = OS_ALIAS ? reinterpret_cast<uint32_t *>(S.keys) + warp * RADIX : S.match[warp];
+  if (OS_ALIAS) {  // every key was read into registers before the barrier above
+    for (int x = lane; x < RADIX; x += 32) mt[x] = 0u;
+    __syncwarp();
+  }
   const uint32_t lt = lanemask_lt();
   if ((a.plan->match_mask >> a.p) & 1u) {
 #pragma unroll
