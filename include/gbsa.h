@@ -112,6 +112,15 @@ typedef struct {
    * tuning table, else 2^22); 0xFFFFFFFF = never bucket. Same SA and ISA
    * for every value. */
   uint32_t bucket_min;
+  /* Rounds after round 0 without a host round trip per round (Algorithm 5's
+   * loop on the GPU): they run as one CUDA graph, a while-node whose body
+   * is two rounds of persistent kernels that read their sizes from a device
+   * round state, with if-nodes for the optional steps. 0 = the library
+   * chooses, 1 = device-driven, 2 = host-driven (one 64-byte readback and
+   * stream synchronisation per round). Doubling only: with multiplier 3 or
+   * 4, a name trace or profile = 1 the rounds are host-driven. Same SA and
+   * ISA either way. */
+  uint32_t device_rounds;
 } sa_options;
 
 /* Tuned build parameters (the autotuner's table, see sa_tuning_set): each

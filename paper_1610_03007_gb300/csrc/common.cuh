@@ -41,6 +41,39 @@ struct RoundCounts {
   unsigned long long large; // classify: (large groups << 32) | large items
 };
 
+// Digit positions of one sort: pass p covers key bits [shift[p], shift[p]+bits[p]).
+struct DigitSpec {
+  uint32_t P;
+  uint8_t shift[MAX_PASSES];
+  uint8_t bits[MAX_PASSES];
+};
+
+constexpr int DEV_MAX_ROUNDS = 64;  // SA_MAX_ROUNDS
+
+// Device-driven rounds (rounds >= 1 run as one CUDA graph with no host
+// round trip): the sizes the host round driver otherwise passes as kernel
+// arguments. k_round_begin writes them from the previous round's counters;
+// every kernel of a round reads them here.
+struct RoundState {
+  uint32_t m, G, mL, GL;  // active items and groups; items and groups of the large groups
+  uint32_t tiles;         // refine tiles: ceil(m / refine window)
+  uint32_t h;             // characters the current names resolve (partner offset)
+  uint32_t h_next;        // h of the next round
+  uint32_t round;         // index of the current round
+  uint32_t live;          // 0 once no suffix is active or an error was raised
+  uint32_t epoch;         // look-back epoch base of the round's launches
+  uint32_t bucket_upd;    // 1: the round's queued ISA updates are bucketed by position
+  uint32_t bucket_surv;   // 1: the large groups' ISA entries are bucketed by position
+  DigitSpec spec;         // digits of the large-group sort
+};
+
+// What one device-driven round saw (the host fills sa_stats from it).
+struct RoundRecord {
+  uint32_t m, G, mL, GL;              // inputs
+  uint32_t m_s, g_s, m_l, g_l, upd;   // outputs (RoundCounts of the round)
+  uint32_t passes;                    // radix passes the large-group sort kept
+};
+
 // Device-resident control block of one build (cleared at build start).
 struct Ctrl {
   uint32_t error;      // first DevError raised by any kernel
@@ -50,6 +83,8 @@ struct Ctrl {
   RoundCounts rc;
   uint32_t zero[4];    // constant zeros (output offsets of round 0)
   uint32_t tile_ctr[TILE_COUNTERS];  // one dynamic tile counter per launch
+  RoundState rs;                     // device-driven rounds only
+  RoundRecord rec[DEV_MAX_ROUNDS];
 };
 static_assert(sizeof(RoundCounts) == 32, "RoundCounts layout");
 
@@ -66,13 +101,6 @@ struct SortPlan {
   const uint64_t *kfinal;
   const uint32_t *vfinal;
   uint32_t match_mask;  // bit p: pass p ranks with match.any (low-entropy digit)
-};
-
-// Digit positions of one sort: pass p covers key bits [shift[p], shift[p]+bits[p]).
-struct DigitSpec {
-  uint32_t P;
-  uint8_t shift[MAX_PASSES];
-  uint8_t bits[MAX_PASSES];
 };
 
 __device__ __forceinline__ uint32_t digit_of(uint64_t key, uint32_t shift, uint32_t bits) {
@@ -129,6 +157,14 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
                "r"(bytes)
                : "memory");
+}
+
+// Orders this thread's earlier generic-proxy accesses to shared memory (and
+// those of the threads a barrier ordered before it) before its following
+// async-proxy (TMA) accesses: a bulk copy into a buffer that ordinary
+// stores wrote before.
+__device__ __forceinline__ void fence_proxy_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 // One 1-D bulk copy; dst, src 16-byte aligned, bytes a multiple of 16.

@@ -571,6 +571,341 @@ struct Build {
            8ull * upd_n;
   }
 
+  // Device-driven rounds: only for doubling (a = 2), without the per-launch
+  // profile or the per-round name trace; sa_options.device_rounds 1 asks
+  // for them, 2 refuses them, 0 leaves the choice to the library.
+  bool device_rounds_wanted() const {
+    if (mult != 2 || prof || (opt.trace_isa && opt.trace_cap > 1)) return false;
+    if (opt.device_rounds == 1) return true;
+    if (opt.device_rounds == 2) return false;
+    return false;
+  }
+
+  // Adds an if-node at the capture point of `outer` (handle h, created on
+  // the graph being captured) and starts capturing its body on `inner`.
+  static cudaError_t begin_if(cudaStream_t outer, cudaStream_t inner,
+                              cudaGraphConditionalHandle h) {
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(outer, &cst, nullptr, &g, &deps, nullptr, &nd);
+    if (e != cudaSuccess) return e;
+    if (cst != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeIf;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &p);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamUpdateCaptureDependencies(outer, &node, nullptr, 1,
+                                            cudaStreamSetCaptureDependencies);
+    if (e != cudaSuccess) return e;
+    return cudaStreamBeginCaptureToGraph(inner, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeRelaxed);
+  }
+
+  static cudaError_t end_capture(cudaStream_t s) {
+    cudaGraph_t g = nullptr;
+    return cudaStreamEndCapture(s, &g);
+  }
+
+  struct RoundHandles {
+    cudaGraphConditionalHandle sort, rename, bucket_upd, bucket_surv;
+  };
+
+  // Captures one round (active list and group tables in buffer `cur`) on
+  // stream cs, its optional steps in if-nodes captured on cs2. Grids are
+  // sized for m1 items (the most any round after round 0 can have) and
+  // capped, the kernels looping over their work.
+  cudaError_t capture_round(cudaStream_t cs, cudaStream_t cs2, int cur, const RoundHandles &hd,
+                            uint32_t m1, uint32_t W) {
+    const int nxt = cur ^ 1;
+    const uint32_t sms = (uint32_t)sm_count();
+    const RoundState *rs = &ctrl->rs;
+    RoundBeginArgs rb{};
+    rb.ctrl = ctrl;
+    rb.hist = hist;
+    rb.W = W;
+    rb.nominal = nominal;
+    rb.bucket_min = bucket_min;
+    rb.N = (uint32_t)N;
+    rb.if_sort = hd.sort;
+    rb.if_rename = hd.rename;
+    rb.if_bucket_upd = hd.bucket_upd;
+    rb.if_bucket_surv = hd.bucket_surv;
+    cudaError_t e = launch_round_begin(rb, cs);
+    if (e != cudaSuccess) return e;
+
+    // Large groups: partner names and the global radix sort.
+    if ((e = begin_if(cs, cs2, hd.sort)) != cudaSuccess) return e;
+    GatherLargeArgs ga{};
+    ga.act = act[cur];
+    ga.gstart = gstart[cur];
+    ga.lg = lg;
+    ga.loff = loff;
+    ga.mL = m1;
+    ga.W = W;
+    ga.mult = 2;
+    ga.isa = isa;
+    ga.isa_len = N + S + 1;
+    ga.keys = ka;
+    ga.vals = va;
+    ga.rs = rs;
+    ga.grid_cap = 8 * sms;
+    if ((e = launch_gather_large(ga, cs2)) != cudaSuccess) return e;
+    const DigitSpec none{};
+    if ((e = launch_digit_histogram(ka, m1, none, hist, (int)sms, cs2, rs)) != cudaSuccess) return e;
+    if ((e = launch_sort_plan(hist, dbase, none, m1, ka, kb, va, vb, plan, ctrl, cs2, rs)) !=
+        cudaSuccess)
+      return e;
+    for (int p = 0; p < MAX_PASSES; ++p) {
+      PassArgs pa{};
+      pa.plan = plan;
+      pa.p = p;
+      pa.digit_base = dbase + p * RADIX;
+      pa.m = m1;
+      pa.status = st_sort;
+      pa.epoch = (uint32_t)p;  // offset from the round's epoch base
+      pa.tile_ctr = &ctrl->tile_ctr[p];
+      pa.ctrl = ctrl;
+      pa.spin_limit = spin;
+      pa.items = sort_items;
+      pa.rs = rs;
+      pa.grid_cap = sms * (sort_items >= 16 ? 3u : (sort_items >= 12 ? 4u : 5u));
+      if ((e = launch_onesweep(pa, cs2)) != cudaSuccess) return e;
+    }
+    if ((e = end_capture(cs2)) != cudaSuccess) return e;
+
+    // Small groups: the tile-local refine.
+    RefineArgs rf{};
+    rf.act = act[cur];
+    rf.gstart = gstart[cur];
+    rf.gname = gname[cur];
+    rf.ghead = ghead[cur];
+    rf.naming = naming;
+    rf.tfirst = tfirst;
+    rf.m = m1;
+    rf.shape = shape;
+    rf.tiles = (m1 + nominal - 1) / nominal;
+    rf.W = W;
+    rf.mult = 2;
+    rf.isa = isa;
+    rf.isa_len = N + S + 1;
+    rf.N = (uint32_t)N;
+    rf.sa = sa;
+    rf.seg_off = segoff;
+    rf.S = S;
+    rf.act_out = act[nxt];
+    rf.gstart_out = gstart[nxt];
+    rf.gname_out = gname[nxt];
+    rf.ghead_out = ghead[nxt];
+    rf.upd = upd;
+    rf.ctrl = ctrl;
+    rf.rs = rs;
+    {  // two waves of the resident blocks (k_refine's launch bounds)
+      const RefineShape sh = REFINE_SHAPE[shape];
+      rf.grid_cap = 2 * sms * ((sh.cap / sh.block > 8 ? 512u : 1024u) / sh.block);
+    }
+    if ((e = launch_refine(rf, cs)) != cudaSuccess) return e;
+
+    // The large groups' rename (after every gather of the round).
+    if ((e = begin_if(cs, cs2, hd.rename)) != cudaSuccess) return e;
+    RenameArgs ra{};
+    ra.plan = plan;
+    ra.m = m1;
+    ra.W = W;
+    ra.seg_off = segoff;
+    ra.S = S;
+    ra.base_in = lbase;
+    ra.old_in = lold;
+    ra.g_in = L.max_large;
+    ra.isa = isa;
+    ra.upd = upd;
+    ra.isa_len = N + S + 1;
+    ra.N = (uint32_t)N;
+    ra.sa = sa;
+    ra.act_out = act[nxt];
+    ra.gstart_out = gstart[nxt];
+    ra.ghead_out = ghead[nxt];
+    ra.gold_out = gold;
+    ra.off_in = &ctrl->rc.m_s;
+    ra.cnt_out = &ctrl->rc.m_l;
+    ra.status = st_ren;
+    ra.epoch = MAX_PASSES;  // offset from the round's epoch base
+    ra.tile_ctr = &ctrl->tile_ctr[MAX_PASSES];
+    ra.ctrl = ctrl;
+    ra.spin_limit = spin;
+    ra.rs = rs;
+    ra.grid_cap = 4 * sms;
+    if ((e = launch_rename(ra, cs2)) != cudaSuccess) return e;
+    if ((e = end_capture(cs2)) != cudaSuccess) return e;
+
+    // The round's queued ISA updates, bucketed by position when many.
+    BucketArgs ba{};
+    const uint32_t bits = bits_for(N + S);
+    ba.shift = bits > 8 ? bits - 8 : 0;
+    ba.blocks = std::min<uint32_t>(BUCKET_BLOCKS_MAX, 4 * sms);
+    ba.counts = bcount;
+    ba.out = kb;
+    ba.in = upd;
+    ba.count = &ctrl->rc.upd;
+    ba.max_count = m1;
+    if ((e = begin_if(cs, cs2, hd.bucket_upd)) != cudaSuccess) return e;
+    if ((e = launch_bucket_count(ba, cs2)) != cudaSuccess) return e;
+    if ((e = launch_bucket_offsets(ba, cs2)) != cudaSuccess) return e;
+    if ((e = launch_bucket_scatter(ba, cs2)) != cudaSuccess) return e;
+    if ((e = end_capture(cs2)) != cudaSuccess) return e;
+    if ((e = launch_scatter_updates(upd, m1, isa, N + S + 1, ctrl, cs, kb, rs, 8 * sms)) !=
+        cudaSuccess)
+      return e;
+
+    // The new groups, and the ISA entries of the rename's survivors.
+    ClassifyArgs ca{};
+    ca.gstart = gstart[nxt];
+    ca.gname = gname[nxt];
+    ca.ghead = ghead[nxt];
+    ca.gold = gold;
+    ca.naming = naming;
+    ca.lg = lg;
+    ca.loff = loff;
+    ca.lbase = lbase;
+    ca.lold = lold;
+    ca.tfirst = tfirst;
+    ca.nominal = nominal;
+    ca.max_groups = L.max_groups;
+    ca.max_tiles = L.max_tiles;
+    ca.ctrl = ctrl;
+    ca.rs = rs;
+    if ((e = launch_classify(ca, (int)sms, cs)) != cudaSuccess) return e;
+    ba.in = act[nxt];
+    ba.lo = &ctrl->rc.m_s;
+    ba.count = &ctrl->rc.m_l;
+    if ((e = begin_if(cs, cs2, hd.bucket_surv)) != cudaSuccess) return e;
+    if ((e = launch_bucket_count(ba, cs2)) != cudaSuccess) return e;
+    if ((e = launch_bucket_offsets(ba, cs2)) != cudaSuccess) return e;
+    if ((e = launch_bucket_scatter(ba, cs2)) != cudaSuccess) return e;
+    if ((e = end_capture(cs2)) != cudaSuccess) return e;
+    return launch_apply_names(act[nxt], &ctrl->rc.m_s, &ctrl->rc.m_l, m1, gname[nxt], gold, isa,
+                              N + S + 1, cs, kb, ctrl->zero, rs, 8 * sms);
+  }
+
+  // Rounds >= 1 as one graph: while (suffixes active) { round; round }.
+  // `round` returns the number of rounds including round 0.
+  sa_status run_device_rounds(const HostCtrl &hc0, uint32_t W, uint32_t h1, int cur,
+                              uint32_t &round) {
+    const uint32_t m1 = hc0.m_next();
+    RoundState rs0{};
+    rs0.live = 1;
+    rs0.round = 0;
+    rs0.h_next = h1;
+    rs0.epoch = epoch + ROUND_EPOCHS;
+    CK(cudaMemcpyAsync(&ctrl->rs, &rs0, sizeof(rs0), cudaMemcpyHostToDevice, st));
+    // Round 0's kernels already set the attributes of the sort and rename
+    // kernels; the refine's are set when it is first captured (a host call
+    // that capture allows).
+    cudaStream_t cs = nullptr, cs2 = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    auto cleanup = [&]() {
+      if (exec) cudaGraphExecDestroy(exec);
+      if (g) cudaGraphDestroy(g);
+      if (cs2) cudaStreamDestroy(cs2);
+      if (cs) cudaStreamDestroy(cs);
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaGraphCreate(&g, 0);
+    cudaGraphConditionalHandle loop{};
+    cudaGraph_t body = nullptr;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&loop, g, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+      cudaGraphNodeParams p{};
+      p.type = cudaGraphNodeTypeConditional;
+      p.conditional.handle = loop;
+      p.conditional.type = cudaGraphCondTypeWhile;
+      p.conditional.size = 1;
+      cudaGraphNode_t node;
+      e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p);
+      if (e == cudaSuccess) body = p.conditional.phGraph_out[0];
+    }
+    RoundHandles hd[2];
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+      cudaGraphConditionalHandle *hs[4] = {&hd[k].sort, &hd[k].rename, &hd[k].bucket_upd,
+                                           &hd[k].bucket_surv};
+      for (cudaGraphConditionalHandle *hp : hs)
+        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(hp, body, 0, 0);
+    }
+    if (e == cudaSuccess)
+      e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      cudaError_t ce = capture_round(cs, cs2, cur, hd[0], m1, W);
+      if (ce == cudaSuccess) ce = capture_round(cs, cs2, cur ^ 1, hd[1], m1, W);
+      if (ce == cudaSuccess) ce = launch_round_end(ctrl, loop, cs);
+      cudaStreamCaptureStatus c2 = cudaStreamCaptureStatusNone;
+      if (cudaStreamIsCapturing(cs2, &c2) == cudaSuccess && c2 != cudaStreamCaptureStatusNone)
+        end_capture(cs2);
+      e = end_capture(cs);
+      if (ce != cudaSuccess) e = ce;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      cleanup();
+      return SA_ERR_CUDA;
+    }
+    launches += 1;  // the graph (its kernels are counted below)
+    // One readback of the whole control block (a few KB): error word, the
+    // last round's counters, the round state and the per-round records.
+    std::vector<uint8_t> raw(sizeof(Ctrl));
+    e = cudaMemcpyAsync(raw.data(), ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cleanup();
+    if (e != cudaSuccess) return SA_ERR_CUDA;
+    const Ctrl &hctrl = *reinterpret_cast<const Ctrl *>(raw.data());
+    HostCtrl hc{};
+    memcpy(&hc, raw.data(), sizeof(HostCtrl));
+    if (hc.error == ERR_TIMEOUT) return SA_ERR_TIMEOUT;
+    if (hc.error != ERR_NONE) return SA_ERR_INTERNAL;
+    // Statistics and byte counts from the device records.
+    const uint32_t last = hctrl.rs.round;
+    if (last >= (uint32_t)DEV_MAX_ROUNDS) return SA_ERR_INTERNAL;
+    std::vector<RoundRecord> rec(hctrl.rec, hctrl.rec + last + 1);
+    if (last >= 1) {  // the last round's outputs are still in the counters
+      RoundRecord &r = rec[last];
+      r.m_s = hc.m_s;
+      r.g_s = hc.g_s;
+      r.m_l = hc.m_l;
+      r.g_l = hc.g_l;
+      r.upd = hc.upd;
+      r.passes = hc.passes;
+    }
+    for (uint32_t r = 1; r <= last; ++r) {
+      const RoundRecord &x = rec[r];
+      const uint32_t kbits = x.mL ? W + (x.GL > 1 ? bits_for(x.GL - 1) : 0) : 0;
+      const uint64_t rbl = x.mL ? rename_bytes(x.mL, x.m_l, x.g_l) : 0;
+      const uint64_t rfb = refine_bytes(x.m - x.mL, x.G - x.GL, x.m_s, x.g_s, x.upd, 2);
+      bytes += (x.mL ? (uint64_t)x.passes * 24 * x.mL + 32ull * x.mL : 0) + rbl + rfb + 8ull * x.G +
+               12ull * x.upd + (x.m >= bucket_min ? 24ull * x.upd : 0) +
+               (x.mL ? 12ull * x.m_l + (x.mL >= bucket_min ? 24ull * x.m_l : 0) : 0);
+      launches += 5 + (x.mL ? 12 + MAX_PASSES - 1 : 0) + (x.m >= bucket_min ? 3 : 0) +
+                  (x.mL && x.mL >= bucket_min ? 3 : 0);
+      if (stats && r < SA_MAX_ROUNDS) {
+        stats->active[r] = x.m;
+        stats->unique[r] = x.m - (x.m_s + x.m_l);
+        stats->passes[r] = x.mL ? x.passes : 0;
+        stats->key_bits[r] = kbits;
+        stats->groups[r] = x.g_s + x.g_l;
+      }
+    }
+    launches += (last + 1) / 2;  // k_round_end, once per body
+    round = last + 1;
+    return SA_OK;
+  }
+
   void record(uint32_t r, uint32_t m, const HostCtrl &hc, uint32_t kbits) {
     if (!stats || r >= SA_MAX_ROUNDS) return;
     stats->active[r] = m;
@@ -711,6 +1046,13 @@ struct Build {
     const uint32_t W = bits_for(N);  // r2 in [0, N]
     uint64_t h = c0;
     uint32_t round = 1;
+    if (hc.m_next() > 0 && device_rounds_wanted()) {
+      // The whole loop as one graph launch; rounds, statistics and byte
+      // counts come back from the device records.
+      s = run_device_rounds(hc, W, (uint32_t)c0, cur, round);
+      if (s != SA_OK) return s;
+      hc = HostCtrl{};  // no suffix left active
+    }
     while (hc.m_next() > 0) {
       if (round >= SA_MAX_ROUNDS || h > N) return SA_ERR_INTERNAL;
       m = hc.m_next();

@@ -55,6 +55,7 @@ __device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t *a, uint32_t 
 }
 
 __global__ void __launch_bounds__(256) k_classify(ClassifyArgs a) {
+  if (a.rs && !a.rs->live) return;
   const uint32_t m = a.ctrl->rc.m_s + a.ctrl->rc.m_l;
   const uint32_t gs = a.ctrl->rc.g_s;
   const uint32_t G = gs + a.ctrl->rc.g_l;
@@ -109,12 +110,26 @@ cudaError_t launch_classify(const ClassifyArgs &a, int num_sms, cudaStream_t str
 
 // ---- large groups: keys for the global radix sort ---------------------------
 
+__device__ __forceinline__ void gather_large_item(const GatherLargeArgs &a, const uint32_t j,
+                                                  const uint32_t GL, const uint32_t h);
+
 __global__ void __launch_bounds__(256) k_gather_large(GatherLargeArgs a) {
-  const uint64_t j64 = (uint64_t)blockIdx.x * 256 + threadIdx.x;
-  if (j64 >= a.mL) return;
-  const uint32_t j = (uint32_t)j64;
+  uint32_t mL = a.mL, GL = a.GL, h = a.h;
+  if (a.rs) {  // device-driven rounds
+    if (!a.rs->live) return;
+    mL = a.rs->mL;
+    GL = a.rs->GL;
+    h = a.rs->h;
+  }
+  for (uint64_t j64 = (uint64_t)blockIdx.x * 256 + threadIdx.x; j64 < mL;
+       j64 += (uint64_t)gridDim.x * 256)
+    gather_large_item(a, (uint32_t)j64, GL, h);
+}
+
+__device__ __forceinline__ void gather_large_item(const GatherLargeArgs &a, const uint32_t j,
+                                                  const uint32_t GL, const uint32_t h) {
   // k = the large group holding item j: the last k with loff[k] <= j
-  uint32_t lo = 0, hi = a.GL - 1;
+  uint32_t lo = 0, hi = GL - 1;
   while (lo < hi) {
     const uint32_t mid = (lo + hi + 1) >> 1;
     if (__ldg(a.loff + mid) <= j)
@@ -125,7 +140,7 @@ __global__ void __launch_bounds__(256) k_gather_large(GatherLargeArgs a) {
   const uint32_t g = __ldg(a.lg + lo);
   const uint64_t e = a.act[__ldg(a.gstart + g) + (j - __ldg(a.loff + lo))];
   const uint32_t ip = (uint32_t)e;
-  const uint64_t at = min((uint64_t)ip + a.h, a.isa_len - 1);
+  const uint64_t at = min((uint64_t)ip + h, a.isa_len - 1);
   const uint32_t r2 = __ldg(a.isa + at) + 1u;
   const uint64_t key1 = ((uint64_t)lo << a.W) | r2;
   if (a.mult == 2) {
@@ -135,9 +150,9 @@ __global__ void __launch_bounds__(256) k_gather_large(GatherLargeArgs a) {
   }
   // a-tuples: the later partners are sorted first (keys), item j rides
   // along; (group, r2) and the later partners are kept by item.
-  const uint32_t r3 = r2 ? __ldg(a.isa + min((uint64_t)ip + (uint64_t)2 * a.h, a.isa_len - 1)) + 1u : 0u;
+  const uint32_t r3 = r2 ? __ldg(a.isa + min((uint64_t)ip + (uint64_t)2 * h, a.isa_len - 1)) + 1u : 0u;
   uint32_t r4 = 0;
-  if (a.mult == 4 && r3) r4 = __ldg(a.isa + min((uint64_t)ip + (uint64_t)3 * a.h, a.isa_len - 1)) + 1u;
+  if (a.mult == 4 && r3) r4 = __ldg(a.isa + min((uint64_t)ip + (uint64_t)3 * h, a.isa_len - 1)) + 1u;
   const uint64_t sec = a.mult == 4 ? (((uint64_t)r3 << a.W) | r4) : (uint64_t)r3;
   a.keys[j] = sec;
   a.vals[j] = j;
@@ -147,7 +162,9 @@ __global__ void __launch_bounds__(256) k_gather_large(GatherLargeArgs a) {
 
 cudaError_t launch_gather_large(const GatherLargeArgs &a, cudaStream_t stream) {
   if (a.mL == 0) return cudaSuccess;
-  k_gather_large<<<(unsigned)(((uint64_t)a.mL + 255) / 256), 256, 0, stream>>>(a);
+  uint64_t grid = ((uint64_t)a.mL + 255) / 256;
+  if (a.grid_cap && grid > a.grid_cap) grid = a.grid_cap;
+  k_gather_large<<<(unsigned)grid, 256, 0, stream>>>(a);
   return cudaGetLastError();
 }
 
@@ -448,15 +465,12 @@ __device__ void rf_tile_sort(RfSmem<BLOCK, CAP, WIDE> &S, uint32_t cnt,
   }
 }
 
-// Up to 8 slots per thread: 64 registers (4 blocks of 256 or 8 of 128 per
-// SM); 16 slots: 128 registers (such tiles fit 2 blocks per SM anyway).
+// One refine tile (whole groups whose starts fall in the tile's window).
+// Every thread of the block calls it; all returns are block-uniform.
 template <int BLOCK, int CAP, bool WIDE>
-__global__ void __launch_bounds__(BLOCK, (CAP / BLOCK > 8 ? 512 : 1024) / BLOCK)
-    k_refine(RefineArgs a) {
+__device__ __forceinline__ void refine_tile(RfSmem<BLOCK, CAP, WIDE> &S, const RefineArgs &a,
+                                            const uint32_t tile, const uint32_t h) {
   using C = RfCfg<BLOCK, CAP>;
-  using Sm = RfSmem<BLOCK, CAP, WIDE>;
-  extern __shared__ __align__(128) uint8_t smem_raw[];
-  Sm &S = *reinterpret_cast<Sm *>(smem_raw);
   const int tid = threadIdx.x;
   if (tid == 0) {
     S.orv = 0ull;
@@ -468,7 +482,6 @@ __global__ void __launch_bounds__(BLOCK, (CAP / BLOCK > 8 ? 512 : 1024) / BLOCK)
   }
   __syncthreads();
   if (S.flag) return;
-  const uint32_t tile = blockIdx.x;
   const uint32_t g0 = __ldg(a.tfirst + tile), g1 = __ldg(a.tfirst + tile + 1);
   const uint32_t ng = g1 - g0;
   if (ng > (uint32_t)C::MAXG) {  // never taken unless a logic error
@@ -562,7 +575,7 @@ __global__ void __launch_bounds__(BLOCK, (CAP / BLOCK > 8 ? 512 : 1024) / BLOCK)
     const uint32_t q = k * BLOCK + tid;
     r2v[k] = 0;
     if ((uint32_t)k < K && q < cnt) {
-      const uint64_t at = min((uint64_t)(uint32_t)ent[k] + a.h, a.isa_len - 1);
+      const uint64_t at = min((uint64_t)(uint32_t)ent[k] + h, a.isa_len - 1);
       r2v[k] = __ldg(a.isa + at) + 1u;
     }
   }
@@ -578,8 +591,8 @@ __global__ void __launch_bounds__(BLOCK, (CAP / BLOCK > 8 ? 512 : 1024) / BLOCK)
       r3v[k] = r4v[k] = 0;
       if ((uint32_t)k < K && q < cnt) {
         const uint64_t ip = (uint32_t)ent[k];
-        r3v[k] = __ldg(a.isa + min(ip + (uint64_t)2 * a.h, a.isa_len - 1)) + 1u;
-        if (a.mult == 4) r4v[k] = __ldg(a.isa + min(ip + (uint64_t)3 * a.h, a.isa_len - 1)) + 1u;
+        r3v[k] = __ldg(a.isa + min(ip + (uint64_t)2 * h, a.isa_len - 1)) + 1u;
+        if (a.mult == 4) r4v[k] = __ldg(a.isa + min(ip + (uint64_t)3 * h, a.isa_len - 1)) + 1u;
       }
     }
 #pragma unroll
@@ -829,13 +842,37 @@ renamed_order:
   }
 }
 
+// Up to 8 slots per thread: 64 registers (4 blocks of 256 or 8 of 128 per
+// SM); 16 slots: 128 registers (such tiles fit 2 blocks per SM anyway).
+// Blocks take tiles blockIdx.x, + gridDim.x, ... (tiles share nothing, so
+// any grid works); in device-driven rounds the tile count and h come from
+// the round state.
+template <int BLOCK, int CAP, bool WIDE>
+__global__ void __launch_bounds__(BLOCK, (CAP / BLOCK > 8 ? 512 : 1024) / BLOCK)
+    k_refine(RefineArgs a) {
+  using Sm = RfSmem<BLOCK, CAP, WIDE>;
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  Sm &S = *reinterpret_cast<Sm *>(smem_raw);
+  uint32_t tiles = a.tiles, h = a.h;
+  if (a.rs) {
+    if (!a.rs->live) return;
+    tiles = a.rs->tiles;
+    h = a.rs->h;
+  }
+  for (uint32_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    refine_tile<BLOCK, CAP, WIDE>(S, a, tile, h);
+    __syncthreads();  // the next tile reuses the shared buffers
+  }
+}
+
 template <int BLOCK, int CAP, bool WIDE>
 cudaError_t launch_refine_t(const RefineArgs &a, cudaStream_t stream) {
   const int smem = (int)sizeof(RfSmem<BLOCK, CAP, WIDE>);
   cudaError_t e = ensure_smem_attributes(
       reinterpret_cast<const void *>(&k_refine<BLOCK, CAP, WIDE>), smem, true);
   if (e != cudaSuccess) return e;
-  k_refine<BLOCK, CAP, WIDE><<<a.tiles, BLOCK, smem, stream>>>(a);
+  const uint32_t grid = a.grid_cap && a.tiles > a.grid_cap ? a.grid_cap : a.tiles;
+  k_refine<BLOCK, CAP, WIDE><<<grid, BLOCK, smem, stream>>>(a);
   return cudaGetLastError();
 }
 
@@ -865,62 +902,91 @@ cudaError_t launch_refine(const RefineArgs &a, cudaStream_t stream) {
 constexpr int WB_ITEMS = 8;
 constexpr int WB_CHUNK = 256 * WB_ITEMS;
 
+// Blocks take chunks blockIdx.x, + gridDim.x, ...; with one block per chunk
+// they start in chunk order. In device-driven rounds (rs) the kernels read
+// from the position-bucketed copy when the round state says the round
+// bucketed its entries.
 __global__ void __launch_bounds__(256) k_apply_names(const uint64_t *__restrict__ act,
                                                     const uint32_t *lo_p, const uint32_t *count_p,
                                                     const uint32_t *__restrict__ gname,
                                                     const uint32_t *__restrict__ gold,
-                                                    uint32_t *isa, uint64_t isa_len) {
-  const uint64_t lo = *lo_p, n = *count_p;
-  const uint64_t c0 = (uint64_t)blockIdx.x * WB_CHUNK;
-  if (c0 >= n) return;
-  uint64_t e[WB_ITEMS];
-#pragma unroll
-  for (int k = 0; k < WB_ITEMS; ++k) {
-    const uint64_t x = c0 + (uint64_t)k * 256 + threadIdx.x;
-    e[k] = x < n ? act[lo + x] : ~0ull;
+                                                    uint32_t *isa, uint64_t isa_len,
+                                                    const uint64_t *__restrict__ bucketed,
+                                                    const uint32_t *zero, const RoundState *rs) {
+  if (rs) {
+    if (!rs->live || rs->mL == 0) return;
+    if (rs->bucket_surv) {
+      act = bucketed;
+      lo_p = zero;
+    }
   }
+  const uint64_t lo = *lo_p, n = *count_p;
+  for (uint64_t c0 = (uint64_t)blockIdx.x * WB_CHUNK; c0 < n;
+       c0 += (uint64_t)gridDim.x * WB_CHUNK) {
+    uint64_t e[WB_ITEMS];
 #pragma unroll
-  for (int k = 0; k < WB_ITEMS; ++k) {
-    if (e[k] == ~0ull) continue;
-    const uint32_t g = (uint32_t)(e[k] >> 32), ip = (uint32_t)e[k];
-    const uint32_t name = __ldg(gname + g);
-    if (name != __ldg(gold + g) && ip < isa_len) isa[ip] = name;
+    for (int k = 0; k < WB_ITEMS; ++k) {
+      const uint64_t x = c0 + (uint64_t)k * 256 + threadIdx.x;
+      e[k] = x < n ? act[lo + x] : ~0ull;
+    }
+#pragma unroll
+    for (int k = 0; k < WB_ITEMS; ++k) {
+      if (e[k] == ~0ull) continue;
+      const uint32_t g = (uint32_t)(e[k] >> 32), ip = (uint32_t)e[k];
+      const uint32_t name = __ldg(gname + g);
+      if (name != __ldg(gold + g) && ip < isa_len) isa[ip] = name;
+    }
   }
 }
 
 cudaError_t launch_apply_names(const uint64_t *act, const uint32_t *lo, const uint32_t *count,
                                uint32_t max_count, const uint32_t *gname, const uint32_t *gold,
-                               uint32_t *isa, uint64_t isa_len, cudaStream_t stream) {
-  const uint64_t blocks = ((uint64_t)max_count + WB_CHUNK - 1) / WB_CHUNK;
+                               uint32_t *isa, uint64_t isa_len, cudaStream_t stream,
+                               const uint64_t *bucketed, const uint32_t *zero,
+                               const RoundState *rs, uint32_t grid_cap) {
+  uint64_t blocks = ((uint64_t)max_count + WB_CHUNK - 1) / WB_CHUNK;
   if (blocks == 0) return cudaSuccess;
-  k_apply_names<<<(unsigned)blocks, 256, 0, stream>>>(act, lo, count, gname, gold, isa, isa_len);
+  if (grid_cap && blocks > grid_cap) blocks = grid_cap;
+  k_apply_names<<<(unsigned)blocks, 256, 0, stream>>>(act, lo, count, gname, gold, isa, isa_len,
+                                                      bucketed, zero, rs);
   return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(256) k_scatter_updates(const uint64_t *__restrict__ upd,
                                                         uint32_t max_upd, uint32_t *isa,
-                                                        uint64_t isa_len, Ctrl *ctrl) {
-  const uint64_t n = min(ctrl->rc.upd, max_upd);
-  const uint64_t c0 = (uint64_t)blockIdx.x * WB_CHUNK;
-  if (c0 >= n) return;
-  uint64_t u[WB_ITEMS];
-#pragma unroll
-  for (int k = 0; k < WB_ITEMS; ++k) {
-    const uint64_t x = c0 + (uint64_t)k * 256 + threadIdx.x;
-    u[k] = x < n ? upd[x] : ~0ull;
+                                                        uint64_t isa_len, Ctrl *ctrl,
+                                                        const uint64_t *__restrict__ bucketed,
+                                                        const RoundState *rs) {
+  if (rs) {
+    if (!rs->live) return;
+    if (rs->bucket_upd) upd = bucketed;
   }
+  const uint64_t n = min(ctrl->rc.upd, max_upd);
+  for (uint64_t c0 = (uint64_t)blockIdx.x * WB_CHUNK; c0 < n;
+       c0 += (uint64_t)gridDim.x * WB_CHUNK) {
+    uint64_t u[WB_ITEMS];
 #pragma unroll
-  for (int k = 0; k < WB_ITEMS; ++k) {
-    const uint32_t ip = (uint32_t)u[k];
-    if (u[k] != ~0ull && ip < isa_len) isa[ip] = (uint32_t)(u[k] >> 32);
+    for (int k = 0; k < WB_ITEMS; ++k) {
+      const uint64_t x = c0 + (uint64_t)k * 256 + threadIdx.x;
+      u[k] = x < n ? upd[x] : ~0ull;
+    }
+#pragma unroll
+    for (int k = 0; k < WB_ITEMS; ++k) {
+      const uint32_t ip = (uint32_t)u[k];
+      if (u[k] != ~0ull && ip < isa_len) isa[ip] = (uint32_t)(u[k] >> 32);
+    }
   }
 }
 
 cudaError_t launch_scatter_updates(const uint64_t *upd, uint32_t max_upd, uint32_t *isa,
-                                   uint64_t isa_len, Ctrl *ctrl, cudaStream_t stream) {
-  const uint64_t blocks = ((uint64_t)max_upd + WB_CHUNK - 1) / WB_CHUNK;
+                                   uint64_t isa_len, Ctrl *ctrl, cudaStream_t stream,
+                                   const uint64_t *bucketed, const RoundState *rs,
+                                   uint32_t grid_cap) {
+  uint64_t blocks = ((uint64_t)max_upd + WB_CHUNK - 1) / WB_CHUNK;
   if (blocks == 0) return cudaSuccess;
-  k_scatter_updates<<<(unsigned)blocks, 256, 0, stream>>>(upd, max_upd, isa, isa_len, ctrl);
+  if (grid_cap && blocks > grid_cap) blocks = grid_cap;
+  k_scatter_updates<<<(unsigned)blocks, 256, 0, stream>>>(upd, max_upd, isa, isa_len, ctrl,
+                                                          bucketed, rs);
   return cudaGetLastError();
 }
 

@@ -57,24 +57,16 @@ struct RnSmem {
 __device__ __forceinline__ uint32_t kidx(uint32_t e) { return e + (e >> 4); }
 __device__ __forceinline__ uint32_t vidx(uint32_t e) { return e + (e >> 5); }
 
-// 8 items: 64 registers, 4 blocks of 256 threads per SM (42 KB of shared
-// memory each); 4 items: 6 blocks.
-__global__ void __launch_bounds__(RN_BLOCK, RN_ITEMS <= 4 ? 6 : 4) k_rename(RenameArgs a) {
-  extern __shared__ __align__(16) uint8_t smem_raw[];
-  RnSmem &S = *reinterpret_cast<RnSmem *>(smem_raw);
+// One rename tile; every thread of the block calls it. Returns false when
+// the block must stop (a wait gave up). m, g_in and epoch as in the kernel.
+__device__ __forceinline__ bool rename_tile(RnSmem &S, const RenameArgs &a, const uint32_t tile,
+                                            const uint32_t m, const uint32_t g_in,
+                                            const uint32_t epoch) {
   const int tid = threadIdx.x;
-  if (tid == 0) {
-    S.tile = atomicAdd(a.tile_ctr, 1u);
-    S.bail = has_error(a.ctrl) ? 1u : 0u;
-    S.upd_local = 0u;
-  }
-  __syncthreads();
-  if (S.bail) return;
-  const uint32_t tile = S.tile;
   const uint64_t *__restrict__ K = a.plan->kfinal;
   const uint32_t *__restrict__ V = a.plan->vfinal;
   const uint32_t base = tile * RN_TILE;
-  const uint32_t count = min((uint32_t)RN_TILE, a.m - base);
+  const uint32_t count = min((uint32_t)RN_TILE, m - base);
 
   // Coalesced load of the tile plus one item of halo on each side.
   for (int k = 0; k < RN_ITEMS; ++k) {
@@ -87,7 +79,7 @@ __global__ void __launch_bounds__(RN_BLOCK, RN_ITEMS <= 4 ? 6 : 4) k_rename(Rena
   if (tid == 0) {
     S.prev_key = base > 0 ? K[base - 1] : 0ull;
     S.prev_val = base > 0 ? V[base - 1] : 0u;
-    const bool has_next = base + count < a.m;
+    const bool has_next = base + count < m;
     S.next_key = has_next ? K[base + count] : 0ull;
     S.next_val = has_next ? V[base + count] : 0u;
   }
@@ -133,8 +125,8 @@ __global__ void __launch_bounds__(RN_BLOCK, RN_ITEMS <= 4 ? 6 : 4) k_rename(Rena
 #pragma unroll
   for (int k = 0; k <= RN_ITEMS; ++k) {
     const uint64_t j = (uint64_t)base + l0 + k;
-    bool b = (j == 0) || (j >= a.m) || key[k + 1] != key[k];
-    if (a.round0 && j > 0 && j < a.m) b = b || is_tail[k + 1] || is_tail[k];
+    bool b = (j == 0) || (j >= m) || key[k + 1] != key[k];
+    if (a.round0 && j > 0 && j < m) b = b || is_tail[k + 1] || is_tail[k];
     if (SEC && !b) b = SEC[j] != SEC[j - 1];
     f[k] = b;
   }
@@ -168,25 +160,25 @@ __global__ void __launch_bounds__(RN_BLOCK, RN_ITEMS <= 4 ? 6 : 4) k_rename(Rena
     uint32_t carry = 0;
     bool ok = true;
     if (tile == 0) {
-      status_store(st, status_word(a.epoch, ST_INC, agg));
+      status_store(st, status_word(epoch, ST_INC, agg));
     } else {
-      status_store(st, status_word(a.epoch, ST_AGG, agg));
+      status_store(st, status_word(epoch, ST_AGG, agg));
       if (which == 0)
-        ok = look_back4(a.status, 3, which, tile, a.epoch, OpMax(), carry, a.ctrl, a.spin_limit);
+        ok = look_back4(a.status, 3, which, tile, epoch, OpMax(), carry, a.ctrl, a.spin_limit);
       else
-        ok = look_back4(a.status, 3, which, tile, a.epoch, OpAdd(), carry, a.ctrl, a.spin_limit);
+        ok = look_back4(a.status, 3, which, tile, epoch, OpAdd(), carry, a.ctrl, a.spin_limit);
       if (ok) {
         const uint32_t inc = which == 0 ? (carry > agg ? carry : agg) : carry + agg;
-        status_store(st, status_word(a.epoch, ST_INC, inc));
+        status_store(st, status_word(epoch, ST_INC, inc));
       }
     }
     if (!ok) S.bail = 1;
     S.carry[which] = carry;
   }
   __syncthreads();
-  if (S.bail) return;
+  if (S.bail) return false;
   if (tid == 0) {
-    if (base + count == a.m) {
+    if (base + count == m) {
       a.cnt_out[0] = S.carry[1] + tot_surv;
       a.cnt_out[1] = S.carry[2] + tot_hs;
     }
@@ -216,7 +208,7 @@ __global__ void __launch_bounds__(RN_BLOCK, RN_ITEMS <= 4 ? 6 : 4) k_rename(Rena
       const uint64_t kk = key[k + 1];
       const uint32_t ip = val[k + 1];
       const uint32_t g = a.round0 ? 0u : (uint32_t)(kk >> a.W);
-      if (!a.round0 && g >= a.g_in) {  // never taken unless a logic error
+      if (!a.round0 && g >= g_in) {  // never taken unless a logic error
         raise_error(a.ctrl, ERR_INTERNAL, 4);
         continue;
       }
@@ -266,6 +258,38 @@ __global__ void __launch_bounds__(RN_BLOCK, RN_ITEMS <= 4 ? 6 : 4) k_rename(Rena
       if (v != NO_NAME) a.sa[base + e] = v;
     }
   }
+  return true;
+}
+
+// 8 items: 64 registers, 4 blocks of 256 threads per SM (42 KB of shared
+// memory each); 4 items: 6 blocks. Tiles are taken from the launch's
+// counter until it passes the last one, so any grid works (a grid smaller
+// than the tile count makes the blocks persistent); in device-driven
+// rounds the item and group counts and the epoch base come from the round
+// state.
+__global__ void __launch_bounds__(RN_BLOCK, RN_ITEMS <= 4 ? 6 : 4) k_rename(RenameArgs a) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  RnSmem &S = *reinterpret_cast<RnSmem *>(smem_raw);
+  uint32_t m = a.m, g_in = a.g_in, epoch = a.epoch;
+  if (a.rs) {
+    if (!a.rs->live) return;
+    m = a.rs->mL;
+    g_in = a.rs->GL;
+    epoch = a.rs->epoch + a.epoch;
+  }
+  const uint32_t tiles = (uint32_t)(((uint64_t)m + RN_TILE - 1) / RN_TILE);
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) {
+      S.tile = atomicAdd(a.tile_ctr, 1u);
+      S.bail = has_error(a.ctrl) ? 1u : 0u;
+      S.upd_local = 0u;
+    }
+    __syncthreads();
+    if (S.bail || S.tile >= tiles) return;
+    if (!rename_tile(S, a, S.tile, m, g_in, epoch)) return;
+    __syncthreads();  // the next tile reuses the shared buffers
+  }
 }
 
 cudaError_t launch_rename(const RenameArgs &a, cudaStream_t stream) {
@@ -273,8 +297,9 @@ cudaError_t launch_rename(const RenameArgs &a, cudaStream_t stream) {
   const int smem = (int)sizeof(RnSmem);
   cudaError_t e = ensure_smem_attributes(reinterpret_cast<const void *>(&k_rename), smem, false);
   if (e != cudaSuccess) return e;
-  const uint32_t tiles = (a.m + RN_TILE - 1) / RN_TILE;
-  k_rename<<<tiles, RN_BLOCK, smem, stream>>>(a);
+  uint32_t grid = (a.m + RN_TILE - 1) / RN_TILE;
+  if (a.grid_cap && grid > a.grid_cap) grid = a.grid_cap;
+  k_rename<<<grid, RN_BLOCK, smem, stream>>>(a);
   return cudaGetLastError();
 }
 

@@ -29,8 +29,13 @@ constexpr int DH_BLOCK = 256;
 
 __global__ void __launch_bounds__(DH_BLOCK)
 k_digit_histogram(const uint64_t *__restrict__ keys, uint32_t m, DigitSpec spec,
-                  uint32_t *__restrict__ hist) {
+                  uint32_t *__restrict__ hist, const RoundState *rs) {
   __shared__ uint32_t s_hist[MAX_PASSES][RADIX];
+  if (rs) {  // device-driven rounds: the large groups' items and digits
+    if (!rs->live) return;
+    m = rs->mL;
+    spec = rs->spec;
+  }
   for (int x = threadIdx.x; x < MAX_PASSES * RADIX; x += DH_BLOCK) (&s_hist[0][0])[x] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -63,12 +68,13 @@ k_digit_histogram(const uint64_t *__restrict__ keys, uint32_t m, DigitSpec spec,
 }
 
 cudaError_t launch_digit_histogram(const uint64_t *keys, uint32_t m, const DigitSpec &spec,
-                                   uint32_t *hist, int num_sms, cudaStream_t stream) {
-  if (m == 0 || spec.P == 0) return cudaSuccess;
+                                   uint32_t *hist, int num_sms, cudaStream_t stream,
+                                   const RoundState *rs) {
+  if (m == 0 || (spec.P == 0 && !rs)) return cudaSuccess;
   uint64_t want = ((uint64_t)m + DH_BLOCK - 1) / DH_BLOCK;
   uint64_t cap = (uint64_t)num_sms * 8;
   unsigned grid = (unsigned)(want > cap ? cap : want);
-  k_digit_histogram<<<grid, DH_BLOCK, 0, stream>>>(keys, m, spec, hist);
+  k_digit_histogram<<<grid, DH_BLOCK, 0, stream>>>(keys, m, spec, hist, rs);
   return cudaGetLastError();
 }
 
@@ -82,8 +88,13 @@ constexpr float MATCH_RANK_MAX_DISTINCT = 24.f;
 __global__ void __launch_bounds__(RADIX)
 k_sort_plan(const uint32_t *__restrict__ hist, uint32_t *__restrict__ digit_base, DigitSpec spec,
             uint32_t m, uint64_t *ka, uint64_t *kb, uint32_t *va, uint32_t *vb,
-            SortPlan *plan, Ctrl *ctrl) {
+            SortPlan *plan, Ctrl *ctrl, const RoundState *rs) {
   __shared__ uint32_t s_tmp[RADIX / 32 + 1];
+  if (rs) {  // device-driven rounds
+    if (!rs->live) return;
+    m = rs->mL;
+    spec = rs->spec;
+  }
   __shared__ uint32_t s_active[MAX_PASSES];
   __shared__ float s_e[RADIX / 32];
   __shared__ uint32_t s_match;
@@ -148,8 +159,9 @@ k_sort_plan(const uint32_t *__restrict__ hist, uint32_t *__restrict__ digit_base
 
 cudaError_t launch_sort_plan(const uint32_t *hist, uint32_t *digit_base, const DigitSpec &spec,
                              uint32_t m, uint64_t *ka, uint64_t *kb, uint32_t *va,
-                             uint32_t *vb, SortPlan *plan, Ctrl *ctrl, cudaStream_t stream) {
-  k_sort_plan<<<1, RADIX, 0, stream>>>(hist, digit_base, spec, m, ka, kb, va, vb, plan, ctrl);
+                             uint32_t *vb, SortPlan *plan, Ctrl *ctrl, cudaStream_t stream,
+                             const RoundState *rs) {
+  k_sort_plan<<<1, RADIX, 0, stream>>>(hist, digit_base, spec, m, ka, kb, va, vb, plan, ctrl, rs);
   return cudaGetLastError();
 }
 
@@ -200,161 +212,182 @@ __global__ void __launch_bounds__(OS_BLOCK, OS_ITEMS >= 16 ? (OS_ALIAS ? 4 : 3)
   extern __shared__ __align__(128) uint8_t smem_raw[];
   OsSmem<OS_ITEMS> &S = *reinterpret_cast<OsSmem<OS_ITEMS> *>(smem_raw);
   if (!a.plan->active[a.p]) return;
+  // Sizes and digit: from the arguments, or in device-driven rounds from
+  // the round state (the pass's launch epoch is then an offset).
+  uint32_t m = a.m, shift = a.shift, bits = a.bits, epoch = a.epoch;
+  if (a.rs) {
+    if (!a.rs->live) return;
+    m = a.rs->mL;
+    shift = a.rs->spec.shift[a.p];
+    bits = a.rs->spec.bits[a.p];
+    epoch = a.rs->epoch + a.epoch;
+  }
+  const uint32_t tiles = (uint32_t)(((uint64_t)m + OS_TILE - 1) / OS_TILE);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) {
-    S.tile = atomicAdd(a.tile_ctr, 1u);
-    S.bail = has_error(a.ctrl) ? 1u : 0u;
-    mbar_init(&S.bar, 1);
-  }
-  for (int x = tid; x < OS_WARPS * RADIX; x += OS_BLOCK) {
-    (&S.whist[0][0])[x] = 0;
-    if (!OS_ALIAS) (&S.match[0][0])[x] = 0u;
-  }
-  S.count[tid] = 0u;
-  __syncthreads();
-  if (S.bail) return;
-  const uint32_t tile = S.tile;
+  if (tid == 0) mbar_init(&S.bar, 1);
   const uint64_t *__restrict__ ksrc = a.plan->ksrc[a.p];
   const uint32_t *__restrict__ vsrc = a.plan->vsrc[a.p];
   uint64_t *__restrict__ kdst = a.plan->kdst[a.p];
   uint32_t *__restrict__ vdst = a.plan->vdst[a.p];
-  const uint64_t base = (uint64_t)tile * OS_TILE;
-  const uint32_t count = (uint32_t)min((uint64_t)OS_TILE, (uint64_t)a.m - base);
+  const uint32_t dmax = (1u << bits) - 1u;
+  uint32_t phase = 0;  // parity of the tile-load barrier's next phase
+  // Tiles are taken from the launch's counter until it passes the last one
+  // (a grid smaller than the tile count makes the blocks persistent).
+  for (;;) {
+    if (tid == 0) {
+      S.tile = atomicAdd(a.tile_ctr, 1u);
+      S.bail = has_error(a.ctrl) ? 1u : 0u;
+    }
+    for (int x = tid; x < OS_WARPS * RADIX; x += OS_BLOCK) {
+      (&S.whist[0][0])[x] = 0;
+      if (!OS_ALIAS) (&S.match[0][0])[x] = 0u;
+    }
+    S.count[tid] = 0u;
+    __syncthreads();
+    if (S.bail || S.tile >= tiles) return;
+    const uint32_t tile = S.tile;
+    const uint64_t base = (uint64_t)tile * OS_TILE;
+    const uint32_t count = (uint32_t)min((uint64_t)OS_TILE, (uint64_t)m - base);
 
-  // Load the tile: one bulk copy each for keys and values (TMA, 16-byte
-  // granules), plain loads for a ragged remainder or unaligned arrays.
-  const uint64_t *kp = ksrc + base;
-  const uint32_t *vp = vsrc + base;
-  const bool aligned = ((((uintptr_t)kp) | ((uintptr_t)vp)) & 15u) == 0;
-  const uint32_t kbytes = aligned ? (count * 8u) & ~15u : 0u;
-  const uint32_t vbytes = aligned ? (count * 4u) & ~15u : 0u;
-  if (tid == 0 && (kbytes | vbytes)) {
-    mbar_expect_tx(&S.bar, kbytes + vbytes);
-    if (kbytes) bulk_g2s(S.keys, kp, kbytes, &S.bar);
-    if (vbytes) bulk_g2s(S.vals, vp, vbytes, &S.bar);
-  }
-  for (uint32_t e = kbytes / 8u + tid; e < count; e += OS_BLOCK) S.keys[e] = kp[e];
-  for (uint32_t e = vbytes / 4u + tid; e < count; e += OS_BLOCK) S.vals[e] = vp[e];
-  if (kbytes | vbytes) {
-    if (!mbar_wait_bounded(&S.bar, 0, a.ctrl, a.spin_limit)) S.bail = 1;
-  }
-  __syncthreads();
-  if (S.bail) return;
+    // Load the tile: one bulk copy each for keys and values (TMA, 16-byte
+    // granules), plain loads for a ragged remainder or unaligned arrays. A
+    // block's earlier tile wrote these buffers through ordinary stores, so
+    // the copy is ordered after them by a proxy fence.
+    const uint64_t *kp = ksrc + base;
+    const uint32_t *vp = vsrc + base;
+    const bool aligned = ((((uintptr_t)kp) | ((uintptr_t)vp)) & 15u) == 0;
+    const uint32_t kbytes = aligned ? (count * 8u) & ~15u : 0u;
+    const uint32_t vbytes = aligned ? (count * 4u) & ~15u : 0u;
+    if (tid == 0 && (kbytes | vbytes)) {
+      fence_proxy_async_shared();
+      mbar_expect_tx(&S.bar, kbytes + vbytes);
+      if (kbytes) bulk_g2s(S.keys, kp, kbytes, &S.bar);
+      if (vbytes) bulk_g2s(S.vals, vp, vbytes, &S.bar);
+    }
+    for (uint32_t e = kbytes / 8u + tid; e < count; e += OS_BLOCK) S.keys[e] = kp[e];
+    for (uint32_t e = vbytes / 4u + tid; e < count; e += OS_BLOCK) S.vals[e] = vp[e];
+    if (kbytes | vbytes) {
+      if (!mbar_wait_bounded(&S.bar, phase, a.ctrl, a.spin_limit)) S.bail = 1;
+      phase ^= 1u;
+    }
+    __syncthreads();
+    if (S.bail) return;
 
-  // Warp-striped items: item k of lane l at warp*32*ITEMS + k*32 + l, so
-  // the order (warp, k, lane) is the input order inside the tile. Items
-  // past the end read as all ones: they take the largest digit and come
-  // last in the tile.
-  uint64_t key[OS_ITEMS];
-  uint32_t pos[OS_ITEMS];
-  const uint32_t dmax = (1u << a.bits) - 1u;
+    // Warp-striped items: item k of lane l at warp*32*ITEMS + k*32 + l, so
+    // the order (warp, k, lane) is the input order inside the tile. Items
+    // past the end read as all ones: they take the largest digit and come
+    // last in the tile.
+    uint64_t key[OS_ITEMS];
+    uint32_t pos[OS_ITEMS];
 #pragma unroll
-  for (int k = 0; k < OS_ITEMS; ++k) {
-    const uint32_t li = warp * (32 * OS_ITEMS) + k * 32 + lane;
-    key[k] = li < count ? S.keys[li] : ~0ull;
-  }
-  // Early counts: the tile's digit histogram by shared-memory atomics
-  // (independent, so cheap), published before the ranking so that the
-  // successors' look-backs find this tile's aggregate while it ranks.
+    for (int k = 0; k < OS_ITEMS; ++k) {
+      const uint32_t li = warp * (32 * OS_ITEMS) + k * 32 + lane;
+      key[k] = li < count ? S.keys[li] : ~0ull;
+    }
+    // Early counts: the tile's digit histogram by shared-memory atomics
+    // (independent, so cheap), published before the ranking so that the
+    // successors' look-backs find this tile's aggregate while it ranks.
 #pragma unroll
-  for (int k = 0; k < OS_ITEMS; ++k) {
-    const uint32_t li = warp * (32 * OS_ITEMS) + k * 32 + lane;
-    if (li < count) atomicAdd(&S.count[digit_of(key[k], a.shift, a.bits)], 1u);
-  }
-  __syncthreads();
-  const uint32_t d = tid;  // thread d owns digit d and its status word
-  const uint32_t mine = S.count[d];
-  uint64_t *st = a.status + (uint64_t)tile * RADIX + d;
-  if (a.inject && tile == 0) {
-    // Test hook: this tile never publishes, so the next tile's wait expires.
-    if (d == 0) S.bail = 1;
-  } else {
-    status_store(st, status_word(a.epoch, tile == 0 ? ST_INC : ST_AGG, mine));
-  }
-
-  // Rank within the tile: stable, by per-warp peers and counts (peers by
-  // match.any on the plan's low-entropy passes, else by the masks).
-  uint16_t *wh = S.whist[warp];
-  uint32_t *mt = OS_ALIAS ? reinterpret_cast<uint32_t *>(S.keys) + warp * RADIX : S.match[warp];
-  if (OS_ALIAS) {  // every key was read into registers before the barrier above
-    for (int x = lane; x < RADIX; x += 32) mt[x] = 0u;
-    __syncwarp();
-  }
-  const uint32_t lt = lanemask_lt();
-  if ((a.plan->match_mask >> a.p) & 1u) {
-#pragma unroll
-    for (int k = 0; k < OS_ITEMS; ++k)
-      pos[k] = warp_rank_digit_match(digit_of(key[k], a.shift, a.bits), wh, lt);
-  } else {
-#pragma unroll
-    for (int k = 0; k < OS_ITEMS; ++k)
-      pos[k] = warp_rank_digit(digit_of(key[k], a.shift, a.bits), mt, wh, lane, lt);
-  }
-  __syncthreads();
-
-  // Thread d: counts of digit d per warp -> per-warp exclusive prefixes.
-  uint32_t total = 0;
-#pragma unroll
-  for (int w = 0; w < OS_WARPS; ++w) {
-    const uint32_t c = S.whist[w][d];
-    S.whist[w][d] = (uint16_t)total;
-    total += c;
-  }
-  uint32_t tile_total;
-  const uint32_t start = block_exclusive<OS_BLOCK>(total, OpAdd(), 0u, S.tmp, tile_total);
-  S.start[d] = start;
-
-  // Look back over the predecessors (their aggregates were published early).
-  if (!S.bail) {
-    if (tile == 0) {
-      S.goff[d] = a.digit_base[d] - start;
+    for (int k = 0; k < OS_ITEMS; ++k) {
+      const uint32_t li = warp * (32 * OS_ITEMS) + k * 32 + lane;
+      if (li < count) atomicAdd(&S.count[digit_of(key[k], shift, bits)], 1u);
+    }
+    __syncthreads();
+    const uint32_t d = tid;  // thread d owns digit d and its status word
+    const uint32_t mine = S.count[d];
+    uint64_t *st = a.status + (uint64_t)tile * RADIX + d;
+    if (a.inject && tile == 0) {
+      // Test hook: this tile never publishes, so the next tile's wait expires.
+      if (d == 0) S.bail = 1;
     } else {
-      uint32_t excl = 0;
-      if (look_back_w<LB_WINDOW>(a.status, RADIX, d, tile, a.epoch, OpAdd(), excl, a.ctrl,
-                                 a.spin_limit)) {
-        status_store(st, status_word(a.epoch, ST_INC, excl + mine));
-        S.goff[d] = a.digit_base[d] + excl - start;
-      } else {
-        S.bail = 1;
-      }
+      status_store(st, status_word(epoch, tile == 0 ? ST_INC : ST_AGG, mine));
     }
-  }
-  __syncthreads();
-  if (S.bail) return;
 
-  // Permute the tile into digit order in place (every read of the input
-  // order happened before the barrier above), then write each digit run
-  // with consecutive addresses.
+    // Rank within the tile: stable, by per-warp peers and counts (peers by
+    // match.any on the plan's low-entropy passes, else by the masks).
+    uint16_t *wh = S.whist[warp];
+    uint32_t *mt = OS_ALIAS ? reinterpret_cast<uint32_t *>(S.keys) + warp * RADIX : S.match[warp];
+    if (OS_ALIAS) {  // every key was read into registers before the barrier above
+      for (int x = lane; x < RADIX; x += 32) mt[x] = 0u;
+      __syncwarp();
+    }
+    const uint32_t lt = lanemask_lt();
+    if ((a.plan->match_mask >> a.p) & 1u) {
 #pragma unroll
-  for (int k = 0; k < OS_ITEMS; ++k) {
-    const uint32_t li = warp * (32 * OS_ITEMS) + k * 32 + lane;
-    const uint32_t dk = li < count ? digit_of(key[k], a.shift, a.bits) : dmax;
-    pos[k] += S.start[dk] + S.whist[warp][dk];
-    S.keys[pos[k]] = key[k];
-  }
-  uint32_t val[OS_ITEMS];
+      for (int k = 0; k < OS_ITEMS; ++k)
+        pos[k] = warp_rank_digit_match(digit_of(key[k], shift, bits), wh, lt);
+    } else {
 #pragma unroll
-  for (int k = 0; k < OS_ITEMS; ++k) {
-    const uint32_t li = warp * (32 * OS_ITEMS) + k * 32 + lane;
-    val[k] = li < count ? S.vals[li] : 0u;
-  }
-  __syncthreads();
+      for (int k = 0; k < OS_ITEMS; ++k)
+        pos[k] = warp_rank_digit(digit_of(key[k], shift, bits), mt, wh, lane, lt);
+    }
+    __syncthreads();
+
+    // Thread d: counts of digit d per warp -> per-warp exclusive prefixes.
+    uint32_t total = 0;
 #pragma unroll
-  for (int k = 0; k < OS_ITEMS; ++k) S.vals[pos[k]] = val[k];
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < OS_ITEMS; ++k) {
-    const uint32_t q = k * OS_BLOCK + tid;
-    if (q < count) {
-      const uint64_t kk = S.keys[q];
-      const uint32_t g = S.goff[digit_of(kk, a.shift, a.bits)] + q;
-      if (g < a.m) {
-        kdst[g] = kk;
-        vdst[g] = S.vals[q];
-      } else {  // never taken unless the histogram and the pass disagree
-        raise_error(a.ctrl, ERR_INTERNAL, 2);
+    for (int w = 0; w < OS_WARPS; ++w) {
+      const uint32_t c = S.whist[w][d];
+      S.whist[w][d] = (uint16_t)total;
+      total += c;
+    }
+    uint32_t tile_total;
+    const uint32_t start = block_exclusive<OS_BLOCK>(total, OpAdd(), 0u, S.tmp, tile_total);
+    S.start[d] = start;
+
+    // Look back over the predecessors (their aggregates were published early).
+    if (!S.bail) {
+      if (tile == 0) {
+        S.goff[d] = a.digit_base[d] - start;
+      } else {
+        uint32_t excl = 0;
+        if (look_back_w<LB_WINDOW>(a.status, RADIX, d, tile, epoch, OpAdd(), excl, a.ctrl,
+                                   a.spin_limit)) {
+          status_store(st, status_word(epoch, ST_INC, excl + mine));
+          S.goff[d] = a.digit_base[d] + excl - start;
+        } else {
+          S.bail = 1;
+        }
       }
     }
+    __syncthreads();
+    if (S.bail) return;
+
+    // Permute the tile into digit order in place (every read of the input
+    // order happened before the barrier above), then write each digit run
+    // with consecutive addresses.
+#pragma unroll
+    for (int k = 0; k < OS_ITEMS; ++k) {
+      const uint32_t li = warp * (32 * OS_ITEMS) + k * 32 + lane;
+      const uint32_t dk = li < count ? digit_of(key[k], shift, bits) : dmax;
+      pos[k] += S.start[dk] + S.whist[warp][dk];
+      S.keys[pos[k]] = key[k];
+    }
+    uint32_t val[OS_ITEMS];
+#pragma unroll
+    for (int k = 0; k < OS_ITEMS; ++k) {
+      const uint32_t li = warp * (32 * OS_ITEMS) + k * 32 + lane;
+      val[k] = li < count ? S.vals[li] : 0u;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < OS_ITEMS; ++k) S.vals[pos[k]] = val[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < OS_ITEMS; ++k) {
+      const uint32_t q = k * OS_BLOCK + tid;
+      if (q < count) {
+        const uint64_t kk = S.keys[q];
+        const uint32_t g = S.goff[digit_of(kk, shift, bits)] + q;
+        if (g < m) {
+          kdst[g] = kk;
+          vdst[g] = S.vals[q];
+        } else {  // never taken unless the histogram and the pass disagree
+          raise_error(a.ctrl, ERR_INTERNAL, 2);
+        }
+      }
+    }
+    __syncthreads();  // the next tile reuses the shared buffers
   }
 }
 
@@ -365,8 +398,9 @@ cudaError_t launch_onesweep_t(const PassArgs &a, cudaStream_t stream) {
       ensure_smem_attributes(reinterpret_cast<const void *>(&k_onesweep<OS_ITEMS>), smem, true);
   if (e != cudaSuccess) return e;
   const uint64_t tile = (uint64_t)OS_BLOCK * OS_ITEMS;
-  const uint64_t tiles = ((uint64_t)a.m + tile - 1) / tile;
-  k_onesweep<OS_ITEMS><<<(unsigned)tiles, OS_BLOCK, smem, stream>>>(a);
+  uint64_t grid = ((uint64_t)a.m + tile - 1) / tile;  // one tile per block
+  if (a.grid_cap && grid > a.grid_cap) grid = a.grid_cap;  // persistent blocks
+  k_onesweep<OS_ITEMS><<<(unsigned)grid, OS_BLOCK, smem, stream>>>(a);
   return cudaGetLastError();
 }
 

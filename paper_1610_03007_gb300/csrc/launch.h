@@ -52,12 +52,16 @@ cudaError_t launch_pack(const PackArgs &a, cudaStream_t stream);
 
 // ---- step A2: radix sort (k_sort.cu) ------------------------------------
 // hist[P*256] += digit counts of keys[0, m) for the digits in spec.
+// rs (device-driven rounds): m and spec come from rs->mL and rs->spec
+// instead (m then sizes the grid only).
 cudaError_t launch_digit_histogram(const uint64_t *keys, uint32_t m, const DigitSpec &spec,
-                                   uint32_t *hist, int num_sms, cudaStream_t stream);
+                                   uint32_t *hist, int num_sms, cudaStream_t stream,
+                                   const RoundState *rs = nullptr);
 // Exclusive digit offsets, constant-digit skipping and buffer ping-pong.
 cudaError_t launch_sort_plan(const uint32_t *hist, uint32_t *digit_base, const DigitSpec &spec,
                              uint32_t m, uint64_t *ka, uint64_t *kb, uint32_t *va,
-                             uint32_t *vb, SortPlan *plan, Ctrl *ctrl, cudaStream_t stream);
+                             uint32_t *vb, SortPlan *plan, Ctrl *ctrl, cudaStream_t stream,
+                             const RoundState *rs = nullptr);
 // One stable one-sweep pass over digit p of the plan.
 struct PassArgs {
   const SortPlan *plan;
@@ -72,6 +76,10 @@ struct PassArgs {
   uint32_t spin_limit;
   uint32_t inject;
   uint32_t items;    // keys per thread: 8, 12 or 16 (tile = 256 * items)
+  // Device-driven rounds: sizes, digit and epoch base from the round state
+  // (m then bounds the grid only; epoch is an offset). NULL: the fields above.
+  const RoundState *rs;
+  uint32_t grid_cap;  // at most this many blocks, each looping over tiles (0: one per tile)
 };
 constexpr int SORT_TILE_MIN = 256 * 8;  // smallest tile (sizes the status array)
 constexpr uint32_t SORT_ITEMS_DEFAULT = 16;
@@ -112,6 +120,10 @@ struct RenameArgs {
   uint32_t *tile_ctr;
   Ctrl *ctrl;
   uint32_t spin_limit;
+  // Device-driven rounds: m = rs->mL, g_in = rs->GL and epoch base
+  // rs->epoch (m above then bounds the grid only). NULL: the fields above.
+  const RoundState *rs;
+  uint32_t grid_cap;         // at most this many blocks, each looping over tiles (0: one per tile)
 };
 #ifndef GBSA_RN_ITEMS
 #define GBSA_RN_ITEMS 8
@@ -158,6 +170,7 @@ struct ClassifyArgs {
   uint32_t max_groups;      // upper bound of G (buffer capacity)
   uint32_t max_tiles;       // upper bound of tiles (buffer capacity - 1)
   Ctrl *ctrl;               // reads rc.m_s + rc.m_l, rc.g_s + rc.g_l; adds to rc.large
+  const RoundState *rs;     // device-driven rounds: nothing once the loop ended (else NULL)
 };
 cudaError_t launch_classify(const ClassifyArgs &a, int num_sms, cudaStream_t stream);
 
@@ -179,6 +192,10 @@ struct GatherLargeArgs {
   uint32_t *vals;
   uint64_t *key1_stash;     // a > 2: (k << W) | r2 by item
   uint64_t *sec_stash;      // a > 2: later partners by item
+  // Device-driven rounds: mL, GL and h from the round state (mL above then
+  // bounds the grid only). NULL: the fields above.
+  const RoundState *rs;
+  uint32_t grid_cap;        // at most this many blocks (grid-stride; 0: one item per thread)
 };
 cudaError_t launch_gather_large(const GatherLargeArgs &a, cudaStream_t stream);
 
@@ -223,6 +240,10 @@ struct RefineArgs {
   uint32_t *gstart_out, *gname_out, *ghead_out;
   uint64_t *upd;            // (new << 32) | i' for every changed name
   Ctrl *ctrl;               // rc.m_s / rc.g_s / rc.upd reserve the outputs
+  // Device-driven rounds: tiles and h from the round state (tiles above
+  // then bounds the grid only). NULL: the fields above.
+  const RoundState *rs;
+  uint32_t grid_cap;        // at most this many blocks, each looping over tiles (0: one per tile)
 };
 cudaError_t launch_refine(const RefineArgs &a, cudaStream_t stream);
 
@@ -230,14 +251,41 @@ cudaError_t launch_refine(const RefineArgs &a, cudaStream_t stream);
 // name differs from their parent's (the rename's survivors, or a bucketed
 // copy of them); *count <= max_count. Blocks take consecutive chunks in
 // launch order.
+// Device-driven rounds (rs): nothing when rs->mL = 0; with rs->bucket_surv
+// the entries are bucketed[0, *count) instead. grid_cap: at most this many
+// blocks (0: one per chunk).
 cudaError_t launch_apply_names(const uint64_t *act, const uint32_t *lo, const uint32_t *count,
                                uint32_t max_count, const uint32_t *gname, const uint32_t *gold,
-                               uint32_t *isa, uint64_t isa_len, cudaStream_t stream);
+                               uint32_t *isa, uint64_t isa_len, cudaStream_t stream,
+                               const uint64_t *bucketed = nullptr, const uint32_t *zero = nullptr,
+                               const RoundState *rs = nullptr, uint32_t grid_cap = 0);
 
 // ISA[i'] = new for the min(ctrl->rc.upd, max_upd) queued updates; blocks
-// take consecutive chunks in launch order.
+// take consecutive chunks in launch order. Device-driven rounds (rs): the
+// updates are bucketed[...] when rs->bucket_upd.
 cudaError_t launch_scatter_updates(const uint64_t *upd, uint32_t max_upd, uint32_t *isa,
-                                   uint64_t isa_len, Ctrl *ctrl, cudaStream_t stream);
+                                   uint64_t isa_len, Ctrl *ctrl, cudaStream_t stream,
+                                   const uint64_t *bucketed = nullptr,
+                                   const RoundState *rs = nullptr, uint32_t grid_cap = 0);
+
+// ---- device-driven rounds (k_rounds.cu) ------------------------------------
+// Look-back epochs one device-driven round may use (its launches take the
+// offsets 0 .. ROUND_EPOCHS - 1 from the round state's base).
+constexpr uint32_t ROUND_EPOCHS = 16;
+struct RoundBeginArgs {
+  Ctrl *ctrl;               // ctrl->rs, ctrl->rc, ctrl->rec, ctrl->tile_ctr
+  uint32_t *hist;           // MAX_PASSES * 256 digit histograms of the large-group sort
+  uint32_t W;               // bits of a partner name
+  uint32_t nominal;         // refine window (tiles = ceil(m / nominal))
+  uint32_t bucket_min;      // discard threshold of the ISA writes
+  uint32_t N;               // characters (h never exceeds it)
+  // If-nodes of this round: large-group sort, its rename, bucketing of the
+  // queued updates, bucketing of the large groups' ISA entries.
+  cudaGraphConditionalHandle if_sort, if_rename, if_bucket_upd, if_bucket_surv;
+};
+cudaError_t launch_round_begin(const RoundBeginArgs &a, cudaStream_t stream);
+// Sets `loop` to 1 while suffixes are active and no error was raised.
+cudaError_t launch_round_end(const Ctrl *c, cudaGraphConditionalHandle loop, cudaStream_t stream);
 
 // ---- position bucketing of ISA writes (k_bucket.cu) ------------------------
 constexpr uint32_t BUCKET_BLOCKS_MAX = 1024;

@@ -142,11 +142,17 @@ def test_every_round_default_names_are_valid(gb, orc, recipe, n):
 
 
 def test_workload_1_full_size(gb, orc):
-    """Uniform DNA, n = 2^20: 32 characters per key resolve it in round 0."""
+    """Uniform DNA, n = 2^20, with the library's own parameters (the tuning
+    table's key width) and with the full 32-character key, which resolves
+    every suffix in round 0."""
     t = gen.text("dna", 1001, 1 << 20)
+    want = orc.pd_sa(t)[0]
     sa, _, stats, _ = gb.sa_build_ex(dev_text(t))
-    assert stats["chars_per_key"] == 32 and stats["bits_per_char"] == 2
-    assert np.array_equal(sa.cpu().numpy().view(np.uint32), orc.pd_sa(t)[0])
+    assert stats["bits_per_char"] == 2
+    assert np.array_equal(sa.cpu().numpy().view(np.uint32), want)
+    sa, _, stats, _ = gb.sa_build_ex(dev_text(t), h0_chars=32)
+    assert stats["chars_per_key"] == 32 and stats["rounds"] == 1
+    assert np.array_equal(sa.cpu().numpy().view(np.uint32), want)
 
 
 @pytest.mark.parametrize("recipe", ["zipf_repeats", "markov"])
@@ -161,7 +167,8 @@ def test_bucketed_isa_writes_elementwise(gb, orc):
     equal the oracle's at a ragged size where both paths run."""
     n = 5 * (1 << 20) + 77
     t = gen.text("zipf_repeats", 2003, n)
-    sa, isa, stats, _ = gb.sa_build_ex(dev_text(t), isa=True, profile=True)
+    sa, isa, stats, _ = gb.sa_build_ex(dev_text(t), isa=True, profile=True, bucket_min=1 << 22,
+                                       h0_chars=8)
     want_sa, want_isa, _, _ = orc.pd_sa(t)
     assert stats["active"][1] >= 1 << 22
     assert stats["kernels"]["bucket"]["launches"] >= 4
