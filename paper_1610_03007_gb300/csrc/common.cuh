@@ -82,6 +82,7 @@ struct Ctrl {
   uint32_t pass_mask;  // bit p set iff pass p of the last plan was kept
   RoundCounts rc;
   uint32_t zero[4];    // constant zeros (output offsets of round 0)
+  uint32_t bucket_total;  // entries a translating position partition kept
   uint32_t tile_ctr[TILE_COUNTERS];  // one dynamic tile counter per launch
   RoundState rs;                     // device-driven rounds only
   RoundRecord rec[DEV_MAX_ROUNDS];

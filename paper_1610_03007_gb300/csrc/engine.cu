@@ -484,16 +484,22 @@ struct Build {
     if (apply_bound == 0) return SA_OK;
     const uint64_t *src = act[out];
     const uint32_t *lo = &ctrl->rc.m_s;
+    const uint32_t *count = &ctrl->rc.m_l;
+    uint32_t translated = 0;
     if (apply_bound >= bucket_min) {
-      s = bucket(src, lo, &ctrl->rc.m_l, apply_bound, 2);
+      // The partition reads the group names while the entries are still in
+      // group order and keeps only the changed ones, as (name, i').
+      s = bucket(src, lo, &ctrl->rc.m_l, apply_bound, 2, gname[out]);
       if (s != SA_OK) return s;
       src = kb;
       lo = ctrl->zero;
+      count = &ctrl->bucket_total;
+      translated = 1;
     }
     ++pend.apply;
     return launch(SA_K_APPLY, 0, PENDING, [&] {
-      return launch_apply_names(src, lo, &ctrl->rc.m_l, apply_bound, gname[out], gold, isa,
-                                N + S + 1, st);
+      return launch_apply_names(src, lo, count, apply_bound, gname[out], gold, isa, N + S + 1,
+                                st, translated);
     });
   }
 
@@ -501,8 +507,13 @@ struct Build {
   // buffer B (free whenever ISA writes are pending). `src_tag` tells the
   // byte settlement which count applies (0: queued updates, 2: survivors).
   sa_status bucket(const uint64_t *in, const uint32_t *lo, const uint32_t *count,
-                   uint32_t max_count, int src_tag) {
+                   uint32_t max_count, int src_tag, const uint32_t *translate_names = nullptr) {
     BucketArgs ba{};
+    if (translate_names) {
+      ba.gname = translate_names;
+      ba.gold = gold;
+      ba.total_out = &ctrl->bucket_total;
+    }
     ba.in = in;
     ba.lo = lo;
     ba.count = count;
@@ -783,13 +794,16 @@ struct Build {
     ba.in = act[nxt];
     ba.lo = &ctrl->rc.m_s;
     ba.count = &ctrl->rc.m_l;
+    ba.gname = gname[nxt];  // translating: (name, i') of the changed names only
+    ba.gold = gold;
+    ba.total_out = &ctrl->bucket_total;
     if ((e = begin_if(cs, cs2, hd.bucket_surv)) != cudaSuccess) return e;
     if ((e = launch_bucket_count(ba, cs2)) != cudaSuccess) return e;
     if ((e = launch_bucket_offsets(ba, cs2)) != cudaSuccess) return e;
     if ((e = launch_bucket_scatter(ba, cs2)) != cudaSuccess) return e;
     if ((e = end_capture(cs2)) != cudaSuccess) return e;
     return launch_apply_names(act[nxt], &ctrl->rc.m_s, &ctrl->rc.m_l, m1, gname[nxt], gold, isa,
-                              N + S + 1, cs, kb, ctrl->zero, rs, 8 * sms);
+                              N + S + 1, cs, 0, kb, ctrl->zero, &ctrl->bucket_total, rs, 8 * sms);
   }
 
   // Rounds >= 1 as one graph: while (suffixes active) { round; round }.

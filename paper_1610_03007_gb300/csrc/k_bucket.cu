@@ -21,6 +21,12 @@
 // Order inside a bucket is arbitrary: the ISA writes of one pass commute,
 // since every position is written at most once.
 //
+// A translating partition (BucketArgs.gname set, for the rename's
+// survivors) drops the entries whose group kept its parent's name and
+// writes the others as (name << 32) | i', reading the group names while the
+// entries are still in group order; the ISA writes after it need no
+// lookups.
+//
 // Bound: HBM. Per entry 8 bytes read by the count, 8 read and 8 written by
 // the scatter.
 #include "launch.h"
@@ -50,6 +56,18 @@ __device__ __forceinline__ uint32_t bucket_of(uint64_t e, uint32_t shift) {
   return min((uint32_t)e >> shift, (uint32_t)RADIX - 1u);
 }
 
+// Translating partition: the entry (g << 32) | i' of a renamed survivor
+// becomes (gname[g] << 32) | i', or is dropped (false) when its group kept
+// its parent's name. Plain partition: the entry as it is.
+__device__ __forceinline__ bool translate(const BucketArgs &a, uint64_t &e) {
+  if (!a.gname) return true;
+  const uint32_t g = (uint32_t)(e >> 32);
+  const uint32_t name = __ldg(a.gname + g);
+  if (name == __ldg(a.gold + g)) return false;
+  e = ((uint64_t)name << 32) | (uint32_t)e;
+  return true;
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(256, 4) k_bucket_count(BucketArgs a) {
@@ -69,7 +87,8 @@ __global__ void __launch_bounds__(256, 4) k_bucket_count(BucketArgs a) {
     }
 #pragma unroll
     for (int k = 0; k < BK_ITEMS; ++k)
-      if (c0 + (uint64_t)k * 256 + t < b1) atomicAdd(&bins[bucket_of(e[k], a.shift)], 1u);
+      if (c0 + (uint64_t)k * 256 + t < b1 && translate(a, e[k]))
+        atomicAdd(&bins[bucket_of(e[k], a.shift)], 1u);
   }
   __syncthreads();
   a.counts[(size_t)blockIdx.x * RADIX + t] = bins[t];
@@ -99,6 +118,7 @@ __global__ void __launch_bounds__(256) k_bucket_offsets(BucketArgs a, uint32_t b
       run += c[i];
     }
   }
+  if (a.total_out && k == RADIX - 1) *a.total_out = run;  // the end of the last bucket
 }
 
 // Per chunk: rank each entry in its bucket (shared atomics), scan the
@@ -109,6 +129,7 @@ __global__ void __launch_bounds__(256, 4) k_bucket_scatter(BucketArgs a) {
   __shared__ uint64_t stage[BK_CHUNK];
   __shared__ uint32_t run[RADIX], cnt[RADIX], at0[RADIX], lofs[RADIX];
   __shared__ uint32_t wtot[8];
+  __shared__ uint32_t kept_sh;
   const uint32_t t = threadIdx.x, lane = t & 31, warp = t >> 5;
   run[t] = a.counts[(size_t)blockIdx.x * RADIX + t];
   cnt[t] = 0u;
@@ -120,6 +141,7 @@ __global__ void __launch_bounds__(256, 4) k_bucket_scatter(BucketArgs a) {
     const uint32_t len = (uint32_t)min((uint64_t)BK_CHUNK, b1 - c0);
     uint64_t e[BK_ITEMS];
     uint32_t rk[BK_ITEMS];
+    uint32_t keep = 0;  // bit k: entry k is written
 #pragma unroll
     for (int k = 0; k < BK_ITEMS; ++k) {
       const uint32_t x = (uint32_t)k * 256 + t;
@@ -127,7 +149,10 @@ __global__ void __launch_bounds__(256, 4) k_bucket_scatter(BucketArgs a) {
     }
 #pragma unroll
     for (int k = 0; k < BK_ITEMS; ++k)
-      if ((uint32_t)k * 256 + t < len) rk[k] = atomicAdd(&cnt[bucket_of(e[k], a.shift)], 1u);
+      if ((uint32_t)k * 256 + t < len && translate(a, e[k])) {
+        keep |= 1u << k;
+        rk[k] = atomicAdd(&cnt[bucket_of(e[k], a.shift)], 1u);
+      }
     __syncthreads();
     {
       const uint32_t c = cnt[t];
@@ -140,14 +165,16 @@ __global__ void __launch_bounds__(256, 4) k_bucket_scatter(BucketArgs a) {
 #pragma unroll
       for (int w = 0; w < 8; ++w) before += (uint32_t)w < warp ? wtot[w] : 0u;
       lofs[t] = before;
+      if (t == RADIX - 1) kept_sh = before + c;  // entries the chunk keeps
       cnt[t] = 0u;
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < BK_ITEMS; ++k)
-      if ((uint32_t)k * 256 + t < len) stage[lofs[bucket_of(e[k], a.shift)] + rk[k]] = e[k];
+      if ((keep >> k) & 1u) stage[lofs[bucket_of(e[k], a.shift)] + rk[k]] = e[k];
     __syncthreads();
-    for (uint32_t i = t; i < len; i += 256) {
+    const uint32_t kept = kept_sh;  // == len unless the partition translates
+    for (uint32_t i = t; i < kept; i += 256) {
       const uint64_t v = stage[i];
       const uint32_t b = bucket_of(v, a.shift);
       const uint32_t at = at0[b] + (i - lofs[b]);

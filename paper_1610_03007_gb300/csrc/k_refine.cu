@@ -847,33 +847,45 @@ renamed_order:
 // Blocks take tiles blockIdx.x, + gridDim.x, ... (tiles share nothing, so
 // any grid works); in device-driven rounds the tile count and h come from
 // the round state.
-template <int BLOCK, int CAP, bool WIDE>
+template <int BLOCK, int CAP, bool WIDE, bool PERSIST>
 __global__ void __launch_bounds__(BLOCK, (CAP / BLOCK > 8 ? 512 : 1024) / BLOCK)
     k_refine(RefineArgs a) {
   using Sm = RfSmem<BLOCK, CAP, WIDE>;
   extern __shared__ __align__(128) uint8_t smem_raw[];
   Sm &S = *reinterpret_cast<Sm *>(smem_raw);
-  uint32_t tiles = a.tiles, h = a.h;
-  if (a.rs) {
-    if (!a.rs->live) return;
-    tiles = a.rs->tiles;
-    h = a.rs->h;
-  }
-  for (uint32_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    refine_tile<BLOCK, CAP, WIDE>(S, a, tile, h);
-    __syncthreads();  // the next tile reuses the shared buffers
+  if constexpr (!PERSIST) {  // one tile per block (host-driven rounds)
+    refine_tile<BLOCK, CAP, WIDE>(S, a, blockIdx.x, a.h);
+  } else {
+    uint32_t tiles = a.tiles, h = a.h;
+    if (a.rs) {
+      if (!a.rs->live) return;
+      tiles = a.rs->tiles;
+      h = a.rs->h;
+    }
+    for (uint32_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+      refine_tile<BLOCK, CAP, WIDE>(S, a, tile, h);
+      __syncthreads();  // the next tile reuses the shared buffers
+    }
   }
 }
 
-template <int BLOCK, int CAP, bool WIDE>
-cudaError_t launch_refine_t(const RefineArgs &a, cudaStream_t stream) {
+template <int BLOCK, int CAP, bool WIDE, bool PERSIST>
+cudaError_t launch_refine_p(const RefineArgs &a, uint32_t grid, cudaStream_t stream) {
   const int smem = (int)sizeof(RfSmem<BLOCK, CAP, WIDE>);
   cudaError_t e = ensure_smem_attributes(
-      reinterpret_cast<const void *>(&k_refine<BLOCK, CAP, WIDE>), smem, true);
+      reinterpret_cast<const void *>(&k_refine<BLOCK, CAP, WIDE, PERSIST>), smem, true);
   if (e != cudaSuccess) return e;
-  const uint32_t grid = a.grid_cap && a.tiles > a.grid_cap ? a.grid_cap : a.tiles;
-  k_refine<BLOCK, CAP, WIDE><<<grid, BLOCK, smem, stream>>>(a);
+  k_refine<BLOCK, CAP, WIDE, PERSIST><<<grid, BLOCK, smem, stream>>>(a);
   return cudaGetLastError();
+}
+
+// The one-tile-per-block instance unless the round state or a grid cap
+// asks for the looping one (its loop costs the single-tile form registers).
+template <int BLOCK, int CAP, bool WIDE>
+cudaError_t launch_refine_t(const RefineArgs &a, cudaStream_t stream) {
+  if (!a.rs && !a.grid_cap) return launch_refine_p<BLOCK, CAP, WIDE, false>(a, a.tiles, stream);
+  const uint32_t grid = a.grid_cap && a.tiles > a.grid_cap ? a.grid_cap : a.tiles;
+  return launch_refine_p<BLOCK, CAP, WIDE, true>(a, grid, stream);
 }
 
 template <bool WIDE>
@@ -911,16 +923,38 @@ __global__ void __launch_bounds__(256) k_apply_names(const uint64_t *__restrict_
                                                     const uint32_t *__restrict__ gname,
                                                     const uint32_t *__restrict__ gold,
                                                     uint32_t *isa, uint64_t isa_len,
+                                                    uint32_t translated,
                                                     const uint64_t *__restrict__ bucketed,
-                                                    const uint32_t *zero, const RoundState *rs) {
+                                                    const uint32_t *zero,
+                                                    const uint32_t *bucketed_count,
+                                                    const RoundState *rs) {
   if (rs) {
     if (!rs->live || rs->mL == 0) return;
     if (rs->bucket_surv) {
       act = bucketed;
       lo_p = zero;
+      count_p = bucketed_count;
+      translated = 1;
     }
   }
   const uint64_t lo = *lo_p, n = *count_p;
+  if (translated) {  // (name << 32) | i', every one a change
+    for (uint64_t c0 = (uint64_t)blockIdx.x * WB_CHUNK; c0 < n;
+         c0 += (uint64_t)gridDim.x * WB_CHUNK) {
+      uint64_t e[WB_ITEMS];
+#pragma unroll
+      for (int k = 0; k < WB_ITEMS; ++k) {
+        const uint64_t x = c0 + (uint64_t)k * 256 + threadIdx.x;
+        e[k] = x < n ? act[lo + x] : ~0ull;
+      }
+#pragma unroll
+      for (int k = 0; k < WB_ITEMS; ++k) {
+        const uint32_t ip = (uint32_t)e[k];
+        if (e[k] != ~0ull && ip < isa_len) isa[ip] = (uint32_t)(e[k] >> 32);
+      }
+    }
+    return;
+  }
   for (uint64_t c0 = (uint64_t)blockIdx.x * WB_CHUNK; c0 < n;
        c0 += (uint64_t)gridDim.x * WB_CHUNK) {
     uint64_t e[WB_ITEMS];
@@ -942,13 +976,15 @@ __global__ void __launch_bounds__(256) k_apply_names(const uint64_t *__restrict_
 cudaError_t launch_apply_names(const uint64_t *act, const uint32_t *lo, const uint32_t *count,
                                uint32_t max_count, const uint32_t *gname, const uint32_t *gold,
                                uint32_t *isa, uint64_t isa_len, cudaStream_t stream,
-                               const uint64_t *bucketed, const uint32_t *zero,
+                               uint32_t translated, const uint64_t *bucketed,
+                               const uint32_t *zero, const uint32_t *bucketed_count,
                                const RoundState *rs, uint32_t grid_cap) {
   uint64_t blocks = ((uint64_t)max_count + WB_CHUNK - 1) / WB_CHUNK;
   if (blocks == 0) return cudaSuccess;
   if (grid_cap && blocks > grid_cap) blocks = grid_cap;
   k_apply_names<<<(unsigned)blocks, 256, 0, stream>>>(act, lo, count, gname, gold, isa, isa_len,
-                                                      bucketed, zero, rs);
+                                                      translated, bucketed, zero, bucketed_count,
+                                                      rs);
   return cudaGetLastError();
 }
 

@@ -267,6 +267,7 @@ __device__ __forceinline__ bool rename_tile(RnSmem &S, const RenameArgs &a, cons
 // than the tile count makes the blocks persistent); in device-driven
 // rounds the item and group counts and the epoch base come from the round
 // state.
+template <bool PERSIST>
 __global__ void __launch_bounds__(RN_BLOCK, RN_ITEMS <= 4 ? 6 : 4) k_rename(RenameArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   RnSmem &S = *reinterpret_cast<RnSmem *>(smem_raw);
@@ -288,6 +289,7 @@ __global__ void __launch_bounds__(RN_BLOCK, RN_ITEMS <= 4 ? 6 : 4) k_rename(Rena
     __syncthreads();
     if (S.bail || S.tile >= tiles) return;
     if (!rename_tile(S, a, S.tile, m, g_in, epoch)) return;
+    if constexpr (!PERSIST) return;  // one tile per block: no second claim
     __syncthreads();  // the next tile reuses the shared buffers
   }
 }
@@ -295,11 +297,17 @@ __global__ void __launch_bounds__(RN_BLOCK, RN_ITEMS <= 4 ? 6 : 4) k_rename(Rena
 cudaError_t launch_rename(const RenameArgs &a, cudaStream_t stream) {
   if (a.m == 0) return cudaSuccess;
   const int smem = (int)sizeof(RnSmem);
-  cudaError_t e = ensure_smem_attributes(reinterpret_cast<const void *>(&k_rename), smem, false);
+  // One tile per block unless the grid is capped (persistent blocks loop).
+  const uint32_t tiles = (a.m + RN_TILE - 1) / RN_TILE;
+  const bool persist = a.grid_cap && tiles > a.grid_cap;
+  const void *fn = persist ? reinterpret_cast<const void *>(&k_rename<true>)
+                           : reinterpret_cast<const void *>(&k_rename<false>);
+  cudaError_t e = ensure_smem_attributes(fn, smem, false);
   if (e != cudaSuccess) return e;
-  uint32_t grid = (a.m + RN_TILE - 1) / RN_TILE;
-  if (a.grid_cap && grid > a.grid_cap) grid = a.grid_cap;
-  k_rename<<<grid, RN_BLOCK, smem, stream>>>(a);
+  if (persist)
+    k_rename<true><<<a.grid_cap, RN_BLOCK, smem, stream>>>(a);
+  else
+    k_rename<false><<<tiles, RN_BLOCK, smem, stream>>>(a);
   return cudaGetLastError();
 }
 

@@ -204,7 +204,7 @@ struct OsSmem {
 // OS_ITEMS keys per thread (8, 12 or 16; chosen per build): 16 fits three
 // blocks per SM (~62 KB of shared memory each), 12 four, 8 five; registers
 // are capped to match.
-template <int OS_ITEMS>
+template <int OS_ITEMS, bool PERSIST>
 __global__ void __launch_bounds__(OS_BLOCK, OS_ITEMS >= 16 ? (OS_ALIAS ? 4 : 3)
                                                       : (OS_ITEMS >= 12 ? 4 : 5))
     k_onesweep(PassArgs a) {
@@ -387,6 +387,7 @@ __global__ void __launch_bounds__(OS_BLOCK, OS_ITEMS >= 16 ? (OS_ALIAS ? 4 : 3)
         }
       }
     }
+    if constexpr (!PERSIST) return;  // one tile per block: no second claim
     __syncthreads();  // the next tile reuses the shared buffers
   }
 }
@@ -394,13 +395,18 @@ __global__ void __launch_bounds__(OS_BLOCK, OS_ITEMS >= 16 ? (OS_ALIAS ? 4 : 3)
 template <int OS_ITEMS>
 cudaError_t launch_onesweep_t(const PassArgs &a, cudaStream_t stream) {
   const int smem = (int)sizeof(OsSmem<OS_ITEMS>);
-  cudaError_t e =
-      ensure_smem_attributes(reinterpret_cast<const void *>(&k_onesweep<OS_ITEMS>), smem, true);
-  if (e != cudaSuccess) return e;
   const uint64_t tile = (uint64_t)OS_BLOCK * OS_ITEMS;
-  uint64_t grid = ((uint64_t)a.m + tile - 1) / tile;  // one tile per block
-  if (a.grid_cap && grid > a.grid_cap) grid = a.grid_cap;  // persistent blocks
-  k_onesweep<OS_ITEMS><<<(unsigned)grid, OS_BLOCK, smem, stream>>>(a);
+  const uint64_t tiles = ((uint64_t)a.m + tile - 1) / tile;
+  // One tile per block unless the grid is capped (persistent blocks loop).
+  const bool persist = a.grid_cap && tiles > a.grid_cap;
+  const void *fn = persist ? reinterpret_cast<const void *>(&k_onesweep<OS_ITEMS, true>)
+                           : reinterpret_cast<const void *>(&k_onesweep<OS_ITEMS, false>);
+  cudaError_t e = ensure_smem_attributes(fn, smem, true);
+  if (e != cudaSuccess) return e;
+  if (persist)
+    k_onesweep<OS_ITEMS, true><<<a.grid_cap, OS_BLOCK, smem, stream>>>(a);
+  else
+    k_onesweep<OS_ITEMS, false><<<(unsigned)tiles, OS_BLOCK, smem, stream>>>(a);
   return cudaGetLastError();
 }
 

@@ -251,13 +251,17 @@ cudaError_t launch_refine(const RefineArgs &a, cudaStream_t stream);
 // name differs from their parent's (the rename's survivors, or a bucketed
 // copy of them); *count <= max_count. Blocks take consecutive chunks in
 // launch order.
+// translated (host-driven): the entries are (name << 32) | i' of a
+// translating bucket pass, all to be written, and *count their number.
 // Device-driven rounds (rs): nothing when rs->mL = 0; with rs->bucket_surv
-// the entries are bucketed[0, *count) instead. grid_cap: at most this many
-// blocks (0: one per chunk).
+// the entries are the translated bucketed[0, *bucketed_count) instead.
+// grid_cap: at most this many blocks (0: one per chunk).
 cudaError_t launch_apply_names(const uint64_t *act, const uint32_t *lo, const uint32_t *count,
                                uint32_t max_count, const uint32_t *gname, const uint32_t *gold,
                                uint32_t *isa, uint64_t isa_len, cudaStream_t stream,
-                               const uint64_t *bucketed = nullptr, const uint32_t *zero = nullptr,
+                               uint32_t translated = 0, const uint64_t *bucketed = nullptr,
+                               const uint32_t *zero = nullptr,
+                               const uint32_t *bucketed_count = nullptr,
                                const RoundState *rs = nullptr, uint32_t grid_cap = 0);
 
 // ISA[i'] = new for the min(ctrl->rc.upd, max_upd) queued updates; blocks
@@ -298,6 +302,14 @@ struct BucketArgs {
   uint32_t blocks;        // partition blocks (<= BUCKET_BLOCKS_MAX)
   uint32_t *counts;       // blocks x 256 words: counts, then run starts
   uint64_t *out;          // entries grouped by bucket
+  // Translation (the rename's survivors, entries (g << 32) | i'): when
+  // gname is set, an entry whose group's name equals its parent's (gold) is
+  // dropped and the others are written as (gname[g] << 32) | i', so that
+  // the ISA writes need no group lookups; the number written goes to
+  // *total_out. Entries come in group order, so these lookups are nearly
+  // sequential here and would be random after the partition.
+  const uint32_t *gname, *gold;
+  uint32_t *total_out;
 };
 cudaError_t launch_bucket_count(const BucketArgs &a, cudaStream_t stream);
 cudaError_t launch_bucket_offsets(const BucketArgs &a, cudaStream_t stream);
