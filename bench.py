@@ -356,15 +356,35 @@ def measure_e2e(t_host, steps):
     h_sa = torch.empty(n, dtype=torch.int32).pin_memory()
     gbsa.sa_build_host_ptr(h_text.data_ptr(), n, h_sa.data_ptr())
     torch.cuda.synchronize()
+    calls = []
     t0 = time.perf_counter()
     for _ in range(steps):
+        t1 = time.perf_counter()
         gbsa.sa_build_host_ptr(h_text.data_ptr(), n, h_sa.data_ptr())
+        calls.append((time.perf_counter() - t1) * 1e3)
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) / steps * 1e3
-    del h_text, h_sa
     gbsa.pool_trim(0)
+    # The copies alone, between the same pinned buffers and the device (not
+    # part of the value: they say how much of it the host link takes).
+    d_text = torch.empty(n, dtype=torch.uint8, device="cuda")
+    d_sa = torch.empty(n, dtype=torch.int32, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record()
+    d_text.copy_(h_text, non_blocking=True)
+    ev[1].record()
+    ev[2].record()
+    h_sa.copy_(d_sa, non_blocking=True)
+    ev[3].record()
+    torch.cuda.synchronize()
+    h2d_ms, d2h_ms = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+    del h_text, h_sa, d_text, d_sa
+    torch.cuda.empty_cache()
     return {"value": n / (e2e_ms * 1e-3) / 1e6, "unit": "MB/s", "h2d_bytes_per_step": n,
-            "d2h_bytes_per_step": 4 * n, "ms_per_step": e2e_ms, "steps": steps}
+            "d2h_bytes_per_step": 4 * n, "ms_per_step": e2e_ms, "steps": steps,
+            "ms_per_call": [round(c, 2) for c in calls],
+            "copies_alone": {"h2d_ms": h2d_ms, "h2d_GBps": n / (h2d_ms * 1e-3) / 1e9,
+                             "d2h_ms": d2h_ms, "d2h_GBps": 4 * n / (d2h_ms * 1e-3) / 1e9}}
 
 
 def cfg2_extras(m, steps):

@@ -121,6 +121,14 @@ typedef struct {
    * 4, a name trace or profile = 1 the rounds are host-driven. Same SA and
    * ISA either way. */
   uint32_t device_rounds;
+  /* Order of the groups of equal names in the active list after round 0:
+   * 0 = the library chooses (the position order below whenever a round
+   * follows), 1 = ordered by each group's smallest member position, so that
+   * groups of suffixes that move together (copies of a repeated text) sit
+   * side by side and their partner-name reads share cache lines, 2 = rank
+   * order (as round 0 leaves them). Same SA and ISA either way: a round
+   * needs each group contiguous, not in any order (names are ranks). */
+  uint32_t group_order;
 } sa_options;
 
 /* Tuned build parameters (the autotuner's table, see sa_tuning_set): each
@@ -147,7 +155,8 @@ enum {
   SA_K_CLASSIFY = 10, /* group classification, tile map      */
   SA_K_APPLY = 11,    /* ISA entries of renamed survivors    */
   SA_K_BUCKET = 12,   /* position bucketing of ISA writes    */
-  SA_K_CLASSES = 13
+  SA_K_REORDER = 13,  /* group order after round 0           */
+  SA_K_CLASSES = 14
 };
 
 /* Per-build statistics (HOST struct filled by the _ex calls). */

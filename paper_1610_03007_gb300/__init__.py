@@ -48,7 +48,8 @@ class Options(ctypes.Structure):
                 ("trace_cap", ctypes.c_uint32), ("paper_names", ctypes.c_uint32),
                 ("refine_shape", ctypes.c_uint32), ("sort_items", ctypes.c_uint32),
                 ("profile", ctypes.c_uint32), ("multiplier", ctypes.c_uint32),
-                ("bucket_min", ctypes.c_uint32), ("device_rounds", ctypes.c_uint32)]
+                ("bucket_min", ctypes.c_uint32), ("device_rounds", ctypes.c_uint32),
+                ("group_order", ctypes.c_uint32)]
 
 
 class Tuned(ctypes.Structure):
@@ -61,7 +62,7 @@ class Tuned(ctypes.Structure):
 
 
 KERNEL_CLASSES = ("byte_hist", "pack", "digit_hist", "plan", "onesweep", "rename", "gather",
-                  "output", "refine", "scatter", "classify", "apply", "bucket")
+                  "output", "refine", "scatter", "classify", "apply", "bucket", "reorder")
 
 
 class Stats(ctypes.Structure):
@@ -276,7 +277,8 @@ def sa_build(text, sa_out=None, stream=None):
 
 def sa_build_ex(text, *, isa=False, workspace=None, h0_chars=0, spin_limit=0,
                 inject_stall=0, trace_cap=0, paper_names=False, refine_shape=0, sort_items=0,
-                profile=False, multiplier=0, bucket_min=0, device_rounds=0, stream=None):
+                profile=False, multiplier=0, bucket_min=0, device_rounds=0, group_order=0,
+                stream=None):
     """sa_build with options. Returns (sa, isa or None, stats dict, trace or None).
 
     multiplier: growth factor a of the resolved prefix per round (0 or 2:
@@ -298,7 +300,7 @@ def sa_build_ex(text, *, isa=False, workspace=None, h0_chars=0, spin_limit=0,
     opt = Options(h0_chars, spin_limit, inject_stall,
                   trace.data_ptr() if trace is not None and n else None, trace_cap,
                   1 if paper_names else 0, refine_shape, sort_items, 1 if profile else 0,
-                  multiplier, bucket_min, device_rounds)
+                  multiplier, bucket_min, device_rounds, group_order)
     st = Stats()
     rc = lib.sa_build_ex(t.data_ptr(), n, sa.data_ptr() if n else None,
                          isa_t.data_ptr() if isa_t is not None and n else None,
@@ -310,7 +312,7 @@ def sa_build_ex(text, *, isa=False, workspace=None, h0_chars=0, spin_limit=0,
 
 def sa_build_batched(texts, offsets, sa_out=None, workspace=None, stream=None, stats=False,
                      profile=False, refine_shape=0, sort_items=0, h0_chars=0, multiplier=0,
-                     bucket_min=0, device_rounds=0):
+                     bucket_min=0, device_rounds=0, group_order=0):
     """SAs of many texts in one launch sequence.
 
     texts: 1-D uint8 CUDA tensor (the texts concatenated); offsets: host
@@ -329,7 +331,7 @@ def sa_build_batched(texts, offsets, sa_out=None, workspace=None, stream=None, s
         workspace = torch.empty(wsb, dtype=torch.uint8, device=t.device)
     st = Stats()
     opt = Options(h0_chars, 0, 0, None, 0, 0, refine_shape, sort_items, 1 if profile else 0,
-                  multiplier, bucket_min, device_rounds)
+                  multiplier, bucket_min, device_rounds, group_order)
     rc = lib.sa_build_batched_ex(t.data_ptr(), off.ctypes.data, count,
                                  sa_out.data_ptr() if N else None,
                                  workspace.data_ptr() if workspace is not None else None,

@@ -63,7 +63,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 const char *const KERNEL_RANGE[SA_K_CLASSES] = {
     "gbsa:byte_hist", "gbsa:pack",     "gbsa:digit_hist", "gbsa:plan",     "gbsa:onesweep",
     "gbsa:rename",    "gbsa:gather",   "gbsa:output",     "gbsa:refine",   "gbsa:scatter",
-    "gbsa:classify",  "gbsa:apply",    "gbsa:bucket"};
+    "gbsa:classify",  "gbsa:apply",    "gbsa:bucket",     "gbsa:reorder"};
 
 struct NvtxRange {
   bool open = true;
@@ -920,6 +920,75 @@ struct Build {
     return SA_OK;
   }
 
+  // The groups of the active list `cur` (hc: its counts) copied to the
+  // other buffer set in order of their smallest member position, then
+  // classified again (large groups, refine tile map); hc is re-read.
+  sa_status reorder_groups(int cur, HostCtrl &hc) {
+    const uint32_t G = hc.g_next(), m = hc.m_next();
+    const int nxt = cur ^ 1;
+    const int sms = sm_count();
+    // Buffers: the records go to the update queue (free now, 8 N bytes >=
+    // 16 G); after the sort only its order (the final value buffer) is
+    // needed, so both key buffers are free: the records in the new order
+    // go to one, the sizes and scan sums to the other.
+    uint4 *info = reinterpret_cast<uint4 *>(upd);
+    sa_status s = launch(SA_K_REORDER, 0, 8ull * m + 44ull * G, [&] {
+      return launch_group_minpos(act[cur], gstart[cur], gname[cur], ghead[cur], G, ka, va, info,
+                                 sms, st);
+    });
+    if (s != SA_OK) return s;
+    bytes += 8ull * m + 44ull * G;
+    // By the 32 position bits (constant digits skipped); the order is in the
+    // plan's final value buffer.
+    s = sort(G, spec_for(32));
+    if (s != SA_OK) return s;
+    uint4 *info_new = reinterpret_cast<uint4 *>(ka);
+    uint32_t *sizes = reinterpret_cast<uint32_t *>(kb);
+    uint32_t *sums = sizes + G;
+    if (2ull * G > N || inclusive_scan_sums_words(G) + G > 2ull * N) return SA_ERR_INTERNAL;
+    s = launch(SA_K_REORDER, 1, 40ull * G, [&] {
+      return launch_group_sizes(plan, info, G, info_new, sizes, ctrl, sms, st);
+    });
+    if (s != SA_OK) return s;
+    s = launch(SA_K_REORDER, 2, 8ull * G,
+               [&] { return launch_inclusive_scan(sizes, sizes, G, sums, st); });
+    if (s != SA_OK) return s;
+    RegroupArgs ra{};
+    ra.info = info_new;
+    ra.act_in = act[cur];
+    ra.ends = sizes;
+    ra.G = G;
+    ra.m = m;
+    ra.act_out = act[nxt];
+    ra.gstart_out = gstart[nxt];
+    ra.gname_out = gname[nxt];
+    ra.ghead_out = ghead[nxt];
+    ra.ctrl = ctrl;
+    s = launch(SA_K_REORDER, 3, 16ull * m + 32ull * G,
+               [&] { return launch_regroup(ra, sms, st); });
+    if (s != SA_OK) return s;
+    bytes += 40ull * G + 8ull * G + 16ull * m + 32ull * G;
+    // Every group is now a "refine" group with its final name.
+    RoundCounts rc{};
+    rc.m_s = m;
+    rc.g_s = G;
+    CK(cudaMemcpyAsync(&ctrl->rc, &rc, sizeof(rc), cudaMemcpyHostToDevice, st));
+    s = classify(nxt, G, 0);
+    if (s != SA_OK) return s;
+    HostCtrl h2{};
+    s = read_ctrl(h2);
+    if (s != SA_OK) return s;
+    const uint32_t passes = h2.passes;
+    s = flush(h2.pass_mask, 0);
+    if (s != SA_OK) return s;
+    bytes += (uint64_t)passes * 24 * G + 8ull * G;
+    h2.passes = hc.passes;
+    h2.pass_mask = hc.pass_mask;
+    h2.upd = hc.upd;
+    hc = h2;
+    return SA_OK;
+  }
+
   void record(uint32_t r, uint32_t m, const HostCtrl &hc, uint32_t kbits) {
     if (!stats || r >= SA_MAX_ROUNDS) return;
     stats->active[r] = m;
@@ -1054,6 +1123,13 @@ struct Build {
       settle(hc);
     }
     if (want_trace) CK(cudaMemcpyAsync(opt.trace_isa, isa, N * 4, cudaMemcpyDeviceToDevice, st));
+    if (hc.m_next() > 0 && opt.group_order != 2) {
+      // The later rounds read partner names through the ISA: groups in
+      // position order make those reads of neighbouring groups neighbours.
+      s = reorder_groups(cur, hc);
+      if (s != SA_OK) return s;
+      cur ^= 1;
+    }
     round0_range.end();
 
     // ---- rounds r >= 1: one doubling step each ----

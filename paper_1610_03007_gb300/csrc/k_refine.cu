@@ -465,6 +465,181 @@ __device__ void rf_tile_sort(RfSmem<BLOCK, CAP, WIDE> &S, uint32_t cnt,
   }
 }
 
+// Tiles whose groups all have at most RF_GROUP_MAX members (the pairs left
+// by long copied segments, for example) are refined group by group: each
+// thread takes its own groups of the tile's table whole -- their active
+// entries, partner names, a stable sort of at most four items in
+// registers, the subgroups and their names -- so no shared-memory sort or
+// item-wise rename runs. One block-wide scan of (survivors, surviving
+// groups, changed names) per thread places the outputs. The names are the
+// item-wise path's: a subgroup of len items starting at a in its group's
+// sorted order has the SA interval [head + a, head + a + len).
+constexpr uint32_t RF_GROUP_MAX = 4;
+
+// Exclusive sum over the block of 64-bit values (one barrier), the total in
+// `total`; `tmp` holds 2 * WARPS words and is not rewritten before the
+// next barrier.
+template <int BLOCK>
+__device__ __forceinline__ uint64_t rf_block_excl_sum64(uint64_t v, uint32_t *tmp,
+                                                        uint64_t &total) {
+  constexpr int WARPS = BLOCK / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t incl = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint64_t o = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += o;
+  }
+  if (lane == 31) {
+    tmp[2 * warp] = (uint32_t)incl;
+    tmp[2 * warp + 1] = (uint32_t)(incl >> 32);
+  }
+  __syncthreads();
+  uint64_t before = 0, all = 0;
+#pragma unroll
+  for (int w = 0; w < WARPS; ++w) {
+    const uint64_t t = ((uint64_t)tmp[2 * w + 1] << 32) | tmp[2 * w];
+    before += w < warp ? t : 0ull;
+    all += t;
+  }
+  total = all;
+  return before + incl - v;
+}
+
+__device__ __forceinline__ void cswap(uint64_t &x, uint64_t &y) {
+  const uint64_t lo = x < y ? x : y, hi = x < y ? y : x;
+  x = lo;
+  y = hi;
+}
+
+template <int BLOCK, int CAP>
+__device__ __forceinline__ void refine_tiny_groups(RfSmem<BLOCK, CAP, false> &S,
+                                                   const RefineArgs &a,
+                                                   const uint32_t (&sz)[RfCfg<BLOCK, CAP>::GPT],
+                                                   const uint32_t h) {
+  using C = RfCfg<BLOCK, CAP>;
+  constexpr int GPT = C::GPT;
+  constexpr int M = (int)RF_GROUP_MAX;
+  const int tid = threadIdx.x;
+  // Entries, then partner names of all of this thread's groups, every load
+  // issued before its use, kept in registers as (r2 << 32) | i'.
+  static_assert(M == 4, "the sorting network below orders four items");
+  uint64_t it[GPT][M];
+#pragma unroll
+  for (int r = 0; r < GPT; ++r) {
+    const uint32_t lg = tid * GPT + r;
+    const uint32_t base = sz[r] ? S.gsrc[lg] : 0u;
+#pragma unroll
+    for (int k = 0; k < M; ++k) it[r][k] = (uint32_t)k < sz[r] ? a.act[base + k] : ~0ull;
+  }
+#pragma unroll
+  for (int r = 0; r < GPT; ++r)
+#pragma unroll
+    for (int k = 0; k < M; ++k)
+      if ((uint32_t)k < sz[r]) {
+        const uint32_t ip = (uint32_t)it[r][k];
+        const uint32_t r2 = __ldg(a.isa + min((uint64_t)ip + h, a.isa_len - 1)) + 1u;
+        it[r][k] = ((uint64_t)r2 << 32) | ip;
+      }
+  uint32_t n_surv = 0, n_grp = 0, n_chg = 0;
+#pragma unroll
+  for (int r = 0; r < GPT; ++r) {
+    const uint32_t z = sz[r];
+    if (!z) continue;
+    // Sort by (partner name, position): padding (all ones) stays last, and
+    // the order among equal names, which names do not depend on, is fixed.
+    cswap(it[r][0], it[r][1]);
+    cswap(it[r][2], it[r][3]);
+    cswap(it[r][0], it[r][2]);
+    cswap(it[r][1], it[r][3]);
+    cswap(it[r][1], it[r][2]);
+    const uint32_t lg = tid * GPT + r;
+    const uint32_t head = S.ghead[lg], old = S.gname[lg];
+    uint32_t a0 = 0;
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      if ((uint32_t)k < z) {
+        const bool end = (uint32_t)k + 1 == z || (it[r][k + 1 < M ? k + 1 : k] >> 32) != (it[r][k] >> 32);
+        if (end) {  // subgroup [a0, k]
+          const uint32_t len = k + 1 - a0, lo = head + a0;
+          const uint32_t name =
+              len == 1 || a.naming != NAMES_RETAIN ? lo : (old - lo < len ? old : lo + len / 2);
+          if (len > 1) {
+            n_surv += len;
+            ++n_grp;
+          }
+          if (name != old) n_chg += len;
+          a0 = k + 1;
+        }
+      }
+    }
+  }
+  // Place the outputs: survivors (21 bits), surviving groups (21 bits) and
+  // changed names (22 bits) scanned together.
+  const uint64_t mine = (uint64_t)n_surv | ((uint64_t)n_grp << 21) | ((uint64_t)n_chg << 42);
+  uint64_t tot;
+  const uint64_t ex = rf_block_excl_sum64<BLOCK>(mine, S.tmp[0], tot);
+  if (tid == 0) {
+    const uint32_t tot_surv = (uint32_t)(tot & 0x1FFFFF), tot_grp = (uint32_t)((tot >> 21) & 0x1FFFFF);
+    const uint32_t tot_chg = (uint32_t)(tot >> 42);
+    const unsigned long long inc = ((unsigned long long)tot_grp << 32) | tot_surv;
+    const unsigned long long o =
+        inc ? atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctrl->rc.m_s), inc) : 0ull;
+    S.surv_base = (uint32_t)o;
+    S.grp_base = (uint32_t)(o >> 32);
+    S.upd_base = tot_chg ? atomicAdd(&a.ctrl->rc.upd, tot_chg) : 0u;
+  }
+  __syncthreads();
+  uint32_t run_surv = S.surv_base + (uint32_t)(ex & 0x1FFFFF);
+  uint32_t run_grp = S.grp_base + (uint32_t)((ex >> 21) & 0x1FFFFF);
+  uint32_t run_chg = S.upd_base + (uint32_t)(ex >> 42);
+#pragma unroll
+  for (int r = 0; r < GPT; ++r) {
+    const uint32_t z = sz[r];
+    if (!z) continue;
+    const uint32_t lg = tid * GPT + r;
+    const uint32_t head = S.ghead[lg], old = S.gname[lg];
+    uint32_t a0 = 0;
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      if ((uint32_t)k < z) {
+        const bool end = (uint32_t)k + 1 == z || (it[r][k + 1 < M ? k + 1 : k] >> 32) != (it[r][k] >> 32);
+        if (end) {
+          const uint32_t len = k + 1 - a0, lo = head + a0;
+          const uint32_t name =
+              len == 1 || a.naming != NAMES_RETAIN ? lo : (old - lo < len ? old : lo + len / 2);
+          if (name >= a.N) {  // never taken unless a logic error
+            raise_error(a.ctrl, ERR_INTERNAL, 15);
+            return;
+          }
+          if (len > 1) {
+            a.gstart_out[run_grp] = run_surv;
+            a.gname_out[run_grp] = name;
+            a.ghead_out[run_grp] = lo;
+          }
+#pragma unroll
+          for (int x = 0; x < M; ++x) {
+            if ((uint32_t)x >= a0 && (uint32_t)x <= (uint32_t)k) {
+              const uint32_t ip = (uint32_t)it[r][x];
+              if (ip >= a.isa_len) {  // never taken unless a logic error
+                raise_error(a.ctrl, ERR_INTERNAL, 16);
+                return;
+              }
+              if (name != old) a.upd[run_chg++] = ((uint64_t)name << 32) | ip;
+              if (len == 1)
+                a.sa[name] = local_index(ip, a.seg_off, a.S);
+              else
+                a.act_out[run_surv++] = ((uint64_t)run_grp << 32) | ip;
+            }
+          }
+          if (len > 1) ++run_grp;
+          a0 = k + 1;
+        }
+      }
+    }
+  }
+}
+
 // One refine tile (whole groups whose starts fall in the tile's window).
 // Every thread of the block calls it; all returns are block-uniform.
 template <int BLOCK, int CAP, bool WIDE>
@@ -542,6 +717,12 @@ __device__ __forceinline__ void refine_tile(RfSmem<BLOCK, CAP, WIDE> &S, const R
   }
   const uint32_t cnt = nitems;
   if (cnt == 0) return;
+  if constexpr (!WIDE && CAP <= 1024) {
+    if (S.gmax <= RF_GROUP_MAX) {  // block-uniform: every group has at most 4 members
+      refine_tiny_groups<BLOCK, CAP>(S, a, sz, h);
+      return;
+    }
+  }
   const uint32_t K = (cnt + BLOCK - 1) / BLOCK;
 
   // Load (g, i') and gather the partner names; all loads of a thread are

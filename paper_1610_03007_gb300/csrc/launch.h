@@ -291,6 +291,31 @@ cudaError_t launch_round_begin(const RoundBeginArgs &a, cudaStream_t stream);
 // Sets `loop` to 1 while suffixes are active and no error was raised.
 cudaError_t launch_round_end(const Ctrl *c, cudaGraphConditionalHandle loop, cudaStream_t stream);
 
+// ---- group order after round 0 (k_reorder.cu) -------------------------------
+// keys[g] = the smallest member position of group g, vals[g] = g,
+// info[g] = (start, size, name, head rank).
+cudaError_t launch_group_minpos(const uint64_t *act, const uint32_t *gstart, const uint32_t *gname,
+                                const uint32_t *ghead, uint32_t G, uint64_t *keys, uint32_t *vals,
+                                uint4 *info, int num_sms, cudaStream_t stream);
+// info_new[x] = info[plan->vfinal[x]], sizes[x] = its size.
+cudaError_t launch_group_sizes(const SortPlan *plan, const uint4 *info, uint32_t G,
+                               uint4 *info_new, uint32_t *sizes, Ctrl *ctrl, int num_sms,
+                               cudaStream_t stream);
+// out[i] = in[0] + .. + in[i] (may alias); sums: inclusive_scan_sums_words(m) words.
+cudaError_t launch_inclusive_scan(const uint32_t *in, uint32_t *out, uint64_t m, uint32_t *sums,
+                                  cudaStream_t stream);
+uint64_t inclusive_scan_sums_words(uint64_t m);
+struct RegroupArgs {
+  const uint4 *info;        // (start, size, name, head rank) of new group x
+  const uint64_t *act_in;   // entries in the old order
+  const uint32_t *ends;     // inclusive prefix sums of the sizes in the new order
+  uint32_t G, m;
+  uint64_t *act_out;        // entries (x << 32) | i' in the new order
+  uint32_t *gstart_out, *gname_out, *ghead_out;     // G + 1, G, G entries
+  Ctrl *ctrl;
+};
+cudaError_t launch_regroup(const RegroupArgs &a, int num_sms, cudaStream_t stream);
+
 // ---- position bucketing of ISA writes (k_bucket.cu) ------------------------
 constexpr uint32_t BUCKET_BLOCKS_MAX = 1024;
 struct BucketArgs {
