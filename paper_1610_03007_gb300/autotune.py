@@ -98,11 +98,19 @@ def _search(time_fn, coords, start):
     return best, best_ms, tried
 
 
+def widest_key(bits_per_char: int, texts: int = 1) -> int:
+    """Characters of the widest initial key: as many as fit in 64 bits
+    beside the text-id bits of a batch of `texts` texts."""
+    seg = (texts - 1).bit_length() if texts > 1 else 0
+    return (64 - seg) // max(1, bits_per_char)
+
+
 def tune(text, workspace=None, reps: int = 3) -> dict:
     """Best {sort_items, refine_shape, h0_chars, bucket_min} for this input
     (a uint8 CUDA tensor), the alphabet's bits per character, and the
     milliseconds measured for every candidate tried. Every candidate is
-    passed explicitly, so the library's current table does not interfere."""
+    passed explicitly (a 0 would mean "the library's table" and make the
+    search depend on the table it is writing)."""
     import torch
 
     import paper_1610_03007_gb300 as gbsa
@@ -113,12 +121,13 @@ def tune(text, workspace=None, reps: int = 3) -> dict:
     def run(p):
         return gbsa.sa_build_ex(text, workspace=workspace, **p)
 
-    _, _, st, _ = run(DEFAULTS)  # warm-up
+    _, _, st, _ = run(DEFAULTS)  # warm-up; gives the alphabet's bits per character
+    c0max = widest_key(st["bits_per_char"])
+    start = dict(DEFAULTS, h0_chars=c0max)
     coords = [("sort_items", SORT_ITEMS), ("refine_shape", REFINE_SHAPES),
-              ("h0_chars", [0] + key_width_candidates(st["chars_per_key"],
-                                                      st["bits_per_char"])),
+              ("h0_chars", [c0max] + key_width_candidates(c0max, st["bits_per_char"])),
               ("bucket_min", BUCKET_MINS)]
-    best, ms, tried = _search(lambda p: _median_ms(lambda: run(p), reps), coords, DEFAULTS)
+    best, ms, tried = _search(lambda p: _median_ms(lambda: run(p), reps), coords, start)
     return {"params": best, "ms": ms, "tried": tried, "bits_per_char": st["bits_per_char"]}
 
 
@@ -132,12 +141,13 @@ def tune_batched(texts, offsets, sa_out, workspace, reps: int = 1) -> dict:
         return gbsa.sa_build_batched(texts, offsets, sa_out=sa_out, workspace=workspace,
                                      stats=True, **p)
 
-    _, st = run(DEFAULTS)  # warm-up
+    _, st = run(DEFAULTS)  # warm-up; gives the alphabet's bits per character
+    c0max = widest_key(st["bits_per_char"], len(offsets) - 1)
+    start = dict(DEFAULTS, h0_chars=c0max)
     coords = [("sort_items", SORT_ITEMS),
-              ("h0_chars", [0] + key_width_candidates(st["chars_per_key"],
-                                                      st["bits_per_char"])),
+              ("h0_chars", [c0max] + key_width_candidates(c0max, st["bits_per_char"])),
               ("bucket_min", BUCKET_MINS)]
-    best, ms, tried = _search(lambda p: _median_ms(lambda: run(p), reps), coords, DEFAULTS)
+    best, ms, tried = _search(lambda p: _median_ms(lambda: run(p), reps), coords, start)
     return {"params": best, "ms": ms, "tried": tried, "bits_per_char": st["bits_per_char"]}
 
 

@@ -24,8 +24,6 @@
 namespace gbsa {
 
 constexpr int PACK_BLOCK = 256;
-constexpr int PACK_ITEMS = 8;
-constexpr int PACK_SPAN = PACK_BLOCK * PACK_ITEMS;
 // Keys of at least this many characters take the sliding fast path (for
 // short keys the per-key loads are already few, and the warp-strided stores
 // of the general path coalesce better: measured 2.89 vs 3.35 ms for 8-char
@@ -49,7 +47,7 @@ __device__ __forceinline__ void pack_hist(uint32_t (*s_hist)[RADIX], const Digit
   }
 }
 
-// One block packs PACK_SPAN consecutive keys. The 256-bin histograms of
+// One block packs PACK_BLOCK * ITEMS consecutive keys. The 256-bin histograms of
 // every radix digit of the keys (the one-sweep sort's upfront histogram)
 // are accumulated here as well, so the sort needs no separate read of the
 // keys.
@@ -58,17 +56,26 @@ __device__ __forceinline__ void pack_hist(uint32_t (*s_hist)[RADIX], const Digit
 // all in one text's non-tail range, where index j holds position j - t and
 // every key has c0 characters): the text
 // window is staged once in shared memory as dense codes, and each thread
-// builds PACK_ITEMS consecutive keys by sliding, one character shifted in
+// builds ITEMS consecutive keys by sliding, one character shifted in
 // per key. Otherwise the text of the block's first and last key is found
 // once, and each key is assembled from its own characters.
+//
+// ITEMS keys per thread: 16 where the sliding path applies (longer slides
+// amortise the c0 - 1 characters each thread reads before its first key:
+// 12.2 -> 10.5 ms for 24-character keys at 2^31), 8 otherwise (the
+// per-key path's stores coalesce better with more blocks: 1.96 vs 2.31 ms
+// for 8-character keys at 2^28).
+template <int ITEMS>
 __global__ void __launch_bounds__(PACK_BLOCK) k_pack(PackArgs a) {
+  constexpr int PACK_SPAN = PACK_BLOCK * ITEMS;
   __shared__ uint8_t s_code[RADIX];
   __shared__ uint32_t s_hist[MAX_PASSES][RADIX];
   __shared__ uint32_t s_seg[2];
   __shared__ uint8_t s_txt[PACK_SPAN + 64];
-  // Fast path: the block's keys, key x at x + x/8 (a thread's 8 consecutive
-  // keys fall in distinct banks), written out with consecutive addresses.
-  __shared__ uint64_t s_keys[PACK_SPAN + PACK_SPAN / 8];
+  // Fast path: the block's keys, key x at x + x / ITEMS (the k-th keys
+  // of a warp's threads fall in distinct banks), written out with
+  // consecutive addresses.
+  __shared__ uint64_t s_keys[PACK_SPAN + PACK_SPAN / ITEMS];
   const int tid = threadIdx.x, lane = tid & 31;
   s_code[tid] = a.code[tid];
   for (int x = tid; x < MAX_PASSES * RADIX; x += PACK_BLOCK) (&s_hist[0][0])[x] = 0;
@@ -95,34 +102,34 @@ __global__ void __launch_bounds__(PACK_BLOCK) k_pack(PackArgs a) {
     __syncthreads();
     const uint64_t mask = a.cb >= 64 ? ~0ull : ((1ull << a.cb) - 1ull);
     const uint64_t segbits = a.S > 1 ? (uint64_t)s_lo << a.cb : 0ull;
-    const uint32_t x0 = (uint32_t)tid * PACK_ITEMS;
+    const uint32_t x0 = (uint32_t)tid * ITEMS;
     uint64_t key = 0;
     if (x0 < span)
       for (uint32_t q = 0; q + 1 < a.c0; ++q) key = (key << a.b) | s_txt[x0 + q];
 #pragma unroll
-    for (int k = 0; k < PACK_ITEMS; ++k) {
+    for (int k = 0; k < ITEMS; ++k) {
       const uint32_t x = x0 + k;
       const bool valid = x < span;
       uint64_t out = 0;
       if (valid) {
         key = ((key << a.b) | s_txt[x + a.c0 - 1]) & mask;
         out = key | segbits;
-        s_keys[x + (x >> 3)] = out;
+        s_keys[x + x / ITEMS] = out;
       }
       pack_hist(s_hist, a.spec, out, valid, lane, a.top_only != 0);
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < PACK_ITEMS; ++k) {
+    for (int k = 0; k < ITEMS; ++k) {
       const uint32_t x = (uint32_t)k * PACK_BLOCK + tid;
       if (x < span) {
-        a.keys[j0 + x] = s_keys[x + (x >> 3)];
+        a.keys[j0 + x] = s_keys[x + x / ITEMS];
         a.vals[j0 + x] = (uint32_t)(pos0 + x) + s_lo;
       }
     }
   } else {
 #pragma unroll
-    for (int k = 0; k < PACK_ITEMS; ++k) {
+    for (int k = 0; k < ITEMS; ++k) {
       const uint64_t j64 = j0 + (uint64_t)k * PACK_BLOCK + tid;
       const bool valid = j64 < a.N;
       uint64_t key = 0;
@@ -200,8 +207,13 @@ __global__ void __launch_bounds__(RADIX) k_pack_hist_fixup(PackArgs a) {
 
 cudaError_t launch_pack(const PackArgs &a, cudaStream_t stream) {
   if (a.N == 0) return cudaSuccess;
-  const uint64_t grid = ((uint64_t)a.N + PACK_SPAN - 1) / PACK_SPAN;
-  k_pack<<<(unsigned)grid, PACK_BLOCK, 0, stream>>>(a);
+  if (a.c0 >= PACK_SLIDE_MIN) {
+    const uint64_t span = PACK_BLOCK * 16;
+    k_pack<16><<<(unsigned)((a.N + span - 1) / span), PACK_BLOCK, 0, stream>>>(a);
+  } else {
+    const uint64_t span = PACK_BLOCK * 8;
+    k_pack<8><<<(unsigned)((a.N + span - 1) / span), PACK_BLOCK, 0, stream>>>(a);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !a.top_only) return e;
   k_pack_hist_fixup<<<1, RADIX, 0, stream>>>(a);

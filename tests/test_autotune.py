@@ -99,6 +99,14 @@ def test_committed_table_parses_if_present():
         assert p["sort_items"] in (0, 8, 12, 16) and 0 <= p["refine_shape"] <= 4
 
 
+def test_widest_key_is_explicit():
+    """The tuner passes the full key width as a number (0 would mean "the
+    library's table" to the library)."""
+    assert autotune.widest_key(2) == 32 and autotune.widest_key(8) == 8
+    assert autotune.widest_key(2, 4096) == 26 and autotune.widest_key(8, 2) == 7
+    assert autotune.widest_key(1, 1) == 64
+
+
 def test_buckets():
     assert autotune.bucket(1) == 0
     assert autotune.bucket(1 << 28) == 28
