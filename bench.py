@@ -289,7 +289,7 @@ def _roofline(kern, workload):
             "ms_per_launch": d["ms"] / max(d["launches"], 1)}
 
 
-def measure_single(cfg, steps, warmup, local, pg=None, clocks=False, h0_chars=0):
+def measure_single(cfg, steps, warmup, local, pg=None, clocks=False, h0_chars=0, sort_items=0):
     """K timed builds of one seeded text resident in HBM, with the library's
     per-launch CUDA events (sa_options.profile) on the same stream; returns
     the timings, the per-kernel table and the device text/workspace."""
@@ -307,7 +307,7 @@ def measure_single(cfg, steps, warmup, local, pg=None, clocks=False, h0_chars=0)
 
     def step(profile):
         st = gbsa.Stats()
-        opt = gbsa.Options(profile=1 if profile else 0, h0_chars=h0_chars)
+        opt = gbsa.Options(profile=1 if profile else 0, h0_chars=h0_chars, sort_items=sort_items)
         rc = lib.sa_build_ex(text.data_ptr(), n, sa.data_ptr(), None, ws.data_ptr(), ws.numel(),
                              gbsa.ctypes.byref(opt), gbsa.ctypes.byref(st), stream.cuda_stream)
         if rc != 0:
@@ -569,7 +569,10 @@ def run_plain(args):
         cfg["workload"] += f" (n = {args.n})"
     if args.h0:
         cfg["workload"] += f" ({args.h0} characters per initial key)"
-    m = measure_single(cfg, args.steps, args.warmup, local, clocks=True, h0_chars=args.h0)
+    if args.sort_items:
+        cfg["workload"] += f" ({args.sort_items} keys per thread in the radix passes)"
+    m = measure_single(cfg, args.steps, args.warmup, local, clocks=True, h0_chars=args.h0,
+                       sort_items=args.sort_items)
     rep = single_report(m, cfg, args.steps, 1)
     if not args.build_only and cfg["recipe"] == "zipf_repeats":
         rep.update(cfg2_extras(m, args.steps))
@@ -836,6 +839,9 @@ def main():
     ap.add_argument("--h0", type=int, default=0,
                     help="plain workload: characters per initial key (0: the library's choice), "
                          "e.g. to profile a smaller text with the full-size key width")
+    ap.add_argument("--sort-items", type=int, default=0,
+                    help="plain workload: keys per thread of the radix passes (8, 12, 16; "
+                         "0: the library's choice)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--headline-only", action="store_true",
                     help="suite: the headline line without the nested workloads")

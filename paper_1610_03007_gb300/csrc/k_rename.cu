@@ -6,7 +6,10 @@
 //    than c0 characters left; see k_pack.cu) and the item after it also get
 //    f = 1, so each tail is a group of its own.
 //  - Head rank (PrefixSum with max, Algorithm 1): s_j = max over j' <= j of
-//    (f_j' ? j' : 0), a device-wide max-scan with decoupled look-back.
+//    (f_j' ? j' : 0). It is read only where f_j = 1 (a unique item, or the
+//    head of a surviving group, whose members take their names from the
+//    head's record in k_classify / k_apply_names), and there s_j = j, so the
+//    max-scan itself is never materialised.
 //  - New name (NameDiscarding, Algorithms 5/6, in head-rank form): round 0
 //    new_j = s_j; later rounds new_j = r + (s_j - group start), stored as
 //    base[g] + s_j with base[g] = r - group start of group g (this kernel
@@ -39,6 +42,11 @@ constexpr int RN_BLOCK = 256;
 constexpr int RN_ITEMS = GBSA_RN_ITEMS;
 constexpr int RN_TILE = RN_BLOCK * RN_ITEMS;
 constexpr int RN_WARPS = RN_BLOCK / 32;
+#ifndef GBSA_RN_LB_WINDOW
+#define GBSA_RN_LB_WINDOW 4
+#endif
+// Predecessors read per look-back round trip.
+constexpr int RN_LB_WINDOW = GBSA_RN_LB_WINDOW;
 static_assert(RN_TILE == RENAME_TILE, "tile size mismatch");
 
 struct RnSmem {
@@ -50,7 +58,7 @@ struct RnSmem {
   uint64_t prev_key, next_key;
   uint32_t prev_val, next_val;
   uint32_t tmp[RN_WARPS + 1];
-  uint32_t carry[3];
+  uint32_t carry[2];
   uint32_t tile, bail, upd_local, upd_base;
 };
 
@@ -130,12 +138,11 @@ __device__ __forceinline__ bool rename_tile(RnSmem &S, const RenameArgs &a, cons
     if (SEC && !b) b = SEC[j] != SEC[j - 1];
     f[k] = b;
   }
-  uint32_t th_head = 0, th_surv = 0, th_hs = 0, th_uniq = 0;
+  uint32_t th_surv = 0, th_hs = 0, th_uniq = 0;
 #pragma unroll
   for (int k = 0; k < RN_ITEMS; ++k) {
     if (l0 + k < count) {
       const bool uniq = f[k] && f[k + 1];
-      if (f[k]) th_head = base + l0 + k;
       if (!uniq) {
         ++th_surv;
         if (f[k]) ++th_hs;
@@ -147,111 +154,131 @@ __device__ __forceinline__ bool rename_tile(RnSmem &S, const RenameArgs &a, cons
   // ISA entries of new unique suffixes are queued (in any order) and applied
   // only when a later round, the ISA output or the trace reads them.
   const uint32_t my_upd = th_uniq ? atomicAdd(&S.upd_local, th_uniq) : 0u;
-  uint32_t tot_head, tot_surv, tot_hs;
-  const uint32_t ex_head = block_exclusive<RN_BLOCK>(th_head, OpMax(), 0u, S.tmp, tot_head);
+  uint32_t tot_surv, tot_hs;
   const uint32_t ex_surv = block_exclusive<RN_BLOCK>(th_surv, OpAdd(), 0u, S.tmp, tot_surv);
   const uint32_t ex_hs = block_exclusive<RN_BLOCK>(th_hs, OpAdd(), 0u, S.tmp, tot_hs);
 
-  // Three device-wide scans: max head position, survivors, group heads.
-  if ((tid & 31) == 0 && tid < 96) {
-    const uint32_t which = tid >> 5;
-    const uint32_t agg = which == 0 ? tot_head : (which == 1 ? tot_surv : tot_hs);
-    uint64_t *st = a.status + (uint64_t)tile * 3 + which;
-    uint32_t carry = 0;
-    bool ok = true;
-    if (tile == 0) {
-      status_store(st, status_word(epoch, ST_INC, agg));
-    } else {
-      status_store(st, status_word(epoch, ST_AGG, agg));
-      if (which == 0)
-        ok = look_back4(a.status, 3, which, tile, epoch, OpMax(), carry, a.ctrl, a.spin_limit);
-      else
-        ok = look_back4(a.status, 3, which, tile, epoch, OpAdd(), carry, a.ctrl, a.spin_limit);
-      if (ok) {
-        const uint32_t inc = which == 0 ? (carry > agg ? carry : agg) : carry + agg;
-        status_store(st, status_word(epoch, ST_INC, inc));
-      }
-    }
-    if (!ok) S.bail = 1;
-    S.carry[which] = carry;
-  }
-  __syncthreads();
-  if (S.bail) return false;
-  if (tid == 0) {
-    if (base + count == m) {
-      a.cnt_out[0] = S.carry[1] + tot_surv;
-      a.cnt_out[1] = S.carry[2] + tot_hs;
-    }
-    S.upd_base = S.upd_local ? atomicAdd(&a.ctrl->rc.upd, S.upd_local) : 0u;
-  }
+  // The tile's survivors and surviving groups, published for the device-wide
+  // sums (decoupled look-back); the look-back itself runs after the staging
+  // below, which needs only tile-local offsets.
+  uint64_t *st_tile = a.status + (uint64_t)tile * 2;
+  if (tid < 2) status_store(st_tile + tid, status_word(epoch, tile == 0 ? ST_INC : ST_AGG,
+                                                        tid == 0 ? tot_surv : tot_hs));
+  if (tid == 0) S.upd_base = S.upd_local ? atomicAdd(&a.ctrl->rc.upd, S.upd_local) : 0u;
   // Outputs are staged in shared memory and written with consecutive
   // addresses afterwards: queued updates in the keys area, survivors' list
-  // entries in `surv`, and (round 0, where a unique item's name is its own
-  // position in the sorted order) SA entries by tile index in the vals area.
+  // entries (with tile-local group ordinals) in `surv`, and (round 0, where a
+  // unique item's name is its own position in the sorted order) SA entries
+  // by tile index in the vals area. Every item's new group starts at a head
+  // (f = 1) whose head rank is that head's own sorted index, so no head rank
+  // from an earlier tile is needed.
   uint64_t *st_upd = S.keys;
   uint32_t *st_sa = S.vals;
   if (a.round0)
     for (uint32_t e = tid; e < count; e += RN_BLOCK) st_sa[e] = NO_NAME;
   __syncthreads();
-  const uint32_t m_off = __ldg(a.off_in), g_off = __ldg(a.off_in + 1);
-
-  uint32_t run_upd = my_upd;
-  uint32_t run_head = S.carry[0] > ex_head ? S.carry[0] : ex_head;
-  uint32_t run_surv = ex_surv;
-  uint32_t run_hs = g_off + S.carry[2] + ex_hs;
-  const uint32_t surv0 = m_off + S.carry[1];
+  {
+    uint32_t run_upd = my_upd, run_surv = ex_surv, run_hs = ex_hs;
 #pragma unroll
-  for (int k = 0; k < RN_ITEMS; ++k) {
-    if (l0 + k < count) {
-      const uint32_t j = base + l0 + k;
-      if (f[k]) run_head = j;
-      const uint64_t kk = key[k + 1];
-      const uint32_t ip = val[k + 1];
-      const uint32_t g = a.round0 ? 0u : (uint32_t)(kk >> a.W);
-      if (!a.round0 && g >= g_in) {  // never taken unless a logic error
-        raise_error(a.ctrl, ERR_INTERNAL, 4);
-        continue;
-      }
-      // Head rank of the item's new group (the start of its SA interval).
-      const uint32_t head = a.round0 ? run_head : __ldg(a.base_in + g) + run_head;
-      if (head >= a.N || ip >= a.isa_len) {  // never taken unless a logic error
-        raise_error(a.ctrl, ERR_INTERNAL, 3);
-        continue;
-      }
-      if (f[k] && f[k + 1]) {
-        // Unique: its name is its rank, final (Algorithm 5 discards it). SA
-        // holds the index local to the suffix's own text.
-        st_upd[run_upd++] = ((uint64_t)head << 32) | ip;
-        uint32_t local = ip;
-        if (a.S > 1) {
-          if (a.round0) {
-            const uint32_t s = (uint32_t)(kk >> a.cb);
-            local = ip - (__ldg(a.seg_off + s) + s);
-          } else {
-            local = local_index(ip, a.seg_off, a.S);
+    for (int k = 0; k < RN_ITEMS; ++k) {
+      if (l0 + k < count) {
+        const uint32_t j = base + l0 + k;
+        const uint64_t kk = key[k + 1];
+        const uint32_t ip = val[k + 1];
+        if (ip >= a.isa_len) {  // never taken unless a logic error
+          raise_error(a.ctrl, ERR_INTERNAL, 3);
+          continue;
+        }
+        if (f[k] && f[k + 1]) {
+          // Unique: its name is its rank, final (Algorithm 5 discards it). SA
+          // holds the index local to the suffix's own text.
+          const uint32_t g = a.round0 ? 0u : (uint32_t)(kk >> a.W);
+          if (!a.round0 && g >= g_in) {  // never taken unless a logic error
+            raise_error(a.ctrl, ERR_INTERNAL, 4);
+            continue;
           }
+          const uint32_t head = a.round0 ? j : __ldg(a.base_in + g) + j;
+          if (head >= a.N) {  // never taken unless a logic error
+            raise_error(a.ctrl, ERR_INTERNAL, 3);
+            continue;
+          }
+          st_upd[run_upd++] = ((uint64_t)head << 32) | ip;
+          uint32_t local = ip;
+          if (a.S > 1) {
+            if (a.round0) {
+              const uint32_t s = (uint32_t)(kk >> a.cb);
+              local = ip - (__ldg(a.seg_off + s) + s);
+            } else {
+              local = local_index(ip, a.seg_off, a.S);
+            }
+          }
+          if (a.round0)
+            st_sa[l0 + k] = local;  // head == j here
+          else
+            a.sa[head] = local;
+        } else {
+          // Survivors get their names, and their ISA entries, once the group
+          // sizes are known (k_classify, k_apply_names).
+          if (f[k]) ++run_hs;
+          S.surv[run_surv++] = ((uint64_t)(run_hs - 1) << 32) | ip;
         }
-        if (a.round0)
-          st_sa[l0 + k] = local;  // head == j here
-        else
-          a.sa[head] = local;
-      } else {
-        // Survivors get their names, and their ISA entries, once the group
-        // sizes are known (k_classify, k_apply_names).
+      }
+    }
+  }
+
+  // Device-wide offsets of the tile's survivors and groups.
+  if (tid < 2) {
+    uint32_t carry = 0;
+    bool ok = true;
+    if (tile > 0) {
+      ok = look_back_w<RN_LB_WINDOW>(a.status, 2, tid, tile, epoch, OpAdd(), carry, a.ctrl,
+                                     a.spin_limit);
+      if (ok)
+        status_store(st_tile + tid,
+                     status_word(epoch, ST_INC, carry + (tid == 0 ? tot_surv : tot_hs)));
+    }
+    if (!ok) S.bail = 1;
+    S.carry[tid] = carry;
+  }
+  __syncthreads();
+  if (S.bail) return false;
+  const uint32_t m_off = __ldg(a.off_in), g_off = __ldg(a.off_in + 1);
+  const uint32_t surv0 = m_off + S.carry[0], grp0 = g_off + S.carry[1];
+  if (tid == 0 && base + count == m) {
+    a.cnt_out[0] = S.carry[0] + tot_surv;
+    a.cnt_out[1] = S.carry[1] + tot_hs;
+  }
+  // Surviving groups: start in the next list, head rank, parent's name.
+  {
+    uint32_t run_surv = ex_surv, run_hs = ex_hs;
+#pragma unroll
+    for (int k = 0; k < RN_ITEMS; ++k) {
+      if (l0 + k < count && !(f[k] && f[k + 1])) {
         if (f[k]) {
+          const uint32_t j = base + l0 + k;
+          const uint32_t g = a.round0 ? 0u : (uint32_t)(key[k + 1] >> a.W);
+          if (!a.round0 && g >= g_in) {  // never taken unless a logic error
+            raise_error(a.ctrl, ERR_INTERNAL, 4);
+            continue;
+          }
+          const uint32_t head = a.round0 ? j : __ldg(a.base_in + g) + j;
+          if (head >= a.N) {  // never taken unless a logic error
+            raise_error(a.ctrl, ERR_INTERNAL, 3);
+            continue;
+          }
+          const uint32_t o = grp0 + run_hs;
+          a.gstart_out[o] = surv0 + run_surv;
+          a.ghead_out[o] = head;
+          a.gold_out[o] = a.round0 ? NO_NAME : __ldg(a.old_in + g);
           ++run_hs;
-          a.gstart_out[run_hs - 1] = surv0 + run_surv;
-          a.ghead_out[run_hs - 1] = head;
-          a.gold_out[run_hs - 1] = a.round0 ? NO_NAME : __ldg(a.old_in + g);
         }
-        S.surv[run_surv] = ((uint64_t)(run_hs - 1) << 32) | ip;
         ++run_surv;
       }
     }
   }
-  __syncthreads();
   for (uint32_t e = tid; e < S.upd_local; e += RN_BLOCK) a.upd[S.upd_base + e] = st_upd[e];
-  for (uint32_t e = tid; e < tot_surv; e += RN_BLOCK) a.act_out[surv0 + e] = S.surv[e];
+  const uint64_t gshift = (uint64_t)grp0 << 32;
+  for (uint32_t e = tid; e < tot_surv; e += RN_BLOCK) a.act_out[surv0 + e] = S.surv[e] + gshift;
   if (a.round0) {
     for (uint32_t e = tid; e < count; e += RN_BLOCK) {
       const uint32_t v = st_sa[e];

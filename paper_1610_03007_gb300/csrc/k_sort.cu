@@ -11,8 +11,8 @@
 //      position whose keys all share one value is skipped; the source and
 //      destination buffers of the remaining passes ping-pong A <-> B.
 //   3. k_onesweep per kept pass: each tile of 256 x 8..16 items ranks its items by
-//      digit (warp ballots give the peers of equal digit, so the local order
-//      is stable), publishes its per-digit counts, finds its per-digit
+//      digit (peers of equal digit by shared-memory masks or match.any, so
+//      the local order is stable), publishes its per-digit counts, finds its per-digit
 //      global offsets by decoupled look-back over the preceding tiles, stages
 //      the tile in shared memory in digit order and writes each digit run
 //      with consecutive addresses.
@@ -177,23 +177,13 @@ static_assert(OS_BLOCK == RADIX, "one thread per digit");
 // per digit thread).
 constexpr int LB_WINDOW = GBSA_LB_WINDOW;
 
-// GBSA_OS_ALIAS = 1: the per-warp peer masks live in the first 8 KB of the
-// key buffer while the tile is ranked (its keys are in registers then), so
-// a 16-key tile needs 55 KB instead of 63 and four blocks fit per SM.
-#ifndef GBSA_OS_ALIAS
-#define GBSA_OS_ALIAS 0
-#endif
-constexpr bool OS_ALIAS = GBSA_OS_ALIAS != 0;
-
 template <int OS_ITEMS>
 struct OsSmem {
   static constexpr int OS_TILE = OS_BLOCK * OS_ITEMS;
   uint64_t keys[OS_TILE];           // tile in input order, then in digit order
   uint32_t vals[OS_TILE];
-  uint32_t match[OS_ALIAS ? 1 : OS_WARPS][RADIX];  // per-warp peer masks (zero between uses)
-  uint16_t whist[OS_WARPS][RADIX];  // per-warp counts, then per-warp prefixes
-  uint32_t start[RADIX];            // tile-local start of each digit run
-  uint32_t count[RADIX];            // the tile's count of each digit (early, by atomics)
+  uint32_t match[OS_WARPS][RADIX];  // per-warp peer masks (zero between uses)
+  uint16_t whist[OS_WARPS][RADIX];  // per-warp counts, then each warp's first slot per digit
   uint32_t goff[RADIX];             // global index of a run = goff + local index
   uint32_t tmp[OS_WARPS + 1];
   uint32_t tile;
@@ -205,8 +195,7 @@ struct OsSmem {
 // blocks per SM (~62 KB of shared memory each), 12 four, 8 five; registers
 // are capped to match.
 template <int OS_ITEMS, bool PERSIST>
-__global__ void __launch_bounds__(OS_BLOCK, OS_ITEMS >= 16 ? (OS_ALIAS ? 4 : 3)
-                                                      : (OS_ITEMS >= 12 ? 4 : 5))
+__global__ void __launch_bounds__(OS_BLOCK, OS_ITEMS >= 16 ? 3 : (OS_ITEMS >= 12 ? 4 : 5))
     k_onesweep(PassArgs a) {
   constexpr int OS_TILE = OS_BLOCK * OS_ITEMS;
   extern __shared__ __align__(128) uint8_t smem_raw[];
@@ -240,9 +229,8 @@ __global__ void __launch_bounds__(OS_BLOCK, OS_ITEMS >= 16 ? (OS_ALIAS ? 4 : 3)
     }
     for (int x = tid; x < OS_WARPS * RADIX; x += OS_BLOCK) {
       (&S.whist[0][0])[x] = 0;
-      if (!OS_ALIAS) (&S.match[0][0])[x] = 0u;
+      (&S.match[0][0])[x] = 0u;
     }
-    S.count[tid] = 0u;
     __syncthreads();
     if (S.bail || S.tile >= tiles) return;
     const uint32_t tile = S.tile;
@@ -284,33 +272,13 @@ __global__ void __launch_bounds__(OS_BLOCK, OS_ITEMS >= 16 ? (OS_ALIAS ? 4 : 3)
       const uint32_t li = warp * (32 * OS_ITEMS) + k * 32 + lane;
       key[k] = li < count ? S.keys[li] : ~0ull;
     }
-    // Early counts: the tile's digit histogram by shared-memory atomics
-    // (independent, so cheap), published before the ranking so that the
-    // successors' look-backs find this tile's aggregate while it ranks.
-#pragma unroll
-    for (int k = 0; k < OS_ITEMS; ++k) {
-      const uint32_t li = warp * (32 * OS_ITEMS) + k * 32 + lane;
-      if (li < count) atomicAdd(&S.count[digit_of(key[k], shift, bits)], 1u);
-    }
-    __syncthreads();
     const uint32_t d = tid;  // thread d owns digit d and its status word
-    const uint32_t mine = S.count[d];
     uint64_t *st = a.status + (uint64_t)tile * RADIX + d;
-    if (a.inject && tile == 0) {
-      // Test hook: this tile never publishes, so the next tile's wait expires.
-      if (d == 0) S.bail = 1;
-    } else {
-      status_store(st, status_word(epoch, tile == 0 ? ST_INC : ST_AGG, mine));
-    }
 
     // Rank within the tile: stable, by per-warp peers and counts (peers by
     // match.any on the plan's low-entropy passes, else by the masks).
     uint16_t *wh = S.whist[warp];
-    uint32_t *mt = OS_ALIAS ? reinterpret_cast<uint32_t *>(S.keys) + warp * RADIX : S.match[warp];
-    if (OS_ALIAS) {  // every key was read into registers before the barrier above
-      for (int x = lane; x < RADIX; x += 32) mt[x] = 0u;
-      __syncwarp();
-    }
+    uint32_t *mt = S.match[warp];
     const uint32_t lt = lanemask_lt();
     if ((a.plan->match_mask >> a.p) & 1u) {
 #pragma unroll
@@ -323,7 +291,10 @@ __global__ void __launch_bounds__(OS_BLOCK, OS_ITEMS >= 16 ? (OS_ALIAS ? 4 : 3)
     }
     __syncthreads();
 
-    // Thread d: counts of digit d per warp -> per-warp exclusive prefixes.
+    // Thread d: counts of digit d per warp -> per-warp exclusive prefixes;
+    // their sum is the tile's count of digit d, published now (taking the
+    // counts from the ranking instead of by one shared-memory atomic per key
+    // before it measured 6 % faster on DNA: the atomics collide on banks).
     uint32_t total = 0;
 #pragma unroll
     for (int w = 0; w < OS_WARPS; ++w) {
@@ -331,11 +302,44 @@ __global__ void __launch_bounds__(OS_BLOCK, OS_ITEMS >= 16 ? (OS_ALIAS ? 4 : 3)
       S.whist[w][d] = (uint16_t)total;
       total += c;
     }
+    const uint32_t mine = total;
+    if (a.inject && tile == 0) {
+      // Test hook: this tile never publishes, so the next tile's wait expires.
+      if (d == 0) S.bail = 1;
+    } else {
+      status_store(st, status_word(epoch, tile == 0 ? ST_INC : ST_AGG, mine));
+    }
     uint32_t tile_total;
     const uint32_t start = block_exclusive<OS_BLOCK>(total, OpAdd(), 0u, S.tmp, tile_total);
-    S.start[d] = start;
+    // Each warp's first slot per digit = run start + warp prefix (< 2^16:
+    // a tile holds at most 4096 keys), so placing a key takes one
+    // digit-indexed load.
+#pragma unroll
+    for (int w = 0; w < OS_WARPS; ++w) S.whist[w][d] = (uint16_t)(S.whist[w][d] + start);
+    __syncthreads();
 
-    // Look back over the predecessors (their aggregates were published early).
+    // Permute the tile into digit order in place (every key of the input
+    // order is in registers since the ranking), values after every read of
+    // their input order. This needs no global offsets, so it runs before
+    // the look-back: the predecessors get that much longer to publish.
+#pragma unroll
+    for (int k = 0; k < OS_ITEMS; ++k) {
+      const uint32_t li = warp * (32 * OS_ITEMS) + k * 32 + lane;
+      const uint32_t dk = li < count ? digit_of(key[k], shift, bits) : dmax;
+      pos[k] += S.whist[warp][dk];
+      S.keys[pos[k]] = key[k];
+    }
+    uint32_t val[OS_ITEMS];
+#pragma unroll
+    for (int k = 0; k < OS_ITEMS; ++k) {
+      const uint32_t li = warp * (32 * OS_ITEMS) + k * 32 + lane;
+      val[k] = li < count ? S.vals[li] : 0u;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < OS_ITEMS; ++k) S.vals[pos[k]] = val[k];
+
+    // Look back over the predecessors.
     if (!S.bail) {
       if (tile == 0) {
         S.goff[d] = a.digit_base[d] - start;
@@ -353,26 +357,7 @@ __global__ void __launch_bounds__(OS_BLOCK, OS_ITEMS >= 16 ? (OS_ALIAS ? 4 : 3)
     __syncthreads();
     if (S.bail) return;
 
-    // Permute the tile into digit order in place (every read of the input
-    // order happened before the barrier above), then write each digit run
-    // with consecutive addresses.
-#pragma unroll
-    for (int k = 0; k < OS_ITEMS; ++k) {
-      const uint32_t li = warp * (32 * OS_ITEMS) + k * 32 + lane;
-      const uint32_t dk = li < count ? digit_of(key[k], shift, bits) : dmax;
-      pos[k] += S.start[dk] + S.whist[warp][dk];
-      S.keys[pos[k]] = key[k];
-    }
-    uint32_t val[OS_ITEMS];
-#pragma unroll
-    for (int k = 0; k < OS_ITEMS; ++k) {
-      const uint32_t li = warp * (32 * OS_ITEMS) + k * 32 + lane;
-      val[k] = li < count ? S.vals[li] : 0u;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < OS_ITEMS; ++k) S.vals[pos[k]] = val[k];
-    __syncthreads();
+    // Write each digit run with consecutive addresses.
 #pragma unroll
     for (int k = 0; k < OS_ITEMS; ++k) {
       const uint32_t q = k * OS_BLOCK + tid;

@@ -115,7 +115,7 @@ struct RenameArgs {
   uint32_t *gold_out;        // name of its parent group (NO_NAME in round 0)
   const uint32_t *off_in;    // device: [survivor offset, group offset] of the output
   uint32_t *cnt_out;         // device: [survivors, groups] written by the last tile
-  uint64_t *status;          // >= 3 * tiles words
+  uint64_t *status;          // >= 2 * tiles words
   uint32_t epoch;
   uint32_t *tile_ctr;
   Ctrl *ctrl;
