@@ -129,6 +129,15 @@ typedef struct {
    * order (as round 0 leaves them). Same SA and ISA either way: a round
    * needs each group contiguous, not in any order (names are ranks). */
   uint32_t group_order;
+  /* Where round 0's initial keys (Algorithm 1's initial names, c0
+   * characters each) are formed: 0 = the library chooses (as 1 whenever it
+   * applies), 1 = inside the first radix pass, which reads the text and
+   * writes the keys once sorted by their lowest digit, so no packed copy is
+   * written and read back (one text whose digits hold whole characters:
+   * 1, 2, 4 or 8 bits per character and c0 * bits a multiple of 8; else as
+   * 2), 2 = by a separate pass that writes every key and position first.
+   * Any other value: SA_ERR_INVALID_ARG. Same SA and ISA either way. */
+  uint32_t initial_keys;
 } sa_options;
 
 /* Tuned build parameters (the autotuner's table, see sa_tuning_set): each

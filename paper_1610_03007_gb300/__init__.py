@@ -49,7 +49,7 @@ class Options(ctypes.Structure):
                 ("refine_shape", ctypes.c_uint32), ("sort_items", ctypes.c_uint32),
                 ("profile", ctypes.c_uint32), ("multiplier", ctypes.c_uint32),
                 ("bucket_min", ctypes.c_uint32), ("device_rounds", ctypes.c_uint32),
-                ("group_order", ctypes.c_uint32)]
+                ("group_order", ctypes.c_uint32), ("initial_keys", ctypes.c_uint32)]
 
 
 class Tuned(ctypes.Structure):
@@ -278,11 +278,12 @@ def sa_build(text, sa_out=None, stream=None):
 def sa_build_ex(text, *, isa=False, workspace=None, h0_chars=0, spin_limit=0,
                 inject_stall=0, trace_cap=0, paper_names=False, refine_shape=0, sort_items=0,
                 profile=False, multiplier=0, bucket_min=0, device_rounds=0, group_order=0,
-                stream=None):
+                initial_keys=0, stream=None):
     """sa_build with options. Returns (sa, isa or None, stats dict, trace or None).
 
     multiplier: growth factor a of the resolved prefix per round (0 or 2:
-    doubling; 3, 4: tripling, quadrupling).
+    doubling; 3, 4: tripling, quadrupling). initial_keys: 0 or 1 = formed
+    inside the first radix pass where that applies, 2 = by a separate pack.
 
     workspace: a uint8 CUDA tensor of at least workspace_bytes(n) bytes, or
     None to let torch's caching allocator provide one."""
@@ -300,7 +301,7 @@ def sa_build_ex(text, *, isa=False, workspace=None, h0_chars=0, spin_limit=0,
     opt = Options(h0_chars, spin_limit, inject_stall,
                   trace.data_ptr() if trace is not None and n else None, trace_cap,
                   1 if paper_names else 0, refine_shape, sort_items, 1 if profile else 0,
-                  multiplier, bucket_min, device_rounds, group_order)
+                  multiplier, bucket_min, device_rounds, group_order, initial_keys)
     st = Stats()
     rc = lib.sa_build_ex(t.data_ptr(), n, sa.data_ptr() if n else None,
                          isa_t.data_ptr() if isa_t is not None and n else None,

@@ -373,7 +373,10 @@ struct Build {
   // device plan says (plan->kfinal / vfinal).
   // chain 1: the first of the two sorts of an a-tuple round (its kept
   // passes are copied to pm1 afterwards; profile records tag pass + 32).
-  sa_status sort(uint32_t m, const DigitSpec &spec, bool hist_ready = false, int chain = 0) {
+  // from_text (round 0, one text): pass 0 builds the keys from the text
+  // (the pack wrote only the histograms), so it is kept even if constant.
+  sa_status sort(uint32_t m, const DigitSpec &spec, bool hist_ready = false, int chain = 0,
+                 const PackArgs *from_text = nullptr) {
     sa_status s = SA_OK;
     if (!hist_ready) {
       CK(cudaMemsetAsync(hist, 0, (size_t)spec.P * RADIX * 4, st));
@@ -384,7 +387,8 @@ struct Build {
       bytes += 8ull * m;  // histogram read
     }
     s = launch(SA_K_PLAN, 0, (uint64_t)spec.P * RADIX * 8, [&] {
-      return launch_sort_plan(hist, dbase, spec, m, ka, kb, va, vb, plan, ctrl, st);
+      return launch_sort_plan(hist, dbase, spec, m, ka, kb, va, vb, plan, ctrl, st, nullptr,
+                              from_text != nullptr);
     });
     if (s != SA_OK) return s;
     for (uint32_t p = 0; p < spec.P; ++p) {
@@ -402,7 +406,17 @@ struct Build {
       pa.spin_limit = spin;
       pa.inject = inject_pending ? 1u : 0u;
       pa.items = sort_items;
-      s = launch(SA_K_ONESWEEP, (int)p + 32 * chain, 24ull * m,
+      uint64_t pass_bytes = 24ull * m;
+      if (from_text && p == 0) {
+        pa.text = from_text->text;
+        pa.code = from_text->code;
+        pa.b = from_text->b;
+        pa.c0 = from_text->c0;
+        pa.cb = from_text->cb;
+        pa.tails = std::min(m, from_text->c0 - 1);
+        pass_bytes = 13ull * m;  // the text read, the sorted keys and positions written
+      }
+      s = launch(SA_K_ONESWEEP, (int)p + 32 * chain, pass_bytes,
                  [&] { return launch_onesweep(pa, st); });
       if (s != SA_OK) return s;
     }
@@ -1091,12 +1105,21 @@ struct Build {
     pk.spec = spec_for(bits0);
     pk.hist = hist;
     pk.top_only = (S == 1 && 8 % b == 0 && cb % 8 == 0 && c0 <= 64 && pk.spec.P * 8 == cb) ? 1u : 0u;
+    // One text with whole-character digits: the first radix pass forms the
+    // keys from the text and the pack only counts (no packed copy written
+    // and read back).
+    const bool keys_in_pass = pk.top_only && opt.initial_keys != 2;
+    if (keys_in_pass) {
+      pk.keys = nullptr;
+      pk.vals = nullptr;
+    }
+    const uint64_t pack_bytes = keys_in_pass ? (uint64_t)N : 13ull * N;
     CK(cudaMemsetAsync(hist, 0, (size_t)pk.spec.P * RADIX * 4, st));
-    s = launch(SA_K_PACK, 0, 13ull * N, [&] { return launch_pack(pk, st); });
+    s = launch(SA_K_PACK, 0, pack_bytes, [&] { return launch_pack(pk, st); });
     if (s != SA_OK) return s;
-    bytes += 13ull * N;
+    bytes += pack_bytes;
     inject_pending = opt.inject_stall != 0;
-    s = sort(N32, pk.spec, true);
+    s = sort(N32, pk.spec, true, 0, keys_in_pass ? &pk : nullptr);
     if (s != SA_OK) return s;
     int cur = 0;  // the active list, group starts and names of this round
     s = rename(N32, true, cb, c0, 0, nullptr, nullptr, 0, cur, ctrl->zero);
@@ -1112,7 +1135,7 @@ struct Build {
     s = flush(hc.pass_mask, rb0);
     if (s != SA_OK) return s;
     record(0, m, hc, bits0);
-    bytes += (uint64_t)hc.passes * 24 * m + rb0;
+    bytes += (uint64_t)hc.passes * 24 * m - (keys_in_pass ? 11ull * m : 0ull) + rb0;
     // The unique suffixes' ISA entries are needed only by a later round, the
     // ISA output or the trace; a text resolved in round 0 skips them.
     const bool want_trace = opt.trace_isa && opt.trace_cap > 0 && S == 1;
@@ -1302,7 +1325,9 @@ sa_status check_offsets(const uint64_t *offsets, uint32_t count) {
 }
 
 bool bad_options(const sa_options *opt) {
-  return opt && opt->multiplier != 0 && (opt->multiplier < 2 || opt->multiplier > 4);
+  if (!opt) return false;
+  if (opt->multiplier != 0 && (opt->multiplier < 2 || opt->multiplier > 4)) return true;
+  return opt->initial_keys > 2;
 }
 
 sa_status run_with_workspace(Build &B, void *workspace, size_t ws_bytes) {

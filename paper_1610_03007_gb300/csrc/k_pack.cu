@@ -205,8 +205,94 @@ __global__ void __launch_bounds__(RADIX) k_pack_hist_fixup(PackArgs a) {
   }
 }
 
+// The top digit's histogram alone (keys == NULL, top_only): the g-character
+// gram (g = 8 / B) at every position p in [0, n), code 0 past the end, is
+// the top digit of the key of p whatever index holds it, so no key is
+// formed. Each thread takes 16 consecutive positions from one 16-byte load
+// (plus the next g - 1 characters from its neighbour lane) and slides the
+// gram through them in registers; per-warp counters in shared memory.
+constexpr int GRAM_PER_THREAD = 16;
+template <int B>
+__global__ void __launch_bounds__(PACK_BLOCK) k_gram_hist(PackArgs a) {
+  constexpr uint32_t G = 8 / B;
+  __shared__ uint8_t s_code[RADIX];
+  __shared__ uint32_t s_hist[PACK_BLOCK / 32][RADIX];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  s_code[tid] = a.code[tid];
+  for (int w = 0; w < PACK_BLOCK / 32; ++w) s_hist[w][tid] = 0u;
+  __syncthreads();
+  const uint64_t n = a.N;
+  const bool vec = (reinterpret_cast<uintptr_t>(a.text) & 15u) == 0;
+  const uint64_t step = (uint64_t)gridDim.x * PACK_BLOCK * GRAM_PER_THREAD;
+  // Whole warps iterate together (the shuffle below needs every lane).
+  for (uint64_t p0 = ((uint64_t)blockIdx.x * PACK_BLOCK + (tid & ~31)) * GRAM_PER_THREAD; p0 < n;
+       p0 += step) {
+    const uint64_t p = p0 + (uint64_t)lane * GRAM_PER_THREAD;
+    uint32_t w[6];  // characters p .. p + 23 (zero bytes past the end)
+    if (vec && p + 16 <= n) {
+      const uint4 v = __ldg(reinterpret_cast<const uint4 *>(a.text + p));
+      w[0] = v.x, w[1] = v.y, w[2] = v.z, w[3] = v.w;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint32_t x = 0;
+        for (int c = 3; c >= 0; --c) {
+          const uint64_t i = p + 4 * q + c;
+          x = (x << 8) | (i < n ? (uint32_t)__ldg(a.text + i) : 0u);
+        }
+        w[q] = x;
+      }
+    }
+    w[4] = __shfl_down_sync(0xffffffffu, w[0], 1);
+    w[5] = __shfl_down_sync(0xffffffffu, w[1], 1);
+    if (lane == 31) {  // the next lane's characters are the next chunk's
+#pragma unroll
+      for (int q = 4; q < 6; ++q) {
+        uint32_t x = 0;
+        for (int c = 3; c >= 0; --c) {
+          const uint64_t i = p + 4 * q + c;
+          x = (x << 8) | (i < n ? (uint32_t)__ldg(a.text + i) : 0u);
+        }
+        w[q] = x;
+      }
+    }
+    if (p >= n) continue;
+    uint32_t gram = 0;
+#pragma unroll
+    for (uint32_t c = 0; c + 1 < G; ++c) gram = (gram << B) | s_code[(w[c >> 2] >> (8 * (c & 3))) & 0xFFu];
+#pragma unroll
+    for (uint32_t i = 0; i < GRAM_PER_THREAD; ++i) {
+      const uint32_t c = i + G - 1;  // the gram's last character
+      gram = ((gram << B) | s_code[(w[c >> 2] >> (8 * (c & 3))) & 0xFFu]) & 0xFFu;
+      if (p + i < n) atomicAdd(&s_hist[warp][gram], 1u);
+    }
+  }
+  __syncthreads();
+  uint32_t v = 0;
+  for (int w = 0; w < PACK_BLOCK / 32; ++w) v += s_hist[w][tid];
+  if (v) atomicAdd(&a.hist[(a.spec.P - 1) * RADIX + tid], v);
+}
+
 cudaError_t launch_pack(const PackArgs &a, cudaStream_t stream) {
   if (a.N == 0) return cudaSuccess;
+  if (!a.keys) {  // histograms only: the first radix pass forms the keys
+    if (!a.top_only) return cudaErrorInvalidValue;
+    const uint64_t span = (uint64_t)PACK_BLOCK * GRAM_PER_THREAD;
+    const uint64_t want = ((uint64_t)a.N + span - 1) / span;
+    const uint64_t cap = (uint64_t)device_sm_count() * 8;
+    const unsigned grid = (unsigned)(want < cap ? want : cap);
+    switch (a.b) {
+      case 1: k_gram_hist<1><<<grid, PACK_BLOCK, 0, stream>>>(a); break;
+      case 2: k_gram_hist<2><<<grid, PACK_BLOCK, 0, stream>>>(a); break;
+      case 4: k_gram_hist<4><<<grid, PACK_BLOCK, 0, stream>>>(a); break;
+      case 8: k_gram_hist<8><<<grid, PACK_BLOCK, 0, stream>>>(a); break;
+      default: return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_pack_hist_fixup<<<1, RADIX, 0, stream>>>(a);
+    return cudaGetLastError();
+  }
   if (a.c0 >= PACK_SLIDE_MIN) {
     const uint64_t span = PACK_BLOCK * 16;
     k_pack<16><<<(unsigned)((a.N + span - 1) / span), PACK_BLOCK, 0, stream>>>(a);

@@ -578,7 +578,9 @@ __device__ __forceinline__ void refine_tiny_groups(RfSmem<BLOCK, CAP, false> &S,
   // changed names (22 bits) scanned together.
   const uint64_t mine = (uint64_t)n_surv | ((uint64_t)n_grp << 21) | ((uint64_t)n_chg << 42);
   uint64_t tot;
-  const uint64_t ex = rf_block_excl_sum64<BLOCK>(mine, S.tmp[0], tot);
+  // S.tmp[1]: the caller's last scan used S.tmp[0], which some warps may
+  // still be reading.
+  const uint64_t ex = rf_block_excl_sum64<BLOCK>(mine, S.tmp[1], tot);
   if (tid == 0) {
     const uint32_t tot_surv = (uint32_t)(tot & 0x1FFFFF), tot_grp = (uint32_t)((tot >> 21) & 0x1FFFFF);
     const uint32_t tot_chg = (uint32_t)(tot >> 42);
@@ -599,42 +601,41 @@ __device__ __forceinline__ void refine_tiny_groups(RfSmem<BLOCK, CAP, false> &S,
     if (!z) continue;
     const uint32_t lg = tid * GPT + r;
     const uint32_t head = S.ghead[lg], old = S.gname[lg];
-    uint32_t a0 = 0;
+    // Bit k of E: item k ends its subgroup (the last item, or the next item
+    // has another partner name). Item x then belongs to the subgroup
+    // [a0, e]: e the first end at or after x, a0 one past the last end
+    // before it.
+    uint32_t E = 0;
 #pragma unroll
-    for (int k = 0; k < M; ++k) {
-      if ((uint32_t)k < z) {
-        const bool end = (uint32_t)k + 1 == z || (it[r][k + 1 < M ? k + 1 : k] >> 32) != (it[r][k] >> 32);
-        if (end) {
-          const uint32_t len = k + 1 - a0, lo = head + a0;
-          const uint32_t name =
-              len == 1 || a.naming != NAMES_RETAIN ? lo : (old - lo < len ? old : lo + len / 2);
-          if (name >= a.N) {  // never taken unless a logic error
-            raise_error(a.ctrl, ERR_INTERNAL, 15);
-            return;
-          }
-          if (len > 1) {
-            a.gstart_out[run_grp] = run_surv;
-            a.gname_out[run_grp] = name;
-            a.ghead_out[run_grp] = lo;
-          }
+    for (int k = 0; k < M; ++k)
+      if ((uint32_t)k < z &&
+          ((uint32_t)k + 1 == z || (it[r][k + 1 < M ? k + 1 : k] >> 32) != (it[r][k] >> 32)))
+        E |= 1u << k;
 #pragma unroll
-          for (int x = 0; x < M; ++x) {
-            if ((uint32_t)x >= a0 && (uint32_t)x <= (uint32_t)k) {
-              const uint32_t ip = (uint32_t)it[r][x];
-              if (ip >= a.isa_len) {  // never taken unless a logic error
-                raise_error(a.ctrl, ERR_INTERNAL, 16);
-                return;
-              }
-              if (name != old) a.upd[run_chg++] = ((uint64_t)name << 32) | ip;
-              if (len == 1)
-                a.sa[name] = local_index(ip, a.seg_off, a.S);
-              else
-                a.act_out[run_surv++] = ((uint64_t)run_grp << 32) | ip;
-            }
-          }
-          if (len > 1) ++run_grp;
-          a0 = k + 1;
-        }
+    for (int x = 0; x < M; ++x) {
+      if ((uint32_t)x >= z) continue;
+      const uint32_t e = (uint32_t)x + __ffs(E >> x) - 1;
+      const uint32_t below = E & ((1u << x) - 1u);
+      const uint32_t a0 = below ? 32u - __clz(below) : 0u;
+      const uint32_t len = e + 1 - a0, lo = head + a0;
+      const uint32_t name =
+          len == 1 || a.naming != NAMES_RETAIN ? lo : (old - lo < len ? old : lo + len / 2);
+      const uint32_t ip = (uint32_t)it[r][x];
+      if (name >= a.N || ip >= a.isa_len) {  // never taken unless a logic error
+        raise_error(a.ctrl, ERR_INTERNAL, name >= a.N ? 15 : 16);
+        return;
+      }
+      if (len > 1 && (uint32_t)x == a0) {  // a surviving subgroup starts here
+        a.gstart_out[run_grp] = run_surv;
+        a.gname_out[run_grp] = name;
+        a.ghead_out[run_grp] = lo;
+      }
+      if (name != old) a.upd[run_chg++] = ((uint64_t)name << 32) | ip;
+      if (len == 1) {
+        a.sa[name] = local_index(ip, a.seg_off, a.S);
+      } else {
+        a.act_out[run_surv++] = ((uint64_t)run_grp << 32) | ip;
+        if ((uint32_t)x == e) ++run_grp;
       }
     }
   }
@@ -699,6 +700,21 @@ __device__ __forceinline__ void refine_tile(RfSmem<BLOCK, CAP, WIDE> &S, const R
   }
   uint32_t nitems;
   uint32_t run = rf_block_excl_sum<BLOCK>(mysum, S.tmp[0], nitems);
+  if (nitems > (uint32_t)CAP) {  // never taken unless a logic error
+    if (tid == 0) raise_error(a.ctrl, ERR_INTERNAL, 9);
+    return;
+  }
+  if (nitems == 0) return;
+  if constexpr (!WIDE && CAP <= 1024) {
+    // Block-uniform (S.gmax is complete after the scan's barrier): every
+    // group has at most 4 members. That path takes each group whole from
+    // its source, so it needs neither the tile offsets below nor their
+    // barriers.
+    if (S.gmax <= RF_GROUP_MAX) {
+      refine_tiny_groups<BLOCK, CAP>(S, a, sz, h);
+      return;
+    }
+  }
 #pragma unroll
   for (int r = 0; r < C::GPT; ++r) {
     const uint32_t lg = tid * C::GPT + r;
@@ -711,18 +727,7 @@ __device__ __forceinline__ void refine_tile(RfSmem<BLOCK, CAP, WIDE> &S, const R
     S.all_small = any_big ? 0u : 1u;
   }
   __syncthreads();
-  if (nitems > (uint32_t)CAP) {  // never taken unless a logic error
-    if (tid == 0) raise_error(a.ctrl, ERR_INTERNAL, 9);
-    return;
-  }
   const uint32_t cnt = nitems;
-  if (cnt == 0) return;
-  if constexpr (!WIDE && CAP <= 1024) {
-    if (S.gmax <= RF_GROUP_MAX) {  // block-uniform: every group has at most 4 members
-      refine_tiny_groups<BLOCK, CAP>(S, a, sz, h);
-      return;
-    }
-  }
   const uint32_t K = (cnt + BLOCK - 1) / BLOCK;
 
   // Load (g, i') and gather the partner names; all loads of a thread are

@@ -88,7 +88,7 @@ constexpr float MATCH_RANK_MAX_DISTINCT = 24.f;
 __global__ void __launch_bounds__(RADIX)
 k_sort_plan(const uint32_t *__restrict__ hist, uint32_t *__restrict__ digit_base, DigitSpec spec,
             uint32_t m, uint64_t *ka, uint64_t *kb, uint32_t *va, uint32_t *vb,
-            SortPlan *plan, Ctrl *ctrl, const RoundState *rs) {
+            SortPlan *plan, Ctrl *ctrl, const RoundState *rs, uint32_t keep_first) {
   __shared__ uint32_t s_tmp[RADIX / 32 + 1];
   if (rs) {  // device-driven rounds
     if (!rs->live) return;
@@ -107,7 +107,7 @@ k_sort_plan(const uint32_t *__restrict__ hist, uint32_t *__restrict__ digit_base
     digit_base[p * RADIX + d] = excl;
     // A digit position is constant iff one bin holds every key.
     const int constant = __syncthreads_or(c == m);
-    if (d == 0) s_active[p] = constant ? 0u : 1u;
+    if (d == 0) s_active[p] = constant && !(keep_first && p == 0) ? 0u : 1u;
     // Expected distinct digits among 32 keys drawn from this histogram:
     // sum over d of 1 - (1 - p_d)^32. Few (a skewed alphabet) -> the pass
     // ranks with match.any, else with the shared-memory masks.
@@ -160,8 +160,9 @@ k_sort_plan(const uint32_t *__restrict__ hist, uint32_t *__restrict__ digit_base
 cudaError_t launch_sort_plan(const uint32_t *hist, uint32_t *digit_base, const DigitSpec &spec,
                              uint32_t m, uint64_t *ka, uint64_t *kb, uint32_t *va,
                              uint32_t *vb, SortPlan *plan, Ctrl *ctrl, cudaStream_t stream,
-                             const RoundState *rs) {
-  k_sort_plan<<<1, RADIX, 0, stream>>>(hist, digit_base, spec, m, ka, kb, va, vb, plan, ctrl, rs);
+                             const RoundState *rs, bool keep_first) {
+  k_sort_plan<<<1, RADIX, 0, stream>>>(hist, digit_base, spec, m, ka, kb, va, vb, plan, ctrl, rs,
+                                       keep_first ? 1u : 0u);
   return cudaGetLastError();
 }
 
@@ -191,10 +192,87 @@ struct OsSmem {
   uint64_t bar;                     // completion of the tile's bulk copies
 };
 
+// Index j of round 0's keys over one text (PassArgs.text): the tail
+// position n-1-j for j < tails, else position j - tails (k_pack.cu's layout).
+__device__ __forceinline__ uint32_t text_position(uint64_t j, uint32_t tails, uint64_t n) {
+  return (uint32_t)(j < tails ? n - 1 - j : j - tails);
+}
+
+// The keys of one tile built from the text (the first pass of round 0): the
+// dense codes of the characters the tile's keys cover are packed MSB-first
+// into 32-bit words in shared memory (the key buffer, unused until the
+// scatter), and each key is the cb bits at its position's bit offset: three
+// word reads and a funnel shift. Tail keys (tile 0 only) read their few
+// characters directly. Items past the end read as all ones.
+template <int OS_ITEMS>
+__device__ __forceinline__ void text_keys(OsSmem<OS_ITEMS> &S, const PassArgs &a, uint64_t base,
+                                          uint32_t count, uint64_t n,
+                                          uint64_t (&key)[OS_ITEMS]) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint8_t *s_code = reinterpret_cast<uint8_t *>(S.vals);
+  uint32_t *words = reinterpret_cast<uint32_t *>(S.keys);
+  const uint32_t b = a.b, cpw = 32 / b, t = a.tails;
+  s_code[tid] = a.code[tid];
+  __syncthreads();
+  // Non-tail indices [jl, jh) hold positions [jl - t, jh - t); their keys
+  // read characters [jl - t, jh - t + c0 - 1), all inside the text.
+  const uint64_t jl = base > t ? base : (uint64_t)t, jh = base + count;
+  uint64_t w0 = 0;
+  if (jl < jh) {
+    w0 = (jl - t) / cpw;
+    const uint64_t c_end = jh - t + a.c0 - 1;
+    const uint32_t nw = (uint32_t)((c_end + cpw - 1) / cpw - w0) + 2;
+    // A word's cpw (>= 4) characters start at a multiple of 4: 4-byte loads
+    // when the text is 4-byte aligned, bytes at the end of the text.
+    const bool v4 = (reinterpret_cast<uintptr_t>(a.text) & 3u) == 0;
+    for (uint32_t x = tid; x < nw; x += OS_BLOCK) {
+      const uint64_t c = (w0 + x) * cpw;
+      uint32_t w = 0;
+      if (v4 && c + cpw <= n) {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(a.text + c);
+        for (uint32_t q = 0; q < cpw / 4; ++q) {
+          const uint32_t v = __ldg(src + q);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) w = (w << b) | s_code[(v >> (8 * k)) & 0xFFu];
+        }
+      } else {
+        for (uint32_t q = 0; q < cpw; ++q)
+          w = (w << b) | (c + q < n ? (uint32_t)s_code[__ldg(a.text + c + q)] : 0u);
+      }
+      words[x] = w;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < OS_ITEMS; ++k) {
+    const uint32_t li = warp * (32 * OS_ITEMS) + k * 32 + lane;
+    const uint64_t j = base + li;
+    if (li >= count) {
+      key[k] = ~0ull;
+    } else if (j >= t) {
+      const uint64_t o = (j - t - w0 * cpw) * b;  // bit offset in the window
+      const uint32_t w = (uint32_t)(o >> 5), r = (uint32_t)(o & 31);
+      const uint64_t hi = ((uint64_t)words[w] << 32) | words[w + 1];
+      const uint64_t x = r ? (hi << r) | (words[w + 2] >> (32 - r)) : hi;
+      key[k] = a.cb >= 64 ? x : x >> (64 - a.cb);
+    } else {  // tail: j + 1 characters left, zero-padded
+      const uint64_t p = n - 1 - j;
+      uint64_t kk = 0;
+      for (uint32_t q = 0; q <= (uint32_t)j; ++q)
+        kk |= (uint64_t)s_code[__ldg(a.text + p + q)] << (a.cb - b * (q + 1));
+      key[k] = kk;
+    }
+  }
+}
+
 // OS_ITEMS keys per thread (8, 12 or 16; chosen per build): 16 fits three
 // blocks per SM (~62 KB of shared memory each), 12 four, 8 five; registers
 // are capped to match.
-template <int OS_ITEMS, bool PERSIST>
+//
+// FROM_TEXT: the first pass of round 0 over one text builds its keys from
+// the text (text_keys) and its values are the positions, so the packed keys
+// are never written and read back.
+template <int OS_ITEMS, bool PERSIST, bool FROM_TEXT>
 __global__ void __launch_bounds__(OS_BLOCK, OS_ITEMS >= 16 ? 3 : (OS_ITEMS >= 12 ? 4 : 5))
     k_onesweep(PassArgs a) {
   constexpr int OS_TILE = OS_BLOCK * OS_ITEMS;
@@ -237,40 +315,44 @@ __global__ void __launch_bounds__(OS_BLOCK, OS_ITEMS >= 16 ? 3 : (OS_ITEMS >= 12
     const uint64_t base = (uint64_t)tile * OS_TILE;
     const uint32_t count = (uint32_t)min((uint64_t)OS_TILE, (uint64_t)m - base);
 
-    // Load the tile: one bulk copy each for keys and values (TMA, 16-byte
-    // granules), plain loads for a ragged remainder or unaligned arrays. A
-    // block's earlier tile wrote these buffers through ordinary stores, so
-    // the copy is ordered after them by a proxy fence.
-    const uint64_t *kp = ksrc + base;
-    const uint32_t *vp = vsrc + base;
-    const bool aligned = ((((uintptr_t)kp) | ((uintptr_t)vp)) & 15u) == 0;
-    const uint32_t kbytes = aligned ? (count * 8u) & ~15u : 0u;
-    const uint32_t vbytes = aligned ? (count * 4u) & ~15u : 0u;
-    if (tid == 0 && (kbytes | vbytes)) {
-      fence_proxy_async_shared();
-      mbar_expect_tx(&S.bar, kbytes + vbytes);
-      if (kbytes) bulk_g2s(S.keys, kp, kbytes, &S.bar);
-      if (vbytes) bulk_g2s(S.vals, vp, vbytes, &S.bar);
-    }
-    for (uint32_t e = kbytes / 8u + tid; e < count; e += OS_BLOCK) S.keys[e] = kp[e];
-    for (uint32_t e = vbytes / 4u + tid; e < count; e += OS_BLOCK) S.vals[e] = vp[e];
-    if (kbytes | vbytes) {
-      if (!mbar_wait_bounded(&S.bar, phase, a.ctrl, a.spin_limit)) S.bail = 1;
-      phase ^= 1u;
-    }
-    __syncthreads();
-    if (S.bail) return;
-
-    // Warp-striped items: item k of lane l at warp*32*ITEMS + k*32 + l, so
-    // the order (warp, k, lane) is the input order inside the tile. Items
-    // past the end read as all ones: they take the largest digit and come
-    // last in the tile.
     uint64_t key[OS_ITEMS];
     uint32_t pos[OS_ITEMS];
+    if constexpr (FROM_TEXT) {
+      text_keys<OS_ITEMS>(S, a, base, count, m, key);
+    } else {
+      // Load the tile: one bulk copy each for keys and values (TMA, 16-byte
+      // granules), plain loads for a ragged remainder or unaligned arrays. A
+      // block's earlier tile wrote these buffers through ordinary stores, so
+      // the copy is ordered after them by a proxy fence.
+      const uint64_t *kp = ksrc + base;
+      const uint32_t *vp = vsrc + base;
+      const bool aligned = ((((uintptr_t)kp) | ((uintptr_t)vp)) & 15u) == 0;
+      const uint32_t kbytes = aligned ? (count * 8u) & ~15u : 0u;
+      const uint32_t vbytes = aligned ? (count * 4u) & ~15u : 0u;
+      if (tid == 0 && (kbytes | vbytes)) {
+        fence_proxy_async_shared();
+        mbar_expect_tx(&S.bar, kbytes + vbytes);
+        if (kbytes) bulk_g2s(S.keys, kp, kbytes, &S.bar);
+        if (vbytes) bulk_g2s(S.vals, vp, vbytes, &S.bar);
+      }
+      for (uint32_t e = kbytes / 8u + tid; e < count; e += OS_BLOCK) S.keys[e] = kp[e];
+      for (uint32_t e = vbytes / 4u + tid; e < count; e += OS_BLOCK) S.vals[e] = vp[e];
+      if (kbytes | vbytes) {
+        if (!mbar_wait_bounded(&S.bar, phase, a.ctrl, a.spin_limit)) S.bail = 1;
+        phase ^= 1u;
+      }
+      __syncthreads();
+      if (S.bail) return;
+
+      // Warp-striped items: item k of lane l at warp*32*ITEMS + k*32 + l, so
+      // the order (warp, k, lane) is the input order inside the tile. Items
+      // past the end read as all ones: they take the largest digit and come
+      // last in the tile.
 #pragma unroll
-    for (int k = 0; k < OS_ITEMS; ++k) {
-      const uint32_t li = warp * (32 * OS_ITEMS) + k * 32 + lane;
-      key[k] = li < count ? S.keys[li] : ~0ull;
+      for (int k = 0; k < OS_ITEMS; ++k) {
+        const uint32_t li = warp * (32 * OS_ITEMS) + k * 32 + lane;
+        key[k] = li < count ? S.keys[li] : ~0ull;
+      }
     }
     const uint32_t d = tid;  // thread d owns digit d and its status word
     uint64_t *st = a.status + (uint64_t)tile * RADIX + d;
@@ -333,7 +415,10 @@ __global__ void __launch_bounds__(OS_BLOCK, OS_ITEMS >= 16 ? 3 : (OS_ITEMS >= 12
 #pragma unroll
     for (int k = 0; k < OS_ITEMS; ++k) {
       const uint32_t li = warp * (32 * OS_ITEMS) + k * 32 + lane;
-      val[k] = li < count ? S.vals[li] : 0u;
+      if constexpr (FROM_TEXT)
+        val[k] = li < count ? text_position(base + li, a.tails, m) : 0u;
+      else
+        val[k] = li < count ? S.vals[li] : 0u;
     }
     __syncthreads();
 #pragma unroll
@@ -382,16 +467,25 @@ cudaError_t launch_onesweep_t(const PassArgs &a, cudaStream_t stream) {
   const int smem = (int)sizeof(OsSmem<OS_ITEMS>);
   const uint64_t tile = (uint64_t)OS_BLOCK * OS_ITEMS;
   const uint64_t tiles = ((uint64_t)a.m + tile - 1) / tile;
+  if (a.text) {  // the first pass of round 0 over one text (never persistent)
+    if (a.p != 0 || a.rs || a.b == 0 || 32 % a.b != 0 || a.cb == 0 || a.cb > 64)
+      return cudaErrorInvalidValue;
+    const void *fn = reinterpret_cast<const void *>(&k_onesweep<OS_ITEMS, false, true>);
+    cudaError_t e = ensure_smem_attributes(fn, smem, true);
+    if (e != cudaSuccess) return e;
+    k_onesweep<OS_ITEMS, false, true><<<(unsigned)tiles, OS_BLOCK, smem, stream>>>(a);
+    return cudaGetLastError();
+  }
   // One tile per block unless the grid is capped (persistent blocks loop).
   const bool persist = a.grid_cap && tiles > a.grid_cap;
-  const void *fn = persist ? reinterpret_cast<const void *>(&k_onesweep<OS_ITEMS, true>)
-                           : reinterpret_cast<const void *>(&k_onesweep<OS_ITEMS, false>);
+  const void *fn = persist ? reinterpret_cast<const void *>(&k_onesweep<OS_ITEMS, true, false>)
+                           : reinterpret_cast<const void *>(&k_onesweep<OS_ITEMS, false, false>);
   cudaError_t e = ensure_smem_attributes(fn, smem, true);
   if (e != cudaSuccess) return e;
   if (persist)
-    k_onesweep<OS_ITEMS, true><<<a.grid_cap, OS_BLOCK, smem, stream>>>(a);
+    k_onesweep<OS_ITEMS, true, false><<<a.grid_cap, OS_BLOCK, smem, stream>>>(a);
   else
-    k_onesweep<OS_ITEMS, false><<<(unsigned)tiles, OS_BLOCK, smem, stream>>>(a);
+    k_onesweep<OS_ITEMS, false, false><<<(unsigned)tiles, OS_BLOCK, smem, stream>>>(a);
   return cudaGetLastError();
 }
 

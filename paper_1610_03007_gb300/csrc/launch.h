@@ -48,6 +48,8 @@ struct PackArgs {
   // the other histograms are derived from it (k_pack_hist_fixup).
   uint32_t top_only;
 };
+// keys == NULL (top_only only): the histograms alone (the first radix pass
+// then builds the keys from the text, PassArgs.text).
 cudaError_t launch_pack(const PackArgs &a, cudaStream_t stream);
 
 // ---- step A2: radix sort (k_sort.cu) ------------------------------------
@@ -58,10 +60,12 @@ cudaError_t launch_digit_histogram(const uint64_t *keys, uint32_t m, const Digit
                                    uint32_t *hist, int num_sms, cudaStream_t stream,
                                    const RoundState *rs = nullptr);
 // Exclusive digit offsets, constant-digit skipping and buffer ping-pong.
+// keep_first: pass 0 is kept even if its digit is constant (it is the pass
+// that reads the text, PassArgs.text).
 cudaError_t launch_sort_plan(const uint32_t *hist, uint32_t *digit_base, const DigitSpec &spec,
                              uint32_t m, uint64_t *ka, uint64_t *kb, uint32_t *va,
                              uint32_t *vb, SortPlan *plan, Ctrl *ctrl, cudaStream_t stream,
-                             const RoundState *rs = nullptr);
+                             const RoundState *rs = nullptr, bool keep_first = false);
 // One stable one-sweep pass over digit p of the plan.
 struct PassArgs {
   const SortPlan *plan;
@@ -80,6 +84,13 @@ struct PassArgs {
   // (m then bounds the grid only; epoch is an offset). NULL: the fields above.
   const RoundState *rs;
   uint32_t grid_cap;  // at most this many blocks, each looping over tiles (0: one per tile)
+  // Pass 0 of round 0 over one text (text != NULL, p == 0, not persistent):
+  // the keys are built from the text in the layout of k_pack.cu (index j <
+  // tails: the tail position n-1-j, zero-padded; j >= tails: position j -
+  // tails) instead of read from the plan's source buffers.
+  const uint8_t *text;
+  const uint8_t *code;  // dense code of each byte (256 entries, device)
+  uint32_t b, c0, cb, tails;
 };
 constexpr int SORT_TILE_MIN = 256 * 8;  // smallest tile (sizes the status array)
 constexpr uint32_t SORT_ITEMS_DEFAULT = 16;

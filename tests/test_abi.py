@@ -112,6 +112,18 @@ def test_multiplier_option_is_checked_on_the_host(lib):
         assert lib.sa_build_ex(None, 0, None, None, None, 0, ctypes.byref(opt), None, None) == 0
 
 
+def test_initial_keys_option_is_checked_on_the_host(lib):
+    """sa_options.initial_keys outside {0, 1, 2} is refused before any GPU
+    work; the valid values with n = 0 return at once."""
+    import paper_1610_03007_gb300 as gbsa
+    for bad in (3, 7, 0xFFFFFFFF):
+        opt = gbsa.Options(initial_keys=bad)
+        assert lib.sa_build_ex(8, 100, 8, None, None, 0, ctypes.byref(opt), None, None) == 1
+    for good in (0, 1, 2):
+        opt = gbsa.Options(initial_keys=good)
+        assert lib.sa_build_ex(None, 0, None, None, None, 0, ctypes.byref(opt), None, None) == 0
+
+
 def test_binding_fails_loudly_without_the_library_or_a_gpu_tensor():
     """No CPU fallback: a missing library and a host tensor both raise."""
     import torch
