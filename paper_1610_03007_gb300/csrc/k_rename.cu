@@ -49,68 +49,45 @@ constexpr int RN_WARPS = RN_BLOCK / 32;
 constexpr int RN_LB_WINDOW = GBSA_RN_LB_WINDOW;
 static_assert(RN_TILE == RENAME_TILE, "tile size mismatch");
 
+// Item e of a tile (e = k * 256 + thread, k < RN_ITEMS) is the k-th item of
+// its thread: a warp's 32 lanes hold 32 consecutive items, so neighbours
+// are one shuffle away, counts come from ballots, and every output is
+// written by consecutive lanes to consecutive (or, for the compacted lists,
+// ballot-ranked) addresses straight from registers. The tile's order is
+// row-major: (k, warp, lane). Its segment (k, warp) of 32 items has its
+// counts in `cnt` and, after one warp's scan, its exclusive prefixes in
+// `pre`.
+constexpr int RN_SEGS = RN_ITEMS * RN_WARPS;
+static_assert(RN_SEGS == 64, "one scanning warp holds two segments per lane (8 items)");
+
 struct RnSmem {
-  // Loading: the tile's keys and values; writing: staged queued updates
-  // (keys) and, in round 0, the SA entries by tile index (vals).
-  uint64_t keys[RN_TILE + RN_TILE / 16];  // element e at e + e/16 (no bank conflicts)
-  uint32_t vals[RN_TILE + RN_TILE / 32];  // element e at e + e/32
-  uint64_t surv[RN_TILE];                 // staged next-list entries of the survivors
-  uint64_t prev_key, next_key;
-  uint32_t prev_val, next_val;
-  uint32_t tmp[RN_WARPS + 1];
-  uint32_t carry[2];
-  uint32_t tile, bail, upd_local, upd_base;
+  // Per segment: unique | survivors << 21 | surviving-group heads << 42.
+  unsigned long long cnt[RN_SEGS];
+  unsigned long long pre[RN_SEGS];
+  uint32_t carry[2];  // survivors and groups of the tiles before this one
+  uint32_t tile, bail, upd_base;
 };
 
-__device__ __forceinline__ uint32_t kidx(uint32_t e) { return e + (e >> 4); }
-__device__ __forceinline__ uint32_t vidx(uint32_t e) { return e + (e >> 5); }
+__device__ __forceinline__ uint32_t lanemask_le_u32() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_le;" : "=r"(m));
+  return m;
+}
 
 // One rename tile; every thread of the block calls it. Returns false when
 // the block must stop (a wait gave up). m, g_in and epoch as in the kernel.
 __device__ __forceinline__ bool rename_tile(RnSmem &S, const RenameArgs &a, const uint32_t tile,
                                             const uint32_t m, const uint32_t g_in,
                                             const uint32_t epoch) {
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint64_t *__restrict__ K = a.plan->kfinal;
   const uint32_t *__restrict__ V = a.plan->vfinal;
+  // a-tuple rounds: items with equal keys are still apart if their later
+  // partners differ (sorted alongside, in the other key buffer).
+  const uint64_t *SEC = a.sec_buf[0] ? a.sec_buf[a.plan->final_idx ^ 1u] : nullptr;
   const uint32_t base = tile * RN_TILE;
   const uint32_t count = min((uint32_t)RN_TILE, m - base);
 
-  // Coalesced load of the tile plus one item of halo on each side.
-  for (int k = 0; k < RN_ITEMS; ++k) {
-    const uint32_t e = k * RN_BLOCK + tid;
-    if (e < count) {
-      S.keys[kidx(e)] = K[base + e];
-      S.vals[vidx(e)] = V[base + e];
-    }
-  }
-  if (tid == 0) {
-    S.prev_key = base > 0 ? K[base - 1] : 0ull;
-    S.prev_val = base > 0 ? V[base - 1] : 0u;
-    const bool has_next = base + count < m;
-    S.next_key = has_next ? K[base + count] : 0ull;
-    S.next_val = has_next ? V[base + count] : 0u;
-  }
-  __syncthreads();
-
-  // Items tid*16 .. tid*16+15 of the tile, with neighbours -1 and +16.
-  const uint32_t l0 = tid * RN_ITEMS;
-  uint64_t key[RN_ITEMS + 2];
-  uint32_t val[RN_ITEMS + 2];
-#pragma unroll
-  for (int k = 0; k < RN_ITEMS + 2; ++k) {
-    const int64_t l = (int64_t)l0 + k - 1;
-    if (l < 0) {
-      key[k] = S.prev_key;
-      val[k] = S.prev_val;
-    } else if (l < (int64_t)count) {
-      key[k] = S.keys[kidx((uint32_t)l)];
-      val[k] = S.vals[vidx((uint32_t)l)];
-    } else {
-      key[k] = S.next_key;
-      val[k] = S.next_val;
-    }
-  }
   // Round 0: does the suffix at gapped position v (key k) have fewer than
   // c0 characters left in its text?
   auto tail = [&](uint64_t k, uint32_t v) -> bool {
@@ -120,110 +97,126 @@ __device__ __forceinline__ bool rename_tile(RnSmem &S, const RenameArgs &a, cons
     const uint32_t len = __ldg(a.seg_off + s + 1) - off;
     return len - (v - (off + s)) < a.c0;
   };
-  // f[k] = boundary flag of item l0 + k (k = 0..16).
-  bool f[RN_ITEMS + 1];
-  bool is_tail[RN_ITEMS + 2];
-  if (a.round0) {
-#pragma unroll
-    for (int k = 0; k < RN_ITEMS + 2; ++k) is_tail[k] = tail(key[k], val[k]);
-  }
-  // a-tuple rounds: items with equal keys are still apart if their later
-  // partners differ (sorted alongside, in the other key buffer).
-  const uint64_t *SEC = a.sec_buf[0] ? a.sec_buf[a.plan->final_idx ^ 1u] : nullptr;
-#pragma unroll
-  for (int k = 0; k <= RN_ITEMS; ++k) {
-    const uint64_t j = (uint64_t)base + l0 + k;
-    bool b = (j == 0) || (j >= m) || key[k + 1] != key[k];
-    if (a.round0 && j > 0 && j < m) b = b || is_tail[k + 1] || is_tail[k];
-    if (SEC && !b) b = SEC[j] != SEC[j - 1];
-    f[k] = b;
-  }
-  uint32_t th_surv = 0, th_hs = 0, th_uniq = 0;
+
+  uint64_t key[RN_ITEMS];
+  uint32_t val[RN_ITEMS];
 #pragma unroll
   for (int k = 0; k < RN_ITEMS; ++k) {
-    if (l0 + k < count) {
-      const bool uniq = f[k] && f[k + 1];
-      if (!uniq) {
-        ++th_surv;
-        if (f[k]) ++th_hs;
-      } else {
-        ++th_uniq;
-      }
-    }
+    const uint32_t e = k * RN_BLOCK + tid;
+    key[k] = e < count ? K[base + e] : 0ull;
+    val[k] = e < count ? V[base + e] : 0u;
   }
-  // ISA entries of new unique suffixes are queued (in any order) and applied
-  // only when a later round, the ISA output or the trace reads them.
-  const uint32_t my_upd = th_uniq ? atomicAdd(&S.upd_local, th_uniq) : 0u;
-  uint32_t tot_surv, tot_hs;
-  const uint32_t ex_surv = block_exclusive<RN_BLOCK>(th_surv, OpAdd(), 0u, S.tmp, tot_surv);
-  const uint32_t ex_hs = block_exclusive<RN_BLOCK>(th_hs, OpAdd(), 0u, S.tmp, tot_hs);
-
-  // The tile's survivors and surviving groups, published for the device-wide
-  // sums (decoupled look-back); the look-back itself runs after the staging
-  // below, which needs only tile-local offsets.
-  uint64_t *st_tile = a.status + (uint64_t)tile * 2;
-  if (tid < 2) status_store(st_tile + tid, status_word(epoch, tile == 0 ? ST_INC : ST_AGG,
-                                                        tid == 0 ? tot_surv : tot_hs));
-  if (tid == 0) S.upd_base = S.upd_local ? atomicAdd(&a.ctrl->rc.upd, S.upd_local) : 0u;
-  // Outputs are staged in shared memory and written with consecutive
-  // addresses afterwards: queued updates in the keys area, survivors' list
-  // entries (with tile-local group ordinals) in `surv`, and (round 0, where a
-  // unique item's name is its own position in the sorted order) SA entries
-  // by tile index in the vals area. Every item's new group starts at a head
-  // (f = 1) whose head rank is that head's own sorted index, so no head rank
-  // from an earlier tile is needed.
-  uint64_t *st_upd = S.keys;
-  uint32_t *st_sa = S.vals;
-  if (a.round0)
-    for (uint32_t e = tid; e < count; e += RN_BLOCK) st_sa[e] = NO_NAME;
-  __syncthreads();
-  {
-    uint32_t run_upd = my_upd, run_surv = ex_surv, run_hs = ex_hs;
+  // Boundary flags f (item j starts a new group: Algorithm 2's CmpName, and
+  // in round 0 the tail rule) and fn = f of the next item, as bit k of each.
+  uint32_t fbits = 0, fnbits = 0;
 #pragma unroll
-    for (int k = 0; k < RN_ITEMS; ++k) {
-      if (l0 + k < count) {
-        const uint32_t j = base + l0 + k;
-        const uint64_t kk = key[k + 1];
-        const uint32_t ip = val[k + 1];
-        if (ip >= a.isa_len) {  // never taken unless a logic error
-          raise_error(a.ctrl, ERR_INTERNAL, 3);
-          continue;
-        }
-        if (f[k] && f[k + 1]) {
-          // Unique: its name is its rank, final (Algorithm 5 discards it). SA
-          // holds the index local to the suffix's own text.
-          const uint32_t g = a.round0 ? 0u : (uint32_t)(kk >> a.W);
-          if (!a.round0 && g >= g_in) {  // never taken unless a logic error
-            raise_error(a.ctrl, ERR_INTERNAL, 4);
-            continue;
-          }
-          const uint32_t head = a.round0 ? j : __ldg(a.base_in + g) + j;
-          if (head >= a.N) {  // never taken unless a logic error
-            raise_error(a.ctrl, ERR_INTERNAL, 3);
-            continue;
-          }
-          st_upd[run_upd++] = ((uint64_t)head << 32) | ip;
-          uint32_t local = ip;
-          if (a.S > 1) {
-            if (a.round0) {
-              const uint32_t s = (uint32_t)(kk >> a.cb);
-              local = ip - (__ldg(a.seg_off + s) + s);
-            } else {
-              local = local_index(ip, a.seg_off, a.S);
-            }
-          }
-          if (a.round0)
-            st_sa[l0 + k] = local;  // head == j here
-          else
-            a.sa[head] = local;
-        } else {
-          // Survivors get their names, and their ISA entries, once the group
-          // sizes are known (k_classify, k_apply_names).
-          if (f[k]) ++run_hs;
-          S.surv[run_surv++] = ((uint64_t)(run_hs - 1) << 32) | ip;
-        }
+  for (int k = 0; k < RN_ITEMS; ++k) {
+    const uint32_t e = k * RN_BLOCK + tid;
+    const uint32_t j = base + e;  // < 2^32: m fits 32 bits
+    const bool valid = e < count;
+    const bool tl = a.round0 && valid && tail(key[k], val[k]);
+    const uint64_t sc = SEC && valid ? SEC[j] : 0ull;
+    // the item before: lane - 1, or (lane 0) read from memory
+    uint64_t pk = __shfl_up_sync(0xffffffffu, key[k], 1);
+    bool ptl = __shfl_up_sync(0xffffffffu, (uint32_t)tl, 1) != 0u;
+    uint64_t ps = __shfl_up_sync(0xffffffffu, sc, 1);
+    if (lane == 0 && valid && j > 0) {
+      pk = K[j - 1];
+      ptl = a.round0 && tail(pk, V[j - 1]);
+      ps = SEC ? SEC[j - 1] : 0ull;
+    }
+    const bool f = !valid || j == 0 || key[k] != pk || (a.round0 && (tl || ptl)) ||
+                   (SEC && sc != ps);
+    // the item after: lane + 1's flag, or (lane 31) computed from memory
+    bool fn = __shfl_down_sync(0xffffffffu, (uint32_t)f, 1) != 0u;
+    if (lane == 31 && valid) {
+      if (j + 1 >= m) {
+        fn = true;
+      } else {
+        const uint64_t nk = K[j + 1];
+        fn = nk != key[k] || (a.round0 && (tl || tail(nk, V[j + 1]))) ||
+             (SEC && SEC[j + 1] != sc);
       }
     }
+    if (f) fbits |= 1u << k;
+    if (fn) fnbits |= 1u << k;
+  }
+  // Per segment: unique items (f and fn), survivors, heads of surviving
+  // groups (f, not fn).
+#pragma unroll
+  for (int k = 0; k < RN_ITEMS; ++k) {
+    const bool valid = (uint32_t)(k * RN_BLOCK + tid) < count;
+    const bool f = (fbits >> k) & 1u, fn = (fnbits >> k) & 1u;
+    const uint32_t U = __ballot_sync(0xffffffffu, valid && f && fn);
+    const uint32_t Sv = __ballot_sync(0xffffffffu, valid && !(f && fn));
+    const uint32_t H = __ballot_sync(0xffffffffu, valid && f && !fn);
+    if (lane == 0)
+      S.cnt[k * RN_WARPS + warp] = (unsigned long long)__popc(U) |
+                                   ((unsigned long long)__popc(Sv) << 21) |
+                                   ((unsigned long long)__popc(H) << 42);
+  }
+  __syncthreads();
+  // One warp scans the segments (two per lane), publishes the tile's
+  // survivors and groups for the device-wide sums, and reserves the queued
+  // updates' space.
+  if (warp == 0) {
+    const unsigned long long c0 = S.cnt[2 * lane], c1 = S.cnt[2 * lane + 1];
+    unsigned long long incl = c0 + c1;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned long long o = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += o;
+    }
+    const unsigned long long tot = __shfl_sync(0xffffffffu, incl, 31);
+    const unsigned long long ex = incl - c0 - c1;
+    S.pre[2 * lane] = ex;
+    S.pre[2 * lane + 1] = ex + c0;
+    const uint32_t tot_u = (uint32_t)(tot & 0x1FFFFFu);
+    const uint32_t tot_s = (uint32_t)((tot >> 21) & 0x1FFFFFu), tot_h = (uint32_t)(tot >> 42);
+    if (lane < 2)
+      status_store(a.status + (uint64_t)tile * 2 + lane,
+                   status_word(epoch, tile == 0 ? ST_INC : ST_AGG, lane == 0 ? tot_s : tot_h));
+    if (lane == 2) S.upd_base = tot_u ? atomicAdd(&a.ctrl->rc.upd, tot_u) : 0u;
+  }
+  __syncthreads();
+
+  // Unique items (Algorithm 5 discards them): name = rank, final. The
+  // queued ISA entry and the SA entry (the index local to the suffix's own
+  // text) need no offsets from earlier tiles, so they go before the
+  // look-back.
+  const uint32_t lt = lanemask_lt(), le = lanemask_le_u32();
+#pragma unroll
+  for (int k = 0; k < RN_ITEMS; ++k) {
+    const uint32_t e = k * RN_BLOCK + tid;
+    const bool valid = e < count;
+    const bool f = (fbits >> k) & 1u, fn = (fnbits >> k) & 1u;
+    const bool uniq = valid && f && fn;
+    const uint32_t U = __ballot_sync(0xffffffffu, uniq);
+    if (!uniq) continue;
+    const uint32_t j = base + e, ip = val[k];
+    const uint32_t g = a.round0 ? 0u : (uint32_t)(key[k] >> a.W);
+    if (!a.round0 && g >= g_in) {  // never taken unless a logic error
+      raise_error(a.ctrl, ERR_INTERNAL, 4);
+      continue;
+    }
+    const uint32_t head = a.round0 ? j : __ldg(a.base_in + g) + j;
+    if (head >= a.N || ip >= a.isa_len) {  // never taken unless a logic error
+      raise_error(a.ctrl, ERR_INTERNAL, 3);
+      continue;
+    }
+    const uint32_t slot = S.upd_base + (uint32_t)(S.pre[k * RN_WARPS + warp] & 0x1FFFFFu) +
+                          __popc(U & lt);
+    a.upd[slot] = ((uint64_t)head << 32) | ip;
+    uint32_t local = ip;
+    if (a.S > 1) {
+      if (a.round0) {
+        const uint32_t s = (uint32_t)(key[k] >> a.cb);
+        local = ip - (__ldg(a.seg_off + s) + s);
+      } else {
+        local = local_index(ip, a.seg_off, a.S);
+      }
+    }
+    a.sa[head] = local;
   }
 
   // Device-wide offsets of the tile's survivors and groups.
@@ -233,9 +226,12 @@ __device__ __forceinline__ bool rename_tile(RnSmem &S, const RenameArgs &a, cons
     if (tile > 0) {
       ok = look_back_w<RN_LB_WINDOW>(a.status, 2, tid, tile, epoch, OpAdd(), carry, a.ctrl,
                                      a.spin_limit);
-      if (ok)
-        status_store(st_tile + tid,
-                     status_word(epoch, ST_INC, carry + (tid == 0 ? tot_surv : tot_hs)));
+      if (ok) {
+        const unsigned long long tot = S.pre[RN_SEGS - 1] + S.cnt[RN_SEGS - 1];
+        const uint32_t mine =
+            tid == 0 ? (uint32_t)((tot >> 21) & 0x1FFFFFu) : (uint32_t)(tot >> 42);
+        status_store(a.status + (uint64_t)tile * 2 + tid, status_word(epoch, ST_INC, carry + mine));
+      }
     }
     if (!ok) S.bail = 1;
     S.carry[tid] = carry;
@@ -245,57 +241,60 @@ __device__ __forceinline__ bool rename_tile(RnSmem &S, const RenameArgs &a, cons
   const uint32_t m_off = __ldg(a.off_in), g_off = __ldg(a.off_in + 1);
   const uint32_t surv0 = m_off + S.carry[0], grp0 = g_off + S.carry[1];
   if (tid == 0 && base + count == m) {
-    a.cnt_out[0] = S.carry[0] + tot_surv;
-    a.cnt_out[1] = S.carry[1] + tot_hs;
+    const unsigned long long tot = S.pre[RN_SEGS - 1] + S.cnt[RN_SEGS - 1];
+    a.cnt_out[0] = S.carry[0] + (uint32_t)((tot >> 21) & 0x1FFFFFu);
+    a.cnt_out[1] = S.carry[1] + (uint32_t)(tot >> 42);
   }
-  // Surviving groups: start in the next list, head rank, parent's name.
-  {
-    uint32_t run_surv = ex_surv, run_hs = ex_hs;
+  // Survivors: compacted, in order, into the next active list with their
+  // group ordinal g' (the surviving-group heads at or before them, minus
+  // one); each group's head records its start there, its head rank (its own
+  // sorted index) and its parent's name. Their names and ISA entries follow
+  // once the group sizes are known (k_classify, k_apply_names).
 #pragma unroll
-    for (int k = 0; k < RN_ITEMS; ++k) {
-      if (l0 + k < count && !(f[k] && f[k + 1])) {
-        if (f[k]) {
-          const uint32_t j = base + l0 + k;
-          const uint32_t g = a.round0 ? 0u : (uint32_t)(key[k + 1] >> a.W);
-          if (!a.round0 && g >= g_in) {  // never taken unless a logic error
-            raise_error(a.ctrl, ERR_INTERNAL, 4);
-            continue;
-          }
-          const uint32_t head = a.round0 ? j : __ldg(a.base_in + g) + j;
-          if (head >= a.N) {  // never taken unless a logic error
-            raise_error(a.ctrl, ERR_INTERNAL, 3);
-            continue;
-          }
-          const uint32_t o = grp0 + run_hs;
-          a.gstart_out[o] = surv0 + run_surv;
-          a.ghead_out[o] = head;
-          a.gold_out[o] = a.round0 ? NO_NAME : __ldg(a.old_in + g);
-          ++run_hs;
-        }
-        ++run_surv;
-      }
+  for (int k = 0; k < RN_ITEMS; ++k) {
+    const uint32_t e = k * RN_BLOCK + tid;
+    const bool valid = e < count;
+    const bool f = (fbits >> k) & 1u, fn = (fnbits >> k) & 1u;
+    const bool surv = valid && !(f && fn);
+    const uint32_t Sv = __ballot_sync(0xffffffffu, surv);
+    const uint32_t H = __ballot_sync(0xffffffffu, valid && f && !fn);
+    if (!surv) continue;
+    const unsigned long long pr = S.pre[k * RN_WARPS + warp];
+    const uint32_t sidx = (uint32_t)((pr >> 21) & 0x1FFFFFu) + __popc(Sv & lt);
+    const uint32_t ord = grp0 + (uint32_t)(pr >> 42) + __popc(H & le) - 1u;
+    const uint32_t ip = val[k];
+    if (ip >= a.isa_len) {  // never taken unless a logic error
+      raise_error(a.ctrl, ERR_INTERNAL, 3);
+      continue;
     }
-  }
-  for (uint32_t e = tid; e < S.upd_local; e += RN_BLOCK) a.upd[S.upd_base + e] = st_upd[e];
-  const uint64_t gshift = (uint64_t)grp0 << 32;
-  for (uint32_t e = tid; e < tot_surv; e += RN_BLOCK) a.act_out[surv0 + e] = S.surv[e] + gshift;
-  if (a.round0) {
-    for (uint32_t e = tid; e < count; e += RN_BLOCK) {
-      const uint32_t v = st_sa[e];
-      if (v != NO_NAME) a.sa[base + e] = v;
+    a.act_out[surv0 + sidx] = ((uint64_t)ord << 32) | ip;
+    if (f) {  // the head of a surviving group
+      const uint32_t j = base + e;
+      const uint32_t g = a.round0 ? 0u : (uint32_t)(key[k] >> a.W);
+      if (!a.round0 && g >= g_in) {  // never taken unless a logic error
+        raise_error(a.ctrl, ERR_INTERNAL, 4);
+        continue;
+      }
+      const uint32_t head = a.round0 ? j : __ldg(a.base_in + g) + j;
+      if (head >= a.N) {  // never taken unless a logic error
+        raise_error(a.ctrl, ERR_INTERNAL, 3);
+        continue;
+      }
+      a.gstart_out[ord] = surv0 + sidx;
+      a.ghead_out[ord] = head;
+      a.gold_out[ord] = a.round0 ? NO_NAME : __ldg(a.old_in + g);
     }
   }
   return true;
 }
 
-// 8 items: 64 registers, 4 blocks of 256 threads per SM (42 KB of shared
-// memory each); 4 items: 6 blocks. Tiles are taken from the launch's
+// 8 items per thread, 4 blocks of 256 threads per SM. Tiles are taken from the launch's
 // counter until it passes the last one, so any grid works (a grid smaller
 // than the tile count makes the blocks persistent); in device-driven
 // rounds the item and group counts and the epoch base come from the round
 // state.
 template <bool PERSIST>
-__global__ void __launch_bounds__(RN_BLOCK, RN_ITEMS <= 4 ? 6 : 4) k_rename(RenameArgs a) {
+__global__ void __launch_bounds__(RN_BLOCK, 4) k_rename(RenameArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   RnSmem &S = *reinterpret_cast<RnSmem *>(smem_raw);
   uint32_t m = a.m, g_in = a.g_in, epoch = a.epoch;
@@ -311,7 +310,6 @@ __global__ void __launch_bounds__(RN_BLOCK, RN_ITEMS <= 4 ? 6 : 4) k_rename(Rena
     if (tid == 0) {
       S.tile = atomicAdd(a.tile_ctr, 1u);
       S.bail = has_error(a.ctrl) ? 1u : 0u;
-      S.upd_local = 0u;
     }
     __syncthreads();
     if (S.bail || S.tile >= tiles) return;
