@@ -289,7 +289,8 @@ def _roofline(kern, workload):
             "ms_per_launch": d["ms"] / max(d["launches"], 1)}
 
 
-def measure_single(cfg, steps, warmup, local, pg=None, clocks=False, h0_chars=0, sort_items=0):
+def measure_single(cfg, steps, warmup, local, pg=None, clocks=False, h0_chars=0, sort_items=0,
+                   refine_shape=0):
     """K timed builds of one seeded text resident in HBM, with the library's
     per-launch CUDA events (sa_options.profile) on the same stream; returns
     the timings, the per-kernel table and the device text/workspace."""
@@ -307,7 +308,8 @@ def measure_single(cfg, steps, warmup, local, pg=None, clocks=False, h0_chars=0,
 
     def step(profile):
         st = gbsa.Stats()
-        opt = gbsa.Options(profile=1 if profile else 0, h0_chars=h0_chars, sort_items=sort_items)
+        opt = gbsa.Options(profile=1 if profile else 0, h0_chars=h0_chars, sort_items=sort_items,
+                           refine_shape=refine_shape)
         rc = lib.sa_build_ex(text.data_ptr(), n, sa.data_ptr(), None, ws.data_ptr(), ws.numel(),
                              gbsa.ctypes.byref(opt), gbsa.ctypes.byref(st), stream.cuda_stream)
         if rc != 0:
@@ -471,7 +473,7 @@ def single_report(m, cfg, steps, world):
         "value": replicas_value(n, world, ms), "unit": "MB/s", "ms_per_step": ms, "steps": steps,
         "config": {"workload": cfg["workload"], "n": n, "seed": cfg["seed"],
                    "rounds": st["rounds"], "params": st["params"],
-                   "active_per_round": st["active"]},
+                   "active_per_round": st["active"], "groups_per_round": st["groups"]},
         "roofline": _roofline(m["kern"], "markov" if cfg["recipe"] == "markov" else "zipf"),
         "path_roofline": {"bytes_per_step": m["bytes_model"] / steps, "achieved_gbs": path_gbs,
                           "frac_measured": path_gbs / hbm, "frac_8tbs": path_gbs / 8000.0},
@@ -571,8 +573,10 @@ def run_plain(args):
         cfg["workload"] += f" ({args.h0} characters per initial key)"
     if args.sort_items:
         cfg["workload"] += f" ({args.sort_items} keys per thread in the radix passes)"
+    if args.refine_shape:
+        cfg["workload"] += f" (refine tile shape {args.refine_shape})"
     m = measure_single(cfg, args.steps, args.warmup, local, clocks=True, h0_chars=args.h0,
-                       sort_items=args.sort_items)
+                       sort_items=args.sort_items, refine_shape=args.refine_shape)
     rep = single_report(m, cfg, args.steps, 1)
     if not args.build_only and cfg["recipe"] == "zipf_repeats":
         rep.update(cfg2_extras(m, args.steps))
@@ -842,6 +846,8 @@ def main():
     ap.add_argument("--sort-items", type=int, default=0,
                     help="plain workload: keys per thread of the radix passes (8, 12, 16; "
                          "0: the library's choice)")
+    ap.add_argument("--refine-shape", type=int, default=0,
+                    help="plain workload: refine tile shape 1-4 (0: the library's choice)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--headline-only", action="store_true",
                     help="suite: the headline line without the nested workloads")
