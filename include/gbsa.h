@@ -353,6 +353,13 @@ typedef struct {
    * n * simulate_ns_per_byte nanoseconds and its SA buffer is untouched. */
   uint32_t simulate;
   double simulate_ns_per_byte;
+  /* 0 (default): a request runs on a CUDA stream whose priority falls with
+   * its size (up to 256 KiB the device's highest priority, then one level
+   * lower for each size class up to 2 MiB, 16 MiB and beyond), so the
+   * block scheduler starts a small request's blocks before the waiting
+   * blocks of large builds in flight and its latency stays near that of a
+   * build alone. 1: every request on a stream of default priority. */
+  uint32_t size_priority;
 } sa_server_config;
 
 typedef struct {
@@ -360,6 +367,8 @@ typedef struct {
   uint64_t n;                 /* text length                                     */
   uint32_t slot;              /* worker that ran it                              */
   double submit_s, start_s, done_s; /* seconds since the server was created     */
+  int32_t priority;           /* CUDA stream priority it ran at (lower = higher; */
+                              /* in simulate mode the range [-5, 0] is assumed) */
 } sa_request_info;
 
 typedef struct {

@@ -102,18 +102,18 @@ class Stats(ctypes.Structure):
 class ServerConfig(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_uint64), ("slots", ctypes.c_uint32),
                 ("device", ctypes.c_int32), ("simulate", ctypes.c_uint32),
-                ("simulate_ns_per_byte", ctypes.c_double)]
+                ("simulate_ns_per_byte", ctypes.c_double), ("size_priority", ctypes.c_uint32)]
 
 
 class RequestInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("n", ctypes.c_uint64), ("slot", ctypes.c_uint32),
                 ("submit_s", ctypes.c_double), ("start_s", ctypes.c_double),
-                ("done_s", ctypes.c_double)]
+                ("done_s", ctypes.c_double), ("priority", ctypes.c_int32)]
 
     def to_dict(self) -> dict:
         return {"status": self.status, "n": self.n, "slot": self.slot,
                 "submit_s": self.submit_s, "start_s": self.start_s, "done_s": self.done_s,
-                "latency_s": self.done_s - self.submit_s}
+                "latency_s": self.done_s - self.submit_s, "priority": self.priority}
 
 
 class ServerStats(ctypes.Structure):
@@ -478,13 +478,15 @@ class Server:
 
     submit() takes a host numpy uint8 text and returns a ticket; the output
     buffer (numpy uint32) is kept alive here until the request is waited on.
+    size_priority: smaller requests run on higher-priority CUDA streams
+    (sa_server_config.size_priority); the info dict reports the priority.
     """
 
     def __init__(self, budget_bytes: int = 0, slots: int = 0, device: int = -1,
-                 simulate_ns_per_byte: float = 0.0):
+                 simulate_ns_per_byte: float = 0.0, size_priority: bool = True):
         self._lib = load()
         cfg = ServerConfig(budget_bytes, slots, device, 1 if simulate_ns_per_byte > 0 else 0,
-                           simulate_ns_per_byte)
+                           simulate_ns_per_byte, 0 if size_priority else 1)
         h = ctypes.c_void_p()
         _check(self._lib.sa_server_create(ctypes.byref(cfg), ctypes.byref(h)), "sa_server_create")
         self._h = h

@@ -12,6 +12,12 @@
 // (sa_server_wait returned, or sa_server_poll reported it done), so a
 // long-running server holds only queued, running and uncollected requests.
 //
+// Each worker holds one stream per priority level, and a request runs on
+// the stream of its size class (sa_server_config.size_priority): the block
+// scheduler starts a small request's blocks ahead of the waiting blocks of
+// large builds in flight, so small requests are not queued behind whole
+// kernels of large ones.
+//
 // The paper has no serving layer; this is the runtime around its method.
 #include <chrono>
 #include <condition_variable>
@@ -34,6 +40,21 @@ constexpr uint32_t DEFAULT_SLOTS = 8;
 constexpr uint32_t MAX_SLOTS = 64;
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Size classes of the stream priorities: up to 256 KiB, 2 MiB, 16 MiB, more.
+constexpr int PRIORITY_CLASSES = 4;
+int size_class(uint64_t n) {
+  if (n <= (256ull << 10)) return 0;
+  if (n <= (2ull << 20)) return 1;
+  if (n <= (16ull << 20)) return 2;
+  return 3;
+}
+// Stream priority of size class c in the device's range [least, greatest]
+// (greatest is the numerically lowest, the highest priority).
+int class_priority(int c, int least, int greatest) {
+  const int p = greatest + c;
+  return p < least ? p : least;
+}
 
 struct Request {
   uint64_t ticket = 0;
@@ -79,11 +100,18 @@ struct sa_server {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
 
+  int prio_least = 0, prio_greatest = -5;  // the simulate-mode range
+
+  int priority_of(int c) const {
+    return cfg.size_priority == 0 ? class_priority(c, prio_least, prio_greatest) : 0;
+  }
+
   void worker(uint32_t slot) {
-    cudaStream_t st = nullptr;
+    cudaStream_t streams[PRIORITY_CLASSES] = {};
     if (!cfg.simulate) {
       cudaSetDevice(device);
-      cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+      for (int c = 0; c < PRIORITY_CLASSES; ++c)
+        cudaStreamCreateWithPriority(&streams[c], cudaStreamNonBlocking, priority_of(c));
     }
     for (;;) {
       Request *r = nullptr;
@@ -104,13 +132,14 @@ struct sa_server {
         stats.queued = (uint32_t)queue.size();
         r->info.start_s = now();
         r->info.slot = slot;
+        r->info.priority = priority_of(size_class(r->n));
       }
       sa_status status = SA_OK;
       if (cfg.simulate) {
         const double ns = (double)r->n * cfg.simulate_ns_per_byte;
         std::this_thread::sleep_for(std::chrono::nanoseconds((int64_t)ns));
       } else {
-        status = sa_build_host(r->text, r->n, r->sa, (gbsa_stream_t)st);
+        status = sa_build_host(r->text, r->n, r->sa, (gbsa_stream_t)streams[size_class(r->n)]);
       }
       {
         std::lock_guard<std::mutex> lk(mu);
@@ -125,7 +154,8 @@ struct sa_server {
       cv_done.notify_all();
       cv_work.notify_all();  // memory and a slot were freed
     }
-    if (st) cudaStreamDestroy(st);
+    for (cudaStream_t st : streams)
+      if (st) cudaStreamDestroy(st);
   }
 };
 
@@ -146,6 +176,15 @@ GBSA_API sa_status sa_server_create(const sa_server_config *cfg, sa_server **out
   if (!s->cfg.simulate && s->device < 0 && cudaGetDevice(&s->device) != cudaSuccess) {
     delete s;
     return SA_ERR_CUDA;
+  }
+  if (!s->cfg.simulate) {
+    int dev0 = 0;
+    if (cudaGetDevice(&dev0) != cudaSuccess || cudaSetDevice(s->device) != cudaSuccess ||
+        cudaDeviceGetStreamPriorityRange(&s->prio_least, &s->prio_greatest) != cudaSuccess ||
+        cudaSetDevice(dev0) != cudaSuccess) {
+      delete s;
+      return SA_ERR_CUDA;
+    }
   }
   s->t0 = std::chrono::steady_clock::now();
   for (uint32_t k = 0; k < s->cfg.slots; ++k) s->workers.emplace_back(&sa_server::worker, s, k);

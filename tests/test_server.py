@@ -132,3 +132,19 @@ def test_finished_requests_are_forgotten(gbsa):
         assert codes == [0, 0, 0, 0] or sorted(codes) == [0] * codes.count(0) + [1] * codes.count(1)
         assert 0 in codes
         assert srv.stats()["tracked"] == 0
+
+
+def test_smaller_requests_get_higher_stream_priority(gbsa):
+    """Size classes up to 256 KiB, 2 MiB, 16 MiB and beyond map to the
+    highest priority and the next three levels (the simulate-mode range is
+    [-5, 0], lower = higher); with size_priority off every request runs at
+    priority 0."""
+    sizes = [1, 256 << 10, (256 << 10) + 1, 2 << 20, (2 << 20) + 1, 16 << 20, (16 << 20) + 1]
+    want = [-5, -5, -4, -4, -3, -3, -2]
+    with gbsa.Server(budget_bytes=1 << 40, slots=2, simulate_ns_per_byte=0.001) as srv:
+        infos = run_all(srv, sizes)
+    assert [i["priority"] for i in infos] == want
+    with gbsa.Server(budget_bytes=1 << 40, slots=2, simulate_ns_per_byte=0.001,
+                     size_priority=False) as srv:
+        infos = run_all(srv, sizes)
+    assert all(i["priority"] == 0 for i in infos)
