@@ -249,7 +249,10 @@ sa_status sa_build_batched_ex(const uint8_t *texts, const uint64_t *offsets,
 /* End-to-end build from HOST memory: copies host_text (HOST, n bytes) to the
  * device on `stream`, builds, and copies SA back to host_sa (HOST, n
  * uint32). Pinned host buffers give the fastest copies; pageable buffers
- * work. Device memory (text, SA and workspace) comes from the library pool. */
+ * work. With both buffers pinned and n <= 4 MiB the copies run as kernels
+ * through the buffers' device mapping instead of on a copy engine, where
+ * they would wait behind the large copies of builds on other streams.
+ * Device memory (text, SA and workspace) comes from the library pool. */
 sa_status sa_build_host(const uint8_t *host_text, uint64_t n, uint32_t *host_sa,
                         gbsa_stream_t stream);
 

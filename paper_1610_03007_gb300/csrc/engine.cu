@@ -193,6 +193,36 @@ struct PoolBuf {
   } while (0)
 
 // Mirror of the first 64 bytes of Ctrl.
+// Pinned host staging for the small readbacks of a build (control block,
+// byte histogram): a kernel writes them into pinned host memory, so a
+// readback does not wait on a copy engine behind the large copies of
+// builds on other streams (a server's concurrent requests). Blocks are
+// allocated once (mapped into every device's address space) and reused.
+constexpr size_t STAGE_BYTES = 16 << 10;
+std::mutex g_stage_mu;
+std::vector<void *> g_stage_free;
+
+struct PinnedStage {
+  void *p = nullptr;
+  cudaError_t get() {
+    if (p) return cudaSuccess;
+    {
+      std::lock_guard<std::mutex> g(g_stage_mu);
+      if (!g_stage_free.empty()) {
+        p = g_stage_free.back();
+        g_stage_free.pop_back();
+        return cudaSuccess;
+      }
+    }
+    return cudaHostAlloc(&p, STAGE_BYTES, cudaHostAllocMapped | cudaHostAllocPortable);
+  }
+  ~PinnedStage() {
+    if (!p) return;
+    std::lock_guard<std::mutex> g(g_stage_mu);
+    g_stage_free.push_back(p);
+  }
+};
+
 struct HostCtrl {
   uint32_t error, err_where, passes, pass_mask;
   uint32_t m_s, g_s, m_l, g_l, upd, pad;
@@ -206,6 +236,8 @@ struct HostCtrl {
 static_assert(sizeof(HostCtrl) == 64, "HostCtrl mirrors the head of Ctrl");
 
 struct Build {
+  PinnedStage stage;            // small readbacks (fetch)
+  bool stage_readbacks = true;  // false: copy-engine readbacks (no host allocation)
   // inputs
   const uint8_t *text = nullptr;
   uint64_t N = 0;
@@ -361,9 +393,25 @@ struct Build {
     return SA_OK;
   }
 
+  // bytes (a multiple of 4, at most STAGE_BYTES) of device memory into
+  // host memory through the pinned stage, by a kernel; synchronises `st`.
+  cudaError_t fetch(void *host, const void *dev, size_t bytes) {
+    if (!stage_readbacks) {
+      cudaError_t e = cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, st);
+      return e == cudaSuccess ? cudaStreamSynchronize(st) : e;
+    }
+    cudaError_t e = stage.get();
+    if (e != cudaSuccess) return e;
+    if (bytes > STAGE_BYTES || bytes % 4) return cudaErrorInvalidValue;
+    e = launch_copy_words(reinterpret_cast<uint32_t *>(stage.p),
+                          reinterpret_cast<const uint32_t *>(dev), bytes / 4, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) memcpy(host, stage.p, bytes);
+    return e;
+  }
+
   sa_status read_ctrl(HostCtrl &hc) {
-    CK(cudaMemcpyAsync(&hc, ctrl, sizeof(HostCtrl), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    CK(fetch(&hc, ctrl, sizeof(HostCtrl)));
     if (hc.error == ERR_TIMEOUT) return SA_ERR_TIMEOUT;
     if (hc.error != ERR_NONE) return SA_ERR_INTERNAL;
     return SA_OK;
@@ -889,8 +937,8 @@ struct Build {
     // One readback of the whole control block (a few KB): error word, the
     // last round's counters, the round state and the per-round records.
     std::vector<uint8_t> raw(sizeof(Ctrl));
-    e = cudaMemcpyAsync(raw.data(), ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    static_assert(sizeof(Ctrl) <= STAGE_BYTES && sizeof(Ctrl) % 4 == 0, "Ctrl fits the stage");
+    e = fetch(raw.data(), ctrl, sizeof(Ctrl));
     cleanup();
     if (e != cudaSuccess) return SA_ERR_CUDA;
     const Ctrl &hctrl = *reinterpret_cast<const Ctrl *>(raw.data());
@@ -1036,8 +1084,7 @@ struct Build {
     });
     if (s != SA_OK) return s;
     uint32_t hh[RADIX];
-    CK(cudaMemcpyAsync(hh, bytehist, sizeof(hh), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    CK(fetch(hh, bytehist, sizeof(hh)));
     s = flush(0, 0);
     if (s != SA_OK) return s;
     uint8_t hcode[RADIX];
@@ -1481,6 +1528,14 @@ GBSA_API size_t sa_batched_workspace_bytes(const uint64_t *offsets, uint32_t cou
 GBSA_API sa_status sa_build_ex(const uint8_t *text, uint64_t n, uint32_t *sa_out,
                                uint32_t *isa_out, void *workspace, size_t ws_bytes,
                                const sa_options *opt, sa_stats *stats, gbsa_stream_t stream) {
+  return gbsa::build_single(text, n, sa_out, isa_out, workspace, ws_bytes, opt, stats, stream,
+                            true);
+}
+
+namespace gbsa {
+sa_status build_single(const uint8_t *text, uint64_t n, uint32_t *sa_out, uint32_t *isa_out,
+                       void *workspace, size_t ws_bytes, const sa_options *opt, sa_stats *stats,
+                       gbsa_stream_t stream, bool stage_readbacks) {
   if (n > SA_MAX_N) return SA_ERR_TOO_LARGE;
   if (n > 0 && (!text || !sa_out)) return SA_ERR_INVALID_ARG;
   if (bad_options(opt)) return SA_ERR_INVALID_ARG;
@@ -1494,6 +1549,7 @@ GBSA_API sa_status sa_build_ex(const uint8_t *text, uint64_t n, uint32_t *sa_out
     return SA_OK;
   }
   Build B;
+  B.stage_readbacks = stage_readbacks;
   B.text = text;
   B.N = n;
   B.S = 1;
@@ -1505,6 +1561,7 @@ GBSA_API sa_status sa_build_ex(const uint8_t *text, uint64_t n, uint32_t *sa_out
   B.st = st;
   return run_with_workspace(B, workspace, ws_bytes);
 }
+}  // namespace gbsa
 
 GBSA_API sa_status sa_build(const uint8_t *text, uint64_t n, uint32_t *sa_out,
                             gbsa_stream_t stream) {
@@ -1545,6 +1602,9 @@ GBSA_API sa_status sa_build_batched(const uint8_t *texts, const uint64_t *offset
   return sa_build_batched_ex(texts, offsets, count, sa_out, nullptr, 0, nullptr, nullptr, stream);
 }
 
+// Largest request whose host copies run as kernels (sa_build_host).
+constexpr uint64_t HOST_KERNEL_COPY_MAX = 4ull << 20;
+
 GBSA_API sa_status sa_build_host(const uint8_t *host_text, uint64_t n, uint32_t *host_sa,
                                  gbsa_stream_t stream) {
   if (n > SA_MAX_N) return SA_ERR_TOO_LARGE;
@@ -1563,12 +1623,35 @@ GBSA_API sa_status sa_build_host(const uint8_t *host_text, uint64_t n, uint32_t 
   uint8_t *d_text = (uint8_t *)buf.p;
   uint32_t *d_sa = (uint32_t *)((uint8_t *)buf.p + tb);
   void *d_ws = (uint8_t *)buf.p + tb + sb;
-  if (cudaMemcpyAsync(d_text, host_text, n, cudaMemcpyHostToDevice, st) != cudaSuccess)
+  // Small requests with pinned host buffers copy by kernels, which read and
+  // write the buffers through their device mapping: a copy engine runs the
+  // copies of all streams in order, so a server's small request would
+  // otherwise wait behind the large copies of concurrent builds. Larger or
+  // pageable buffers take the copy engine.
+  const uint8_t *src_dev = nullptr;
+  uint32_t *dst_dev = nullptr;
+  if (n <= HOST_KERNEL_COPY_MAX) {
+    cudaPointerAttributes at{}, as{};
+    if (cudaPointerGetAttributes(&at, host_text) == cudaSuccess &&
+        cudaPointerGetAttributes(&as, host_sa) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+        as.type == cudaMemoryTypeHost && at.devicePointer && as.devicePointer) {
+      src_dev = (const uint8_t *)at.devicePointer;
+      dst_dev = (uint32_t *)as.devicePointer;
+    }
+    cudaGetLastError();  // a pageable pointer is not an error here
+  }
+  if (src_dev) {
+    if (launch_copy_bytes(d_text, src_dev, n, st) != cudaSuccess) return SA_ERR_CUDA;
+  } else if (cudaMemcpyAsync(d_text, host_text, n, cudaMemcpyHostToDevice, st) != cudaSuccess) {
     return SA_ERR_CUDA;
+  }
   sa_status s = sa_build_ex(d_text, n, d_sa, nullptr, d_ws, wb, nullptr, nullptr, stream);
   if (s != SA_OK) return s;
-  if (cudaMemcpyAsync(host_sa, d_sa, n * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+  if (dst_dev) {
+    if (launch_copy_words(dst_dev, d_sa, n, st) != cudaSuccess) return SA_ERR_CUDA;
+  } else if (cudaMemcpyAsync(host_sa, d_sa, n * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
     return SA_ERR_CUDA;
+  }
   if (cudaStreamSynchronize(st) != cudaSuccess) return SA_ERR_CUDA;
   return SA_OK;
 }

@@ -28,4 +28,39 @@ cudaError_t launch_isa_to_local(const uint32_t *isa, uint32_t *isa_out, uint32_t
   return cudaGetLastError();
 }
 
+// Copies by the SMs instead of a copy engine: small readbacks of the
+// control block into pinned host memory, and the text and SA of small
+// requests between pinned host buffers and the device. A copy engine runs
+// the copies of all streams in order, so a small copy waits behind the
+// large copies of concurrent builds; kernel stores and loads to pinned host
+// memory (mapped into the device's address space) do not.
+__global__ void __launch_bounds__(GA_BLOCK)
+k_copy_words(uint32_t *__restrict__ dst, const uint32_t *__restrict__ src, uint64_t words) {
+  for (uint64_t i = (uint64_t)blockIdx.x * GA_BLOCK + threadIdx.x; i < words;
+       i += (uint64_t)gridDim.x * GA_BLOCK)
+    dst[i] = src[i];
+}
+
+__global__ void __launch_bounds__(GA_BLOCK)
+k_copy_bytes(uint8_t *__restrict__ dst, const uint8_t *__restrict__ src, uint64_t n) {
+  for (uint64_t i = (uint64_t)blockIdx.x * GA_BLOCK + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * GA_BLOCK)
+    dst[i] = src[i];
+}
+
+cudaError_t launch_copy_words(uint32_t *dst, const uint32_t *src, uint64_t words,
+                              cudaStream_t stream) {
+  if (words == 0) return cudaSuccess;
+  const uint64_t want = (words + GA_BLOCK - 1) / GA_BLOCK, cap = (uint64_t)device_sm_count() * 4;
+  k_copy_words<<<(unsigned)(want < cap ? want : cap), GA_BLOCK, 0, stream>>>(dst, src, words);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_bytes(uint8_t *dst, const uint8_t *src, uint64_t n, cudaStream_t stream) {
+  if (n == 0) return cudaSuccess;
+  const uint64_t want = (n + GA_BLOCK - 1) / GA_BLOCK, cap = (uint64_t)device_sm_count() * 4;
+  k_copy_bytes<<<(unsigned)(want < cap ? want : cap), GA_BLOCK, 0, stream>>>(dst, src, n);
+  return cudaGetLastError();
+}
+
 }  // namespace gbsa

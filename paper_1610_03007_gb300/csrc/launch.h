@@ -19,9 +19,21 @@ int device_sm_count();
 // launches on several GPUs, or again after cudaDeviceReset, must set them
 // in each. Thread-safe; concurrent first calls may both set them (harmless).
 cudaError_t ensure_smem_attributes(const void *fn, int smem_bytes, bool max_carveout);
+// sa_build_ex; stage_readbacks false keeps every readback on the copy
+// engine through pageable memory (no pinned host allocation, for
+// sa_build_noalloc).
+sa_status build_single(const uint8_t *text, uint64_t n, uint32_t *sa_out, uint32_t *isa_out,
+                       void *workspace, size_t ws_bytes, const sa_options *opt, sa_stats *stats,
+                       gbsa_stream_t stream, bool stage_readbacks);
 // The tuning table's parameters for a build of this class (tuning.cu); all
 // fields 0 when no entry applies.
 void tuned_params(bool batched, uint32_t bits, uint64_t n, sa_tuned *out);
+
+// Copies by kernels (k_gather.cu): dst/src may be pinned host memory
+// (device-mapped), so the copy does not queue on a copy engine.
+cudaError_t launch_copy_words(uint32_t *dst, const uint32_t *src, uint64_t words,
+                              cudaStream_t stream);
+cudaError_t launch_copy_bytes(uint8_t *dst, const uint8_t *src, uint64_t n, cudaStream_t stream);
 
 // ---- step A0: alphabet (k_alphabet.cu) ----------------------------------
 // hist[256] += occurrences of each byte value in text[0, n). hist must be

@@ -28,7 +28,7 @@
 // captured into a CUDA graph. All calls share the one array: calls whose GPU
 // work overlaps (two host threads, or two streams without ordering between
 // them) race on it and produce garbage, so callers must serialise them.
-#include "../../include/gbsa.h"
+#include "launch.h"
 
 #define GBSA_API extern "C" __attribute__((visibility("default")))
 
@@ -52,6 +52,8 @@ GBSA_API sa_status sa_build_noalloc(const uint8_t *text, uint64_t n, uint32_t *s
     cudaGetLastError();
     return SA_ERR_CUDA;
   }
-  return sa_build_ex(text, n, sa_out, nullptr, ws, NOALLOC_SCRATCH_BYTES, nullptr, nullptr,
-                     stream);
+  // sa_build_ex with its small readbacks on the copy engine: the pinned
+  // staging the other entry points use is a host allocation.
+  return gbsa::build_single(text, n, sa_out, nullptr, ws, NOALLOC_SCRATCH_BYTES, nullptr,
+                            nullptr, stream, false);
 }

@@ -288,3 +288,24 @@ def test_workload_3_full_size_complete(gb, orc):
     assert orc.check_adjacent(t, s, rng.integers(0, n - 1, 200000)) == 0
     j = int(rng.integers(0, n))
     assert orc.suffix_rank(t, int(s[j])) == j
+
+
+@pytest.mark.parametrize("n", [1, 2, 1000, (4 << 20) - 1, 4 << 20, (4 << 20) + 1])
+def test_host_build_with_pinned_buffers(gb, orc, n):
+    """sa_build_host with both host buffers pinned copies by kernels up to
+    4 MiB (their device mapping) and by the copy engine above; with one
+    buffer pageable it always takes the copy engine. Every form gives the
+    device build's SA, on a text that starts at an odd offset of its
+    pinned buffer."""
+    import torch
+    t = gen.text("markov", 31 + n % 7, n + 3)
+    pinned = torch.from_numpy(t).pin_memory()
+    out = torch.empty(n, dtype=torch.int32).pin_memory()
+    want = gb.sa_build(torch.from_numpy(t[3:3 + n]).cuda()).cpu().numpy().view(np.uint32)
+    gb.sa_build_host_ptr(pinned.data_ptr() + 3, n, out.data_ptr())
+    assert np.array_equal(out.numpy().view(np.uint32), want)
+    pageable = np.empty(n, dtype=np.uint32)
+    gb.sa_build_host_ptr(pinned.data_ptr() + 3, n, pageable.ctypes.data)
+    assert np.array_equal(pageable, want)
+    if n <= 4096:
+        assert np.array_equal(want, orc.pd_sa(t[3:3 + n])[0])
