@@ -33,6 +33,11 @@ namespace gbsa {
 // keys[g] = smallest member position, vals[g] = g, info[g] = (start, size,
 // name, head rank): read here in group order (coalesced), so that after
 // the sort one 16-byte record per group is all that is read at random.
+// After round 0 a group's members are in increasing position order (the
+// keys are laid out with positions ascending after a text's tails, which
+// are never survivors, and the sort is stable), so the smallest is the
+// first: one read per group. (Were it not, the order would only be
+// approximate; every order of the groups is valid.)
 __global__ void __launch_bounds__(256) k_group_minpos(const uint64_t *__restrict__ act,
                                                      const uint32_t *__restrict__ gstart,
                                                      const uint32_t *__restrict__ gname,
@@ -43,9 +48,7 @@ __global__ void __launch_bounds__(256) k_group_minpos(const uint64_t *__restrict
   for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < G;
        g += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t s = gstart[g], e = gstart[g + 1];
-    uint32_t mn = 0xFFFFFFFFu;
-    for (uint32_t x = s; x < e; ++x) mn = min(mn, (uint32_t)act[x]);
-    keys[g] = mn;
+    keys[g] = (uint32_t)act[s];
     vals[g] = (uint32_t)g;
     info[g] = make_uint4(s, e - s, gname[g], ghead[g]);
   }
