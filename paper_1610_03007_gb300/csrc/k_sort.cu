@@ -252,8 +252,10 @@ __device__ __forceinline__ void text_keys(OsSmem<OS_ITEMS> &S, const PassArgs &a
     } else if (j >= t) {
       const uint64_t o = (j - t - w0 * cpw) * b;  // bit offset in the window
       const uint32_t w = (uint32_t)(o >> 5), r = (uint32_t)(o & 31);
-      const uint64_t hi = ((uint64_t)words[w] << 32) | words[w + 1];
-      const uint64_t x = r ? (hi << r) | (words[w + 2] >> (32 - r)) : hi;
+      const uint32_t w0v = words[w], w1v = words[w + 1], w2v = words[w + 2];
+      // the 64 bits from bit r of w0v:w1v:w2v, as two funnel shifts
+      const uint64_t x =
+          ((uint64_t)__funnelshift_l(w1v, w0v, r) << 32) | __funnelshift_l(w2v, w1v, r);
       key[k] = a.cb >= 64 ? x : x >> (64 - a.cb);
     } else {  // tail: j + 1 characters left, zero-padded
       const uint64_t p = n - 1 - j;
