@@ -393,18 +393,21 @@ struct Build {
     return SA_OK;
   }
 
-  // bytes (a multiple of 4, at most STAGE_BYTES) of device memory into
-  // host memory through the pinned stage, by a kernel; synchronises `st`.
+  // bytes of device memory into host memory, synchronising `st`: through
+  // the pinned stage by a kernel (a multiple of 4 bytes, at most
+  // STAGE_BYTES), else, or without a stage, on the copy engine.
   cudaError_t fetch(void *host, const void *dev, size_t bytes) {
-    if (!stage_readbacks) {
+    if (stage_readbacks && bytes <= STAGE_BYTES && bytes % 4 == 0 && stage.get() != cudaSuccess) {
+      cudaGetLastError();  // no pinned block to be had: the copy engine instead
+      stage_readbacks = false;
+    }
+    if (!stage_readbacks || bytes > STAGE_BYTES || bytes % 4) {
       cudaError_t e = cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, st);
       return e == cudaSuccess ? cudaStreamSynchronize(st) : e;
     }
-    cudaError_t e = stage.get();
-    if (e != cudaSuccess) return e;
-    if (bytes > STAGE_BYTES || bytes % 4) return cudaErrorInvalidValue;
-    e = launch_copy_words(reinterpret_cast<uint32_t *>(stage.p),
-                          reinterpret_cast<const uint32_t *>(dev), bytes / 4, st);
+    cudaError_t e = launch_copy_words(reinterpret_cast<uint32_t *>(stage.p),
+                                      reinterpret_cast<const uint32_t *>(dev), bytes / 4, st);
+    if (e == cudaSuccess) ++launches;
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) memcpy(host, stage.p, bytes);
     return e;
