@@ -309,3 +309,27 @@ def test_host_build_with_pinned_buffers(gb, orc, n):
     assert np.array_equal(pageable, want)
     if n <= 4096:
         assert np.array_equal(want, orc.pd_sa(t[3:3 + n])[0])
+
+
+@pytest.mark.parametrize("copies", [5, 8, 12, 16])
+@pytest.mark.parametrize("alphabet", [4, 200])
+def test_groups_of_up_to_sixteen_copies(gb, orc, copies, alphabet):
+    """A random block repeated `copies` times (a few substitutions per
+    copy) leaves groups of up to `copies` members for several rounds, whose
+    refine tiles take the counting path (groups of 5 to 64 members) rather
+    than the per-thread path for groups of up to 4. SA and ISA equal the
+    oracle's."""
+    rng = np.random.default_rng(copies * 1000 + alphabet)
+    block = rng.integers(0, alphabet, 20011).astype(np.uint8)
+    parts = []
+    for c in range(copies):
+        b = block.copy()
+        hits = rng.integers(0, b.size, 3)
+        b[hits] = rng.integers(0, alphabet, 3).astype(np.uint8)
+        parts.append(b)
+    t = np.concatenate(parts)
+    want_sa, want_isa, _, _ = orc.pd_sa(t)
+    sa, isa, st, _ = gb.sa_build_ex(dev_text(t), isa=True, refine_shape=1)
+    assert np.array_equal(sa.cpu().numpy().view(np.uint32), want_sa)
+    assert np.array_equal(isa.cpu().numpy().view(np.uint32), want_isa)
+    assert st["rounds"] > 2
