@@ -70,41 +70,55 @@ __global__ void __launch_bounds__(256) k_classify(ClassifyArgs a) {
   }
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t total = (uint64_t)(G > tiles + 1 ? G : tiles + 1);
-  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += stride) {
-    if (x < G) {
-      const uint32_t s = a.gstart[x];
-      const uint32_t e = x + 1 < G ? a.gstart[x + 1] : m;
-      const uint32_t size = e - s;
-      uint32_t name;
-      if (x >= gs) {
-        // A group written by the rename: its name is chosen now that its
-        // size (its SA interval [head, head + size)) is known.
-        const uint32_t head = a.ghead[x], old = a.gold[x];
-        if (a.naming == NAMES_RETAIN)
-          name = (old != NO_NAME && old - head < size) ? old : head + size / 2;
-        else
-          name = head;
-        a.gname[x] = name;
-      } else {
-        name = a.gname[x];
-      }
-      if (size > a.nominal) {
-        const unsigned long long old =
-            atomicAdd(&a.ctrl->rc.large, (1ull << 32) | (unsigned long long)size);
-        const uint32_t k = (uint32_t)(old >> 32), off = (uint32_t)old;
-        a.lg[k] = (uint32_t)x;
-        a.loff[k] = off;
-        a.lbase[k] = a.ghead[x] - off;
-        a.lold[k] = name;
-      }
+  // CL_UNROLL groups per thread and iteration, their starts loaded before
+  // any is used (independent loads in flight).
+  constexpr int CL_UNROLL = 4;
+  for (uint64_t x0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x0 < total;
+       x0 += CL_UNROLL * stride) {
+    uint32_t sv[CL_UNROLL], ev[CL_UNROLL];
+#pragma unroll
+    for (int u = 0; u < CL_UNROLL; ++u) {
+      const uint64_t x = x0 + u * stride;
+      sv[u] = x < G ? a.gstart[x] : 0u;
+      ev[u] = x + 1 < G ? a.gstart[x + 1] : m;
     }
-    if (x <= tiles) a.tfirst[x] = lower_bound_u32(a.gstart, G, (uint32_t)x * a.nominal);
-    if (x == 0) a.gstart[G] = m;
+#pragma unroll
+    for (int u = 0; u < CL_UNROLL; ++u) {
+      const uint64_t x = x0 + u * stride;
+      if (x >= total) break;
+      if (x < G) {
+        const uint32_t size = ev[u] - sv[u];
+        uint32_t name = 0;
+        if (x >= gs) {
+          // A group written by the rename: its name is chosen now that its
+          // size (its SA interval [head, head + size)) is known.
+          const uint32_t head = a.ghead[x], old = a.gold[x];
+          if (a.naming == NAMES_RETAIN)
+            name = (old != NO_NAME && old - head < size) ? old : head + size / 2;
+          else
+            name = head;
+          a.gname[x] = name;
+        }
+        if (size > a.nominal) {
+          if (x < gs) name = a.gname[x];
+          const unsigned long long old =
+              atomicAdd(&a.ctrl->rc.large, (1ull << 32) | (unsigned long long)size);
+          const uint32_t k = (uint32_t)(old >> 32), off = (uint32_t)old;
+          a.lg[k] = (uint32_t)x;
+          a.loff[k] = off;
+          a.lbase[k] = a.ghead[x] - off;
+          a.lold[k] = name;
+        }
+      }
+      if (x <= tiles) a.tfirst[x] = lower_bound_u32(a.gstart, G, (uint32_t)x * a.nominal);
+      if (x == 0) a.gstart[G] = m;
+    }
   }
 }
 
 cudaError_t launch_classify(const ClassifyArgs &a, int num_sms, cudaStream_t stream) {
-  k_classify<<<num_sms * 4, 256, 0, stream>>>(a);
+  // One full wave (8 blocks of 256 threads per SM).
+  k_classify<<<num_sms * 8, 256, 0, stream>>>(a);
   return cudaGetLastError();
 }
 
