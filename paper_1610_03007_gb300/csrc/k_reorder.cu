@@ -45,51 +45,106 @@ __global__ void __launch_bounds__(256) k_group_minpos(const uint64_t *__restrict
                                                      uint32_t G, uint64_t *__restrict__ keys,
                                                      uint32_t *__restrict__ vals,
                                                      uint4 *__restrict__ info) {
-  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < G;
-       g += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t s = gstart[g], e = gstart[g + 1];
-    keys[g] = (uint32_t)act[s];
-    vals[g] = (uint32_t)g;
-    info[g] = make_uint4(s, e - s, gname[g], ghead[g]);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t g0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g0 < G; g0 += 4 * stride) {
+    uint32_t s[4], e[4];  // four groups' loads in flight before any is used
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint64_t g = g0 + u * stride;
+      s[u] = g < G ? gstart[g] : 0u;
+      e[u] = g < G ? gstart[g + 1] : 0u;
+    }
+    uint64_t first[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) first[u] = g0 + u * stride < G ? act[s[u]] : 0ull;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint64_t g = g0 + u * stride;
+      if (g >= G) break;
+      keys[g] = (uint32_t)first[u];
+      vals[g] = (uint32_t)g;
+      info[g] = make_uint4(s[u], e[u] - s[u], gname[g], ghead[g]);
+    }
   }
 }
 
 // The records in the new order (one random 16-byte read per group), and
 // the sizes for the scan.
+// RG_UNROLL groups per thread and iteration in the two gathering kernels
+// below: their loads are issued before any is used, so each thread keeps
+// several random reads in flight.
+constexpr int RG_UNROLL = 4;
+
 __global__ void __launch_bounds__(256) k_group_sizes(const SortPlan *__restrict__ plan,
                                                     const uint4 *__restrict__ info, uint32_t G,
                                                     uint4 *__restrict__ info_new,
                                                     uint32_t *__restrict__ sizes, Ctrl *ctrl) {
   const uint32_t *order = plan->vfinal;
-  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < G;
-       x += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t g = order[x];
-    if (g >= G) {  // never taken unless a logic error
-      raise_error(ctrl, ERR_INTERNAL, 17);
-      return;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t x0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x0 < G;
+       x0 += RG_UNROLL * stride) {
+    uint32_t g[RG_UNROLL];
+#pragma unroll
+    for (int u = 0; u < RG_UNROLL; ++u) g[u] = x0 + u * stride < G ? order[x0 + u * stride] : 0u;
+    uint4 r[RG_UNROLL];
+#pragma unroll
+    for (int u = 0; u < RG_UNROLL; ++u) {
+      if (g[u] >= G) {  // never taken unless a logic error
+        raise_error(ctrl, ERR_INTERNAL, 17);
+        return;
+      }
+      r[u] = x0 + u * stride < G ? info[g[u]] : make_uint4(0u, 0u, 0u, 0u);
     }
-    const uint4 r = info[g];
-    info_new[x] = r;
-    sizes[x] = r.y;
+#pragma unroll
+    for (int u = 0; u < RG_UNROLL; ++u) {
+      const uint64_t x = x0 + u * stride;
+      if (x < G) {
+        info_new[x] = r[u];
+        sizes[x] = r[u].y;
+      }
+    }
   }
 }
 
 __global__ void __launch_bounds__(256) k_regroup(RegroupArgs a) {
-  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < a.G;
-       x += (uint64_t)gridDim.x * blockDim.x) {
-    const uint4 r = a.info[x];  // (start, size, name, head) of new group x
-    const uint32_t s = r.x, z = r.y;
-    const uint32_t ns = a.ends[x] - z;
-    if ((uint64_t)ns + z > a.m || (uint64_t)s + z > a.m) {  // never taken unless a logic error
-      raise_error(a.ctrl, ERR_INTERNAL, 18);
-      return;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t x0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x0 < a.G;
+       x0 += RG_UNROLL * stride) {
+    uint4 r[RG_UNROLL];  // (start, size, name, head) of new group x
+    uint32_t end[RG_UNROLL];
+#pragma unroll
+    for (int u = 0; u < RG_UNROLL; ++u) {
+      const uint64_t x = x0 + u * stride;
+      r[u] = x < a.G ? a.info[x] : make_uint4(0u, 0u, 0u, 0u);
+      end[u] = x < a.G ? a.ends[x] : 0u;
     }
-    a.gstart_out[x] = ns;
-    a.gname_out[x] = r.z;
-    a.ghead_out[x] = r.w;
-    for (uint32_t k = 0; k < z; ++k)
-      a.act_out[ns + k] = (x << 32) | (uint32_t)a.act_in[s + k];
-    if (x == 0) a.gstart_out[a.G] = a.m;
+    // The first two members of each group (most groups are pairs), loaded
+    // together; longer groups read the rest in their own loop.
+    uint64_t e0[RG_UNROLL], e1[RG_UNROLL];
+#pragma unroll
+    for (int u = 0; u < RG_UNROLL; ++u) {
+      const uint32_t s = r[u].x, z = r[u].y;
+      // never taken unless a logic error
+      if ((uint64_t)end[u] > a.m || (uint64_t)s + z > a.m || z > end[u]) {
+        raise_error(a.ctrl, ERR_INTERNAL, 18);
+        return;
+      }
+      e0[u] = z > 0 ? a.act_in[s] : 0ull;
+      e1[u] = z > 1 ? a.act_in[s + 1] : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < RG_UNROLL; ++u) {
+      const uint64_t x = x0 + u * stride;
+      if (x >= a.G) break;
+      const uint32_t s = r[u].x, z = r[u].y, ns = end[u] - z;
+      a.gstart_out[x] = ns;
+      a.gname_out[x] = r[u].z;
+      a.ghead_out[x] = r[u].w;
+      if (z > 0) a.act_out[ns] = (x << 32) | (uint32_t)e0[u];
+      if (z > 1) a.act_out[ns + 1] = (x << 32) | (uint32_t)e1[u];
+      for (uint32_t k = 2; k < z; ++k) a.act_out[ns + k] = (x << 32) | (uint32_t)a.act_in[s + k];
+      if (x == 0) a.gstart_out[a.G] = a.m;
+    }
   }
 }
 
