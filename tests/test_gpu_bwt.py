@@ -22,7 +22,7 @@ def gb():
 def gpu_bwt(gb, t):
     import torch
     a = np.frombuffer(bytes(t), dtype=np.uint8) if isinstance(t, (bytes, bytearray)) else t
-    d = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    d = torch.from_numpy(np.array(a, dtype=np.uint8, copy=True)).cuda()
     sa = gb.sa_build(d)
     bwt, prim = gb.sa_bwt(d, sa)
     torch.cuda.synchronize()
