@@ -679,8 +679,9 @@ SERVE_LO, SERVE_HI = 10 << 10, 64 << 20
 
 
 def run_serving(args, emit=True):
-    """Workload 5: Poisson arrivals of SA builds at each offered rate, sizes
-    log-uniform in [10 KiB, 64 MiB], a fair coin choosing uniform DNA or
+    """Workload 5: Poisson arrivals of SA builds at each offered rate (rate
+    0: a burst, every request submitted at once), sizes log-uniform in
+    [10 KiB, 64 MiB] (--serve-max lowers the top), a fair coin choosing uniform DNA or
     i.i.d. Zipf(1.1) bytes; continuous batching under a 100 GB device budget
     (sa_server_*). Each request's text is a slice of one of two 64 MiB
     buffers drawn from those two distributions (same statistics as a fresh
@@ -704,12 +705,19 @@ def run_serving(args, emit=True):
     # Pinned result buffers, as a serving client would hand the server (a
     # pageable destination turns each result copy into a staged one): one
     # arena large enough for the largest rate's requests, carved per request.
-    streams = {lam: gen.request_stream(SERVE_SEED + int(lam), count, lam, SERVE_LO, SERVE_HI)
-               for lam in rates}
+    hi = args.serve_max or SERVE_HI
+    if not SERVE_LO < hi <= SERVE_HI:
+        raise SystemExit(f"--serve-max must lie in ({SERVE_LO}, {SERVE_HI}]")
+    streams = {}
+    for lam in rates:
+        arr, sizes, kinds = gen.request_stream(SERVE_SEED + int(lam), count, lam or 1.0,
+                                               SERVE_LO, hi)
+        streams[lam] = (arr if lam > 0 else np.zeros_like(arr), sizes, kinds)
     arena_n = max(int(np.sum(v[1])) for v in streams.values())
     arena = torch.empty(arena_n, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
     out_rates = []
-    with gbsa.Server(budget_bytes=100 * 10**9, slots=args.slots) as srv:
+    with gbsa.Server(budget_bytes=100 * 10**9, slots=args.slots,
+                     merge_requests=args.merge_requests) as srv:
         # Warm-up: module, streams, and the library's memory pool grown to
         # one largest request per slot, as a server that has been running a
         # while holds it (growing the pool inside a timed rate would charge
@@ -722,6 +730,7 @@ def run_serving(args, emit=True):
             arr, sizes, kinds = streams[lam]
             outs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
             tickets = []
+            st0 = srv.stats()
             t0 = time.perf_counter()
             for k in range(count):
                 delay = t0 + float(arr[k]) - time.perf_counter()
@@ -744,14 +753,19 @@ def run_serving(args, emit=True):
                               "achieved_rps": count / span,
                               "input_MB": total / 1e6,
                               "peak_in_flight": st["peak_in_flight"],
+                              "builds": st["builds"] - st0["builds"],
+                              "merged_requests": st["merged"] - st0["merged"],
                               "peak_GB_in_use": st["peak_bytes_in_use"] / 1e9})
     del arena, pools
     line = {"metric": "serving latency p50/p99 (ms) and input MB/s per offered rate",
             "unit": "ms", "higher_is_better": False, "data": "synthetic",
-            "config": {"workload": "Poisson arrivals, sizes log-uniform [10 KiB, 64 MiB], "
+            "config": {"workload": "Poisson arrivals (rate 0: a burst, every request "
+                                   "submitted at once), sizes log-uniform "
+                                   f"[10 KiB, {hi / 2**20:g} MiB], "
                                    "50/50 uniform DNA / Zipf(1.1) bytes, 100 GB budget",
                        "host_buffers": "texts and results in pinned host memory",
-                       "slots": args.slots, "requests_per_rate": count, "seed": SERVE_SEED},
+                       "slots": args.slots, "requests_per_rate": count, "seed": SERVE_SEED,
+                       "merge_requests": max(args.merge_requests, 1)},
             "rates": out_rates}
     if emit:
         print(json.dumps(line), flush=True)
@@ -836,8 +850,15 @@ def main():
     ap.add_argument("--recipe", default="zipf_repeats",
                     help="plain workload: zipf_repeats (configuration 2), markov (3), dna, ...")
     ap.add_argument("--requests", type=int, default=0, help="requests per rate (serving)")
-    ap.add_argument("--rates", default="", help="comma-separated offered rates (serving)")
+    ap.add_argument("--rates", default="",
+                    help="comma-separated offered rates (serving; 0 = a burst: every request "
+                         "submitted at once)")
     ap.add_argument("--slots", type=int, default=16, help="server slots (serving)")
+    ap.add_argument("--serve-max", type=int, default=0,
+                    help="largest request in bytes (serving; 0 = 64 MiB)")
+    ap.add_argument("--merge-requests", type=int, default=0,
+                    help="most queued small requests one build takes (serving; 0 or 1 = "
+                         "none merged, the library default)")
     ap.add_argument("--batch-count", type=int, default=0, help="texts in the batched workload")
     ap.add_argument("--n", type=int, default=0, help="override the text length (testing)")
     ap.add_argument("--h0", type=int, default=0,

@@ -256,6 +256,27 @@ sa_status sa_build_batched_ex(const uint8_t *texts, const uint64_t *offsets,
 sa_status sa_build_host(const uint8_t *host_text, uint64_t n, uint32_t *host_sa,
                         gbsa_stream_t stream);
 
+/* sa_build_host for `count` texts at once, built together as one batch
+ * (sa_build_batched: shared doubling rounds, each text leaving them as soon
+ * as all its suffixes are unique), the form the server uses to merge the
+ * small requests queued at one moment into one build.
+ * host_texts : HOST array of count HOST pointers; text k has lengths[k]
+ *              bytes (its pointer may be NULL when lengths[k] = 0).
+ * lengths    : HOST, count uint64.
+ * host_sas   : HOST array of count HOST pointers; host_sas[k] receives the
+ *              SA of text k (lengths[k] uint32, local indices).
+ * The texts are gathered into one device buffer and the SAs scattered
+ * back: when the total is at most 4 MiB and every buffer is pinned, by one
+ * kernel launch per 64 texts in each direction (through the buffers'
+ * device mapping); otherwise one copy-engine copy per text and direction.
+ * Device memory comes from the library pool; returns after the stream has
+ * synchronised. SA_ERR_INVALID_ARG for count = 0 or a NULL array or
+ * non-empty text's pointer; SA_ERR_TOO_LARGE for count > 2^20 or a total
+ * above SA_MAX_N. Each SA is exactly sa_build's for that text. */
+sa_status sa_build_batched_host(const uint8_t *const *host_texts, const uint64_t *lengths,
+                                uint32_t *const *host_sas, uint32_t count,
+                                gbsa_stream_t stream);
+
 /* Stable LSD radix sort of (key, value) pairs by key bits
  * [begin_bit, end_bit), the building block of the sort step (Algorithm 1,
  * "Sort triples by name pair"). One-sweep passes of 8-bit digits with
@@ -345,7 +366,11 @@ sa_status sa_build_noalloc(const uint8_t *text, uint64_t n, uint32_t *sa_out,
  * (rank and ISA state) resident on the device for all its rounds and frees
  * them when it completes, so requests that arrive while others run are
  * admitted as slots and memory free up, and the builds in flight overlap
- * on the device. Every request's result is exactly sa_build's. */
+ * on the device. With merge_requests >= 2, a worker that takes a small
+ * request also takes the small requests queued directly behind it and
+ * builds them as one batch (sa_build_batched_host): one launch sequence and one set of doubling
+ * rounds for all of them, each text leaving the rounds once its suffixes
+ * are unique. Every request's result is exactly sa_build's. */
 typedef struct sa_server sa_server;
 
 typedef struct {
@@ -363,6 +388,16 @@ typedef struct {
    * blocks of large builds in flight and its latency stays near that of a
    * build alone. 1: every request on a stream of default priority. */
   uint32_t size_priority;
+  /* Most requests one build takes: a worker that takes a request of at
+   * most 256 KiB also takes the requests queued directly behind it while
+   * each is at most 256 KiB, the batch stays within 4 MiB of text, its
+   * footprint (text, SA and batched workspace) fits in the budget and it
+   * holds no more than the worker's share of the queue (the queued requests
+   * divided among the idle workers, this one included, rounded up), so
+   * requests merge only when the queue outgrows the idle workers. The batch
+   * is built by sa_build_batched_host. Queue order is kept. 0 (default)
+   * or 1 = every request built alone; values above 64 mean 64. */
+  uint32_t merge_requests;
 } sa_server_config;
 
 typedef struct {
@@ -372,13 +407,16 @@ typedef struct {
   double submit_s, start_s, done_s; /* seconds since the server was created     */
   int32_t priority;           /* CUDA stream priority it ran at (lower = higher; */
                               /* in simulate mode the range [-5, 0] is assumed) */
+  uint32_t batch;             /* requests in the build it ran in (1 = alone)     */
 } sa_request_info;
 
 typedef struct {
   uint64_t submitted, completed;
   uint64_t bytes_in_use, peak_bytes_in_use;
-  uint32_t in_flight, peak_in_flight, queued;
+  uint32_t in_flight, peak_in_flight, queued;  /* requests (not builds)      */
   uint32_t tracked;           /* requests held: queued, running or uncollected */
+  uint64_t builds;            /* builds started (a merged batch counts once)   */
+  uint64_t merged;            /* requests that ran in a batch of two or more   */
 } sa_server_stats;
 
 /* Device bytes a request of n characters holds while it runs (text, SA and

@@ -27,7 +27,7 @@ SA_MAX_ROUNDS = 64
 
 # Symbols include/gbsa.h declares; the loader checks that all are exported.
 EXPORTED = ("sa_build", "sa_workspace_bytes", "sa_build_ex", "sa_build_batched",
-            "sa_batched_workspace_bytes", "sa_build_batched_ex", "sa_build_host",
+            "sa_batched_workspace_bytes", "sa_build_batched_ex", "sa_build_host", "sa_build_batched_host",
             "sa_sort_pairs", "sa_sort_workspace_bytes", "sa_status_string",
             "sa_build_noalloc", "sa_request_footprint", "sa_server_create", "sa_server_submit",
             "sa_server_poll", "sa_server_wait", "sa_server_get_stats", "sa_server_destroy",
@@ -102,25 +102,29 @@ class Stats(ctypes.Structure):
 class ServerConfig(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_uint64), ("slots", ctypes.c_uint32),
                 ("device", ctypes.c_int32), ("simulate", ctypes.c_uint32),
-                ("simulate_ns_per_byte", ctypes.c_double), ("size_priority", ctypes.c_uint32)]
+                ("simulate_ns_per_byte", ctypes.c_double), ("size_priority", ctypes.c_uint32),
+                ("merge_requests", ctypes.c_uint32)]
 
 
 class RequestInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("n", ctypes.c_uint64), ("slot", ctypes.c_uint32),
                 ("submit_s", ctypes.c_double), ("start_s", ctypes.c_double),
-                ("done_s", ctypes.c_double), ("priority", ctypes.c_int32)]
+                ("done_s", ctypes.c_double), ("priority", ctypes.c_int32),
+                ("batch", ctypes.c_uint32)]
 
     def to_dict(self) -> dict:
         return {"status": self.status, "n": self.n, "slot": self.slot,
                 "submit_s": self.submit_s, "start_s": self.start_s, "done_s": self.done_s,
-                "latency_s": self.done_s - self.submit_s, "priority": self.priority}
+                "latency_s": self.done_s - self.submit_s, "priority": self.priority,
+                "batch": self.batch}
 
 
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
                 ("bytes_in_use", ctypes.c_uint64), ("peak_bytes_in_use", ctypes.c_uint64),
                 ("in_flight", ctypes.c_uint32), ("peak_in_flight", ctypes.c_uint32),
-                ("queued", ctypes.c_uint32), ("tracked", ctypes.c_uint32)]
+                ("queued", ctypes.c_uint32), ("tracked", ctypes.c_uint32),
+                ("builds", ctypes.c_uint64), ("merged", ctypes.c_uint64)]
 
 
 _lib = None
@@ -151,6 +155,7 @@ def load(path: str | None = None):
     lib.sa_build_batched_ex.argtypes = [vp, vp, u32, vp, vp, sz, ctypes.POINTER(Options),
                                         ctypes.POINTER(Stats), vp]
     lib.sa_build_host.argtypes = [vp, u64, vp, vp]
+    lib.sa_build_batched_host.argtypes = [vp, vp, vp, u32, vp]
     lib.sa_build_noalloc.argtypes = [vp, u64, vp, vp]
     lib.sa_sort_pairs.argtypes = [vp, vp, u64, u32, u32, vp, sz, vp]
     lib.sa_bwt.argtypes = [vp, u64, vp, vp, vp, vp]
@@ -189,7 +194,7 @@ def load(path: str | None = None):
     lib.sa_status_string.argtypes = [ctypes.c_int]
     lib.sa_status_string.restype = ctypes.c_char_p
     for f in ("sa_build", "sa_build_ex", "sa_build_batched", "sa_build_batched_ex",
-              "sa_build_host", "sa_sort_pairs", "sa_build_noalloc"):
+              "sa_build_host", "sa_build_batched_host", "sa_sort_pairs", "sa_build_noalloc"):
         getattr(lib, f).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -358,6 +363,24 @@ def sa_build_host_ptr(host_text_ptr: int, n: int, host_sa_ptr: int, stream=None)
     _check(load().sa_build_host(host_text_ptr, n, host_sa_ptr, _stream(stream)), "sa_build_host")
 
 
+def sa_build_batched_host(texts, outs=None, stream=None) -> list:
+    """sa_build_host for several host texts built as one batch: texts is a
+    sequence of uint8 numpy arrays (or objects with .ctypes, e.g. pinned
+    torch tensors' numpy views); returns one uint32 SA per text (outs, when
+    given, are filled instead)."""
+    lib = load()
+    arrs = [np.ascontiguousarray(t, dtype=np.uint8) for t in texts]
+    if outs is None:
+        outs = [np.empty(a.size, dtype=np.uint32) for a in arrs]
+    count = len(arrs)
+    assert len(outs) == count
+    tp = (ctypes.c_void_p * max(count, 1))(*[a.ctypes.data if a.size else None for a in arrs])
+    sp = (ctypes.c_void_p * max(count, 1))(*[o.ctypes.data if o.size else None for o in outs])
+    ln = (ctypes.c_uint64 * max(count, 1))(*[a.size for a in arrs])
+    _check(lib.sa_build_batched_host(tp, ln, sp, count, _stream(stream)), "sa_build_batched_host")
+    return outs
+
+
 def sa_sort_pairs(keys, vals, begin_bit=0, end_bit=64, workspace=None, stream=None):
     """Stable in-place LSD radix sort of (int64 keys as uint64, int32 vals as
     uint32) CUDA tensors by key bits [begin_bit, end_bit)."""
@@ -480,13 +503,17 @@ class Server:
     buffer (numpy uint32) is kept alive here until the request is waited on.
     size_priority: smaller requests run on higher-priority CUDA streams
     (sa_server_config.size_priority); the info dict reports the priority.
+    merge_requests: most queued small requests one build takes
+    (sa_server_config.merge_requests; 0 or 1 = none merged, the default);
+    the info dict reports the batch size.
     """
 
     def __init__(self, budget_bytes: int = 0, slots: int = 0, device: int = -1,
-                 simulate_ns_per_byte: float = 0.0, size_priority: bool = True):
+                 simulate_ns_per_byte: float = 0.0, size_priority: bool = True,
+                 merge_requests: int = 0):
         self._lib = load()
         cfg = ServerConfig(budget_bytes, slots, device, 1 if simulate_ns_per_byte > 0 else 0,
-                           simulate_ns_per_byte, 0 if size_priority else 1)
+                           simulate_ns_per_byte, 0 if size_priority else 1, merge_requests)
         h = ctypes.c_void_p()
         _check(self._lib.sa_server_create(ctypes.byref(cfg), ctypes.byref(h)), "sa_server_create")
         self._h = h

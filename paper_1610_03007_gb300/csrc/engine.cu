@@ -41,6 +41,7 @@
 
 #include "../../include/gbsa.h"
 #include "launch.h"
+#include "segcopy.h"
 
 #define GBSA_API extern "C" __attribute__((visibility("default")))
 
@@ -1654,6 +1655,89 @@ GBSA_API sa_status sa_build_host(const uint8_t *host_text, uint64_t n, uint32_t 
     if (launch_copy_words(dst_dev, d_sa, n, st) != cudaSuccess) return SA_ERR_CUDA;
   } else if (cudaMemcpyAsync(host_sa, d_sa, n * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
     return SA_ERR_CUDA;
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) return SA_ERR_CUDA;
+  return SA_OK;
+}
+
+GBSA_API sa_status sa_build_batched_host(const uint8_t *const *host_texts, const uint64_t *lengths,
+                                         uint32_t *const *host_sas, uint32_t count,
+                                         gbsa_stream_t stream) {
+  if (count == 0 || !host_texts || !lengths || !host_sas) return SA_ERR_INVALID_ARG;
+  if (count > (1u << 20)) return SA_ERR_TOO_LARGE;
+  std::vector<uint64_t> off((size_t)count + 1, 0);
+  for (uint32_t k = 0; k < count; ++k) {
+    if (lengths[k] > SA_MAX_N) return SA_ERR_TOO_LARGE;
+    if (lengths[k] > 0 && (!host_texts[k] || !host_sas[k])) return SA_ERR_INVALID_ARG;
+    off[k + 1] = off[k] + lengths[k];
+    if (off[k + 1] > SA_MAX_N) return SA_ERR_TOO_LARGE;
+  }
+  const uint64_t N = off[count];
+  if (N == 0) return SA_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t tb = align256(N), sb = align256(N * 4);
+  const size_t wb = sa_batched_workspace_bytes(off.data(), count);
+  PoolBuf buf;
+  buf.st = st;
+  if (pool_alloc(&buf.p, tb + sb + wb, st) != cudaSuccess) {
+    buf.p = nullptr;
+    cudaGetLastError();
+    return SA_ERR_OOM;
+  }
+  uint8_t *d_text = (uint8_t *)buf.p;
+  uint32_t *d_sa = (uint32_t *)((uint8_t *)buf.p + tb);
+  void *d_ws = (uint8_t *)buf.p + tb + sb;
+  // As in sa_build_host: a small batch whose buffers are all pinned copies
+  // by kernels (one launch per SegCopy::MAX texts each way), so it does not
+  // queue behind the copy-engine traffic of other streams; otherwise one
+  // copy-engine copy per text and direction.
+  std::vector<void *> src_dev, dst_dev;
+  bool mapped = N <= HOST_KERNEL_COPY_MAX;
+  if (mapped) {
+    src_dev.assign(count, nullptr);
+    dst_dev.assign(count, nullptr);
+    for (uint32_t k = 0; k < count && mapped; ++k) {
+      if (lengths[k] == 0) continue;
+      cudaPointerAttributes at{}, as{};
+      mapped = cudaPointerGetAttributes(&at, host_texts[k]) == cudaSuccess &&
+               cudaPointerGetAttributes(&as, host_sas[k]) == cudaSuccess &&
+               at.type == cudaMemoryTypeHost && as.type == cudaMemoryTypeHost &&
+               at.devicePointer && as.devicePointer;
+      src_dev[k] = at.devicePointer;
+      dst_dev[k] = as.devicePointer;
+    }
+    cudaGetLastError();  // a pageable pointer is not an error here
+  }
+  auto kernel_copies = [&](bool to_flat) -> cudaError_t {
+    for (uint32_t k0 = 0; k0 < count; k0 += SegCopy::MAX) {
+      SegCopy t{};
+      t.count = std::min<uint32_t>(SegCopy::MAX, count - k0);
+      for (uint32_t j = 0; j < t.count; ++j) t.ext[j] = to_flat ? src_dev[k0 + j] : dst_dev[k0 + j];
+      for (uint32_t j = 0; j <= t.count; ++j) t.off[j] = off[k0 + j];
+      const cudaError_t e = launch_copy_segments(to_flat ? (void *)d_text : (void *)d_sa, t,
+                                                 to_flat ? 1 : 4, to_flat, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  if (mapped) {
+    if (kernel_copies(true) != cudaSuccess) return SA_ERR_CUDA;
+  } else {
+    for (uint32_t k = 0; k < count; ++k)
+      if (lengths[k] && cudaMemcpyAsync(d_text + off[k], host_texts[k], lengths[k],
+                                        cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return SA_ERR_CUDA;
+  }
+  const sa_status s =
+      sa_build_batched_ex(d_text, off.data(), count, d_sa, d_ws, wb, nullptr, nullptr, stream);
+  if (s != SA_OK) return s;
+  if (mapped) {
+    if (kernel_copies(false) != cudaSuccess) return SA_ERR_CUDA;
+  } else {
+    for (uint32_t k = 0; k < count; ++k)
+      if (lengths[k] && cudaMemcpyAsync(host_sas[k], d_sa + off[k], lengths[k] * 4,
+                                        cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return SA_ERR_CUDA;
   }
   if (cudaStreamSynchronize(st) != cudaSuccess) return SA_ERR_CUDA;
   return SA_OK;

@@ -5,6 +5,7 @@
 //
 // Bound: HBM; 8 bytes per character.
 #include "launch.h"
+#include "segcopy.h"
 
 namespace gbsa {
 
@@ -60,6 +61,54 @@ cudaError_t launch_copy_bytes(uint8_t *dst, const uint8_t *src, uint64_t n, cuda
   if (n == 0) return cudaSuccess;
   const uint64_t want = (n + GA_BLOCK - 1) / GA_BLOCK, cap = (uint64_t)device_sm_count() * 4;
   k_copy_bytes<<<(unsigned)(want < cap ? want : cap), GA_BLOCK, 0, stream>>>(dst, src, n);
+  return cudaGetLastError();
+}
+
+// The host copies of a merged batch of small requests in one launch: block
+// row y copies segment y between the batch's flat device buffer and that
+// request's pinned host buffer.
+template <typename T, bool TO_FLAT>
+__global__ void __launch_bounds__(GA_BLOCK) k_copy_segments(T *__restrict__ flat, SegCopy t) {
+  const uint32_t s = blockIdx.y;
+  const uint64_t base = t.off[s], len = t.off[s + 1] - base;
+  T *ext = static_cast<T *>(t.ext[s]);
+  for (uint64_t i = (uint64_t)blockIdx.x * GA_BLOCK + threadIdx.x; i < len;
+       i += (uint64_t)gridDim.x * GA_BLOCK) {
+    if (TO_FLAT)
+      flat[base + i] = ext[i];
+    else
+      ext[i] = flat[base + i];
+  }
+}
+
+cudaError_t launch_copy_segments(void *flat, const SegCopy &t, uint32_t elem_bytes, bool to_flat,
+                                 cudaStream_t stream) {
+  if (t.count == 0 || t.count > SegCopy::MAX || (elem_bytes != 1 && elem_bytes != 4))
+    return cudaErrorInvalidValue;
+  uint64_t longest = 0;
+  for (uint32_t s = 0; s < t.count; ++s) {
+    if (t.off[s + 1] < t.off[s]) return cudaErrorInvalidValue;
+    const uint64_t len = t.off[s + 1] - t.off[s];
+    if (len && !t.ext[s]) return cudaErrorInvalidValue;
+    if (len > longest) longest = len;
+  }
+  if (longest == 0) return cudaSuccess;
+  // About four blocks per SM over the whole batch.
+  const uint64_t want = (longest + GA_BLOCK - 1) / GA_BLOCK;
+  uint64_t cap = (uint64_t)device_sm_count() * 4 / t.count;
+  if (cap == 0) cap = 1;
+  const dim3 grid((unsigned)(want < cap ? want : cap), t.count);
+  if (elem_bytes == 1) {
+    if (to_flat)
+      k_copy_segments<uint8_t, true><<<grid, GA_BLOCK, 0, stream>>>((uint8_t *)flat, t);
+    else
+      k_copy_segments<uint8_t, false><<<grid, GA_BLOCK, 0, stream>>>((uint8_t *)flat, t);
+  } else {
+    if (to_flat)
+      k_copy_segments<uint32_t, true><<<grid, GA_BLOCK, 0, stream>>>((uint32_t *)flat, t);
+    else
+      k_copy_segments<uint32_t, false><<<grid, GA_BLOCK, 0, stream>>>((uint32_t *)flat, t);
+  }
   return cudaGetLastError();
 }
 

@@ -18,7 +18,20 @@
 // large builds in flight, so small requests are not queued behind whole
 // kernels of large ones.
 //
+// Merged builds (sa_server_config.merge_requests >= 2): a worker that takes a
+// small head request also takes the small requests queued directly behind
+// it and builds them all as one batch (sa_build_batched_host). They share
+// one launch sequence and its doubling rounds; each text drops out of the
+// rounds as soon as its suffixes are unique, so the batch costs about one
+// small build instead of one per request. A worker takes only its share of
+// the queue (the queued requests divided among it and the workers idle
+// beside it), so requests that idle workers can start at once on their own
+// streams are not serialised behind one batch: merging sets in when the
+// queue outgrows the idle workers. Only requests already queued join: a
+// request that arrives while a batch runs waits for the next free worker.
+//
 // The paper has no serving layer; this is the runtime around its method.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -38,6 +51,16 @@ namespace {
 constexpr uint64_t DEFAULT_BUDGET = 100ull * 1000 * 1000 * 1000;  // 100 GB
 constexpr uint32_t DEFAULT_SLOTS = 8;
 constexpr uint32_t MAX_SLOTS = 64;
+// Merging: requests of up to MERGE_MAX_N characters (the highest-priority
+// size class), at most MERGE_TOTAL_MAX in one build (the largest batch whose
+// host copies run as kernels), at most MAX_MERGE requests (one copy launch
+// per direction). Off by default (DEFAULT_MERGE = 1): on a GB300 it raised a
+// burst of small requests from 26k to 110k requests/s, but it did not help
+// an overloaded mix of small and large requests.
+constexpr uint64_t MERGE_MAX_N = 256ull << 10;
+constexpr uint64_t MERGE_TOTAL_MAX = 4ull << 20;
+constexpr uint32_t DEFAULT_MERGE = 1;
+constexpr uint32_t MAX_MERGE = 64;
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -54,6 +77,14 @@ int size_class(uint64_t n) {
 int class_priority(int c, int least, int greatest) {
   const int p = greatest + c;
   return p < least ? p : least;
+}
+
+// Device bytes of one batched build of texts with these offsets (text, SA
+// and the batched workspace), the merged counterpart of sa_request_footprint.
+size_t merged_footprint(const std::vector<uint64_t> &off) {
+  const uint64_t N = off.back();
+  return align256(N) + align256(N * 4) +
+         sa_batched_workspace_bytes(off.data(), (uint32_t)(off.size() - 1));
 }
 
 struct Request {
@@ -81,6 +112,7 @@ struct sa_server {
   uint64_t next_ticket = 1;
   uint64_t in_use = 0;
   uint32_t in_flight = 0;
+  uint32_t busy = 0;  // workers running a build
   sa_server_stats stats{};
   bool stop = false;
   std::vector<std::thread> workers;
@@ -106,6 +138,38 @@ struct sa_server {
     return cfg.size_priority == 0 ? class_priority(c, prio_least, prio_greatest) : 0;
   }
 
+  // Takes the head request and, when it is small, the small requests
+  // queued directly behind it while the merged build fits the budget, up to
+  // this worker's share of the queue. Called with `mu` held, the head
+  // admissible and this worker not yet counted in `busy`; returns the bytes
+  // to charge against the budget.
+  size_t take_batch(std::vector<Request *> &batch, std::vector<uint64_t> &off) {
+    const uint64_t queued = queue.size();
+    const uint64_t idle = cfg.slots > busy ? cfg.slots - busy : 1;  // this worker included
+    const uint64_t share = (queued + idle - 1) / idle;
+    Request *head = queue.front();
+    queue.pop_front();
+    batch.assign(1, head);
+    size_t charge = head->footprint;
+    const uint64_t limit = std::min<uint64_t>(cfg.merge_requests, share);
+    if (limit <= 1 || head->n > MERGE_MAX_N) return charge;
+    off.assign({0, head->n});
+    while (!queue.empty() && batch.size() < limit) {
+      Request *q = queue.front();
+      if (q->n > MERGE_MAX_N || off.back() + q->n > MERGE_TOTAL_MAX) break;
+      off.push_back(off.back() + q->n);
+      const size_t f = merged_footprint(off);
+      if (in_use + f > cfg.budget_bytes) {
+        off.pop_back();
+        break;
+      }
+      queue.pop_front();
+      batch.push_back(q);
+      charge = f;
+    }
+    return charge;
+  }
+
   void worker(uint32_t slot) {
     cudaStream_t streams[PRIORITY_CLASSES] = {};
     if (!cfg.simulate) {
@@ -113,8 +177,15 @@ struct sa_server {
       for (int c = 0; c < PRIORITY_CLASSES; ++c)
         cudaStreamCreateWithPriority(&streams[c], cudaStreamNonBlocking, priority_of(c));
     }
+    std::vector<Request *> batch;
+    std::vector<uint64_t> off;
+    std::vector<const uint8_t *> texts;
+    std::vector<uint64_t> lens;
+    std::vector<uint32_t *> sas;
     for (;;) {
-      Request *r = nullptr;
+      size_t charge = 0;
+      uint64_t total = 0;
+      int cls = 0;
       {
         std::unique_lock<std::mutex> lk(mu);
         cv_work.wait(lk, [&] {
@@ -122,34 +193,62 @@ struct sa_server {
           return !queue.empty() && in_use + queue.front()->footprint <= cfg.budget_bytes;
         });
         if (queue.empty()) break;  // stopping and drained
-        r = queue.front();
-        queue.pop_front();
-        in_use += r->footprint;
-        ++in_flight;
+        charge = take_batch(batch, off);
+        ++busy;
+        for (Request *r : batch) {
+          total += r->n;
+          cls = std::max(cls, size_class(r->n));
+        }
+        in_use += charge;
+        in_flight += (uint32_t)batch.size();
+        stats.in_flight = in_flight;
+        ++stats.builds;
+        if (batch.size() > 1) stats.merged += batch.size();
         stats.bytes_in_use = in_use;
         if (in_use > stats.peak_bytes_in_use) stats.peak_bytes_in_use = in_use;
         if (in_flight > stats.peak_in_flight) stats.peak_in_flight = in_flight;
         stats.queued = (uint32_t)queue.size();
-        r->info.start_s = now();
-        r->info.slot = slot;
-        r->info.priority = priority_of(size_class(r->n));
+        const double t = now();
+        for (Request *r : batch) {
+          r->info.start_s = t;
+          r->info.slot = slot;
+          r->info.priority = priority_of(cls);
+          r->info.batch = (uint32_t)batch.size();
+        }
       }
       sa_status status = SA_OK;
       if (cfg.simulate) {
-        const double ns = (double)r->n * cfg.simulate_ns_per_byte;
+        const double ns = (double)total * cfg.simulate_ns_per_byte;
         std::this_thread::sleep_for(std::chrono::nanoseconds((int64_t)ns));
+      } else if (batch.size() == 1) {
+        Request *r = batch[0];
+        status = sa_build_host(r->text, r->n, r->sa, (gbsa_stream_t)streams[cls]);
       } else {
-        status = sa_build_host(r->text, r->n, r->sa, (gbsa_stream_t)streams[size_class(r->n)]);
+        texts.clear();
+        lens.clear();
+        sas.clear();
+        for (Request *r : batch) {
+          texts.push_back(r->text);
+          lens.push_back(r->n);
+          sas.push_back(r->sa);
+        }
+        status = sa_build_batched_host(texts.data(), lens.data(), sas.data(),
+                                       (uint32_t)batch.size(), (gbsa_stream_t)streams[cls]);
       }
       {
         std::lock_guard<std::mutex> lk(mu);
-        in_use -= r->footprint;
-        --in_flight;
+        in_use -= charge;
+        in_flight -= (uint32_t)batch.size();
+        --busy;
+        stats.in_flight = in_flight;
         stats.bytes_in_use = in_use;
-        ++stats.completed;
-        r->info.status = status;
-        r->info.done_s = now();
-        r->done = true;
+        stats.completed += batch.size();
+        const double t = now();
+        for (Request *r : batch) {
+          r->info.status = status;
+          r->info.done_s = t;
+          r->done = true;
+        }
       }
       cv_done.notify_all();
       cv_work.notify_all();  // memory and a slot were freed
@@ -172,6 +271,8 @@ GBSA_API sa_status sa_server_create(const sa_server_config *cfg, sa_server **out
   if (s->cfg.budget_bytes == 0) s->cfg.budget_bytes = DEFAULT_BUDGET;
   if (s->cfg.slots == 0) s->cfg.slots = DEFAULT_SLOTS;
   if (s->cfg.slots > MAX_SLOTS) s->cfg.slots = MAX_SLOTS;
+  if (s->cfg.merge_requests == 0) s->cfg.merge_requests = DEFAULT_MERGE;
+  if (s->cfg.merge_requests > MAX_MERGE) s->cfg.merge_requests = MAX_MERGE;
   s->device = s->cfg.device;
   if (!s->cfg.simulate && s->device < 0 && cudaGetDevice(&s->device) != cudaSuccess) {
     delete s;

@@ -124,6 +124,31 @@ def test_initial_keys_option_is_checked_on_the_host(lib):
         assert lib.sa_build_ex(None, 0, None, None, None, 0, ctypes.byref(opt), None, None) == 0
 
 
+def test_batched_host_build_checks_its_arguments_on_the_host(lib):
+    """sa_build_batched_host refuses malformed calls before touching the
+    device, and a batch of empty texts returns at once."""
+    vp3 = ctypes.c_void_p * 3
+    ln = (ctypes.c_uint64 * 3)(0, 0, 0)
+    texts, sas = vp3(None, None, None), vp3(None, None, None)
+    assert lib.sa_build_batched_host(texts, ln, sas, 0, None) == 1     # count = 0
+    assert lib.sa_build_batched_host(None, ln, sas, 3, None) == 1      # NULL arrays
+    assert lib.sa_build_batched_host(texts, None, sas, 3, None) == 1
+    assert lib.sa_build_batched_host(texts, ln, None, 3, None) == 1
+    assert lib.sa_build_batched_host(texts, ln, sas, 3, None) == 0     # all empty
+    assert lib.sa_build_batched_host(texts, ln, sas, (1 << 20) + 1, None) == 2
+    buf = (ctypes.c_uint8 * 8)()
+    out = (ctypes.c_uint32 * 8)()
+    ln[1] = 5
+    assert lib.sa_build_batched_host(texts, ln, sas, 3, None) == 1     # NULL non-empty text
+    texts[1], sas[1] = ctypes.addressof(buf), ctypes.addressof(out)
+    ln[2] = (1 << 31) + 1
+    assert lib.sa_build_batched_host(texts, ln, sas, 3, None) == 2     # one text too long
+    ln[0], ln[2] = 1 << 30, 1 << 30
+    texts[0] = texts[2] = ctypes.addressof(buf)
+    sas[0] = sas[2] = ctypes.addressof(out)
+    assert lib.sa_build_batched_host(texts, ln, sas, 3, None) == 2     # total above 2^31
+
+
 def test_binding_fails_loudly_without_the_library_or_a_gpu_tensor():
     """No CPU fallback: a missing library and a host tensor both raise."""
     import torch

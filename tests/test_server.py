@@ -1,7 +1,8 @@
 """Serving loop admission logic, on the host: the server in simulate mode
 does no GPU work (a request of n bytes "runs" for n * ns_per_byte), so
 these run without a GPU and check FIFO admission, the byte budget, the slot
-limit and that requests arriving during others' runs are admitted."""
+limit, that requests arriving during others' runs are admitted, and which
+queued requests a worker merges into one build."""
 import time
 
 import numpy as np
@@ -35,7 +36,8 @@ def test_footprint_model(gbsa):
 
 
 def test_fifo_order_and_slot_limit(gbsa):
-    with gbsa.Server(budget_bytes=1 << 40, slots=3, simulate_ns_per_byte=20.0) as srv:
+    with gbsa.Server(budget_bytes=1 << 40, slots=3, simulate_ns_per_byte=20.0,
+                     merge_requests=1) as srv:
         infos = run_all(srv, [100_000] * 12)
         st = srv.stats()
     starts = [i["start_s"] for i in infos]
@@ -49,7 +51,8 @@ def test_fifo_order_and_slot_limit(gbsa):
 def test_budget_limits_concurrency(gbsa):
     n = 200_000
     budget = 2 * foot(gbsa, n) + 1000  # room for two requests at a time
-    with gbsa.Server(budget_bytes=budget, slots=8, simulate_ns_per_byte=20.0) as srv:
+    with gbsa.Server(budget_bytes=budget, slots=8, simulate_ns_per_byte=20.0,
+                     merge_requests=1) as srv:
         run_all(srv, [n] * 10)
         st = srv.stats()
     assert st["peak_in_flight"] == 2
@@ -148,3 +151,119 @@ def test_smaller_requests_get_higher_stream_priority(gbsa):
                      size_priority=False) as srv:
         infos = run_all(srv, sizes)
     assert all(i["priority"] == 0 for i in infos)
+
+
+def merged_foot(g, sizes):
+    """Device bytes of one batched build of texts of these sizes (text, SA
+    and batched workspace)."""
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    N = int(off[-1])
+    a256 = lambda x: (x + 255) & ~255
+    return a256(N) + a256(4 * N) + int(g.load().sa_batched_workspace_bytes(off.ctypes.data,
+                                                                           len(sizes)))
+
+
+def queue_behind_one(srv, sizes, first=2_000_000):
+    """Submits a request that keeps the server's only slot busy (~0.2 s at
+    100 ns/byte), then `sizes` behind it; returns the infos of the queued
+    ones and of the first."""
+    first_t = srv.submit(np.zeros(first, np.uint8))
+    while srv.stats()["in_flight"] == 0:
+        time.sleep(0.001)
+    tickets = [srv.submit(np.zeros(n, np.uint8)) for n in sizes]
+    _, a = srv.wait(first_t)
+    return [srv.wait(t)[1] for t in tickets], a
+
+
+def test_merged_build_takes_the_queued_small_requests(gbsa):
+    """A worker that takes a small request also takes the small requests
+    queued directly behind it: they start and finish together and count as
+    one build; the request that ran while they queued ran alone."""
+    with gbsa.Server(budget_bytes=1 << 40, slots=1, simulate_ns_per_byte=100.0,
+                     merge_requests=32) as srv:
+        infos, a = queue_behind_one(srv, [10_000 + k for k in range(10)])
+        st = srv.stats()
+    assert a["batch"] == 1
+    assert [i["batch"] for i in infos] == [10] * 10
+    assert len({i["start_s"] for i in infos}) == 1
+    assert len({i["done_s"] for i in infos}) == 1
+    assert (st["builds"], st["merged"], st["completed"]) == (2, 10, 11)
+
+
+@pytest.mark.parametrize("limit,want", [(1, [1] * 10), (4, [4] * 8 + [2] * 2),
+                                        (0, [1] * 10), (1000, [10] * 10)])
+def test_merge_limit(gbsa, limit, want):
+    """merge_requests caps a batch (0 and 1 = no merging, the default;
+    values above 64 mean 64)."""
+    with gbsa.Server(budget_bytes=1 << 40, slots=1, simulate_ns_per_byte=100.0,
+                     merge_requests=limit) as srv:
+        infos, _ = queue_behind_one(srv, [10_000] * 10)
+        st = srv.stats()
+    assert [i["batch"] for i in infos] == want
+    assert st["builds"] == 1 + len(set((i["start_s"] for i in infos)))
+
+
+def test_merging_keeps_queue_order(gbsa):
+    """A request above 256 KiB is not merged and ends the batch in front of
+    it; the small requests behind it wait for it (queue order is kept)."""
+    sizes = [1000, 2000, 300_000, 3000, 4000]
+    with gbsa.Server(budget_bytes=1 << 40, slots=1, simulate_ns_per_byte=100.0,
+                     merge_requests=32) as srv:
+        infos, _ = queue_behind_one(srv, sizes)
+    assert [i["batch"] for i in infos] == [2, 2, 1, 2, 2]
+    starts = [i["start_s"] for i in infos]
+    assert starts == sorted(starts)
+    assert starts[0] < starts[2] < starts[3]
+
+
+def test_merged_batch_stays_within_4_mib(gbsa):
+    """A batch holds at most 4 MiB of text: 16 requests of 250,000 bytes fit,
+    a 17th does not."""
+    with gbsa.Server(budget_bytes=1 << 40, slots=1, simulate_ns_per_byte=10.0,
+                     merge_requests=64) as srv:
+        infos, _ = queue_behind_one(srv, [250_000] * 20, first=20_000_000)
+    assert [i["batch"] for i in infos] == [16] * 16 + [4] * 4
+
+
+def test_merged_batch_fits_the_budget(gbsa):
+    """A request joins a batch only while the batch's own footprint (text,
+    SA and batched workspace) fits in the budget, and that footprint is what
+    the batch holds against it."""
+    n = 100_000
+    budget = merged_foot(gbsa, [n] * 3)
+    assert merged_foot(gbsa, [n] * 4) > budget
+    with gbsa.Server(budget_bytes=budget, slots=1, simulate_ns_per_byte=1000.0,
+                     merge_requests=32) as srv:
+        infos, _ = queue_behind_one(srv, [n] * 10, first=200_000)
+        st = srv.stats()
+    assert [i["batch"] for i in infos] == [3] * 9 + [1]
+    assert st["peak_bytes_in_use"] == budget
+    assert st["bytes_in_use"] == 0
+
+
+def test_idle_workers_take_requests_unmerged(gbsa):
+    """While workers are idle, each queued request goes to a worker of its
+    own (running on its own stream at once) rather than into a batch."""
+    with gbsa.Server(budget_bytes=1 << 40, slots=4, simulate_ns_per_byte=100.0,
+                     merge_requests=32) as srv:
+        infos = run_all(srv, [10_000] * 3)
+        st = srv.stats()
+    assert [i["batch"] for i in infos] == [1, 1, 1]
+    assert (st["builds"], st["merged"]) == (3, 0)
+
+
+def test_queue_is_shared_among_the_idle_workers(gbsa):
+    """Four workers held idle by the budget (a large request fills it) wake
+    together when it ends; each takes its share of the twelve queued small
+    requests, a batch of three, instead of one worker taking all twelve."""
+    big, n = 2_000_000, 10_000
+    budget = foot(gbsa, big) + foot(gbsa, n) - 1  # no small request fits beside it
+    assert 4 * merged_foot(gbsa, [n] * 3) <= budget
+    with gbsa.Server(budget_bytes=budget, slots=4, simulate_ns_per_byte=100.0,
+                     merge_requests=32) as srv:
+        infos, a = queue_behind_one(srv, [n] * 12, first=big)
+        st = srv.stats()
+    assert a["batch"] == 1
+    assert [i["batch"] for i in infos] == [3] * 12
+    assert len({i["slot"] for i in infos}) == 4
+    assert st["builds"] == 5
