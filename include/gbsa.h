@@ -88,10 +88,11 @@ typedef struct {
   /* Tile shape of the small-group refine of rounds >= 1 (threads per block
    * x items per tile): 0 = automatic, 1 = 128 x 1024, 2 = 256 x 2048,
    * 3 = 256 x 4096, 4 = 256 x 1024. Groups of up to half a tile are refined
-   * inside one tile; larger ones take the global radix sort. */
+   * inside one tile; larger ones take the global radix sort. Any other
+   * value: SA_ERR_INVALID_ARG. */
   uint32_t refine_shape;
   /* Keys per thread of the one-sweep radix pass (tile = 256 x this):
-   * 8, 12 or 16; 0 = automatic (16). */
+   * 8, 12 or 16; 0 = automatic (16). Any other value: SA_ERR_INVALID_ARG. */
   uint32_t sort_items;
   /* When 1, CUDA events are recorded on `stream` around every kernel launch
    * and the per-kernel-class times, launch counts and algorithmic bytes are

@@ -215,7 +215,9 @@ struct PinnedStage {
         return cudaSuccess;
       }
     }
-    return cudaHostAlloc(&p, STAGE_BYTES, cudaHostAllocMapped | cudaHostAllocPortable);
+    const cudaError_t e = cudaHostAlloc(&p, STAGE_BYTES, cudaHostAllocMapped | cudaHostAllocPortable);
+    if (e != cudaSuccess) p = nullptr;  // nothing to hand back to the free list
+    return e;
   }
   ~PinnedStage() {
     if (!p) return;
@@ -1378,6 +1380,10 @@ sa_status check_offsets(const uint64_t *offsets, uint32_t count) {
 bool bad_options(const sa_options *opt) {
   if (!opt) return false;
   if (opt->multiplier != 0 && (opt->multiplier < 2 || opt->multiplier > 4)) return true;
+  if (opt->sort_items != 0 && opt->sort_items != 8 && opt->sort_items != 12 &&
+      opt->sort_items != 16)
+    return true;
+  if (opt->refine_shape > (uint32_t)REFINE_SHAPES) return true;
   return opt->initial_keys > 2;
 }
 

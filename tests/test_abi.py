@@ -124,6 +124,21 @@ def test_initial_keys_option_is_checked_on_the_host(lib):
         assert lib.sa_build_ex(None, 0, None, None, None, 0, ctypes.byref(opt), None, None) == 0
 
 
+def test_tile_options_are_checked_on_the_host(lib):
+    """sort_items outside {0, 8, 12, 16} and refine_shape above 4 are refused
+    before any GPU work, by the single and the batched build."""
+    import paper_1610_03007_gb300 as gbsa
+    off = (ctypes.c_uint64 * 3)(0, 50, 100)
+    for kw in ({"sort_items": 7}, {"sort_items": 24}, {"sort_items": 1}, {"refine_shape": 5},
+               {"refine_shape": 0xFFFFFFFF}):
+        opt = gbsa.Options(**kw)
+        assert lib.sa_build_ex(8, 100, 8, None, None, 0, ctypes.byref(opt), None, None) == 1
+        assert lib.sa_build_batched_ex(8, off, 2, 8, None, 0, ctypes.byref(opt), None, None) == 1
+    for kw in ({"sort_items": 8}, {"sort_items": 12}, {"sort_items": 16}, {"refine_shape": 4}):
+        opt = gbsa.Options(**kw)
+        assert lib.sa_build_ex(None, 0, None, None, None, 0, ctypes.byref(opt), None, None) == 0
+
+
 def test_batched_host_build_checks_its_arguments_on_the_host(lib):
     """sa_build_batched_host refuses malformed calls before touching the
     device, and a batch of empty texts returns at once."""
