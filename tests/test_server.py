@@ -267,3 +267,47 @@ def test_queue_is_shared_among_the_idle_workers(gbsa):
     assert [i["batch"] for i in infos] == [3] * 12
     assert len({i["slot"] for i in infos}) == 4
     assert st["builds"] == 5
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_mixes_keep_the_invariants(gbsa, seed):
+    """Random sizes (small and large), slots, budgets and merge limits: every
+    request completes; starts follow queue order; a batch is a run of
+    consecutive requests that started together on one worker, of at most
+    merge_requests requests, each at most 256 KiB and 4 MiB in all when
+    there are several; the budget is never exceeded and ends unused."""
+    rng = np.random.default_rng(seed)
+    count = 60
+    small = rng.integers(1, 256 << 10, count)
+    large = rng.integers((256 << 10) + 1, 3 << 20, count)
+    sizes = np.where(rng.random(count) < 0.7, small, large)
+    slots = int(rng.integers(1, 7))
+    limit = int(rng.choice([1, 2, 5, 32, 64]))
+    budget = int(foot(gbsa, int(sizes.max())) * rng.uniform(1.0, 4.0))
+    with gbsa.Server(budget_bytes=budget, slots=slots, simulate_ns_per_byte=2.0,
+                     merge_requests=limit) as srv:
+        tickets = []
+        for n in sizes:
+            tickets.append(srv.submit(np.zeros(int(n), np.uint8)))
+            if rng.random() < 0.2:
+                time.sleep(0.002)
+        infos = [srv.wait(t)[1] for t in tickets]
+        st = srv.stats()
+    assert st["completed"] == count and st["bytes_in_use"] == 0 and st["in_flight"] == 0
+    assert st["peak_bytes_in_use"] <= budget
+    assert all(i["status"] == 0 for i in infos)
+    starts = [i["start_s"] for i in infos]
+    assert starts == sorted(starts)
+    k, builds = 0, 0
+    while k < count:
+        b = infos[k]["batch"]
+        group = infos[k:k + b]
+        assert len(group) == b and b <= max(limit, 1)
+        assert len({(i["slot"], i["start_s"], i["done_s"], i["batch"]) for i in group}) == 1
+        if b > 1:
+            assert all(int(sizes[j]) <= 256 << 10 for j in range(k, k + b))
+            assert int(sizes[k:k + b].sum()) <= 4 << 20
+        k += b
+        builds += 1
+    assert st["builds"] == builds
+    assert st["merged"] == sum(1 for i in infos if i["batch"] > 1)
