@@ -263,6 +263,41 @@ def _dev_u8(t):
     return t.contiguous()
 
 
+def _dev_buf(x, name: str, device, itemsize: int, at_least: int):
+    """x, if it is a contiguous CUDA tensor on `device` holding at least
+    `at_least` elements of `itemsize` bytes: the library reads or writes that
+    many elements from the first one, so any other buffer could take a
+    kernel past its end."""
+    torch = _torch()
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.device == device
+            and x.is_contiguous() and x.element_size() == itemsize and x.numel() >= at_least):
+        raise ValueError(f"{name} must be a contiguous CUDA tensor on {device} with at least "
+                         f"{at_least} elements of {itemsize} bytes")
+    return x
+
+
+def _dev_ws(x, device):
+    """(pointer, bytes) of a caller's workspace, a contiguous CUDA tensor on
+    `device` (the library checks the size); (None, 0) for None."""
+    torch = _torch()
+    if x is None:
+        return None, 0
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.device == device
+            and x.is_contiguous()):
+        raise ValueError(f"workspace must be a contiguous CUDA tensor on {device}")
+    return x.data_ptr(), x.numel() * x.element_size()
+
+
+def _host_out(x, n: int, name: str):
+    """x, if it is a writable C-contiguous numpy array of n elements of 4
+    bytes (the library writes n uint32 from its first one)."""
+    if not (isinstance(x, np.ndarray) and x.itemsize == 4 and x.size == n
+            and x.flags.c_contiguous and x.flags.writeable):
+        raise ValueError(f"{name} must be a writable C-contiguous numpy array of {n} "
+                         "4-byte elements")
+    return x
+
+
 def workspace_bytes(n: int) -> int:
     return int(load().sa_workspace_bytes(n))
 
@@ -275,6 +310,7 @@ def sa_build(text, sa_out=None, stream=None):
     n = t.numel()
     if sa_out is None:
         sa_out = torch.empty(n, dtype=torch.int32, device=t.device)
+    _dev_buf(sa_out, "sa_out", t.device, 4, n)
     _check(lib.sa_build(t.data_ptr(), n, sa_out.data_ptr() if n else None, _stream(stream)),
            "sa_build")
     return sa_out
@@ -302,6 +338,7 @@ def sa_build_ex(text, *, isa=False, workspace=None, h0_chars=0, spin_limit=0,
     wsb = int(lib.sa_workspace_bytes(n))
     if workspace is None:
         workspace = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    ws_ptr, ws_bytes = _dev_ws(workspace, dev)
     trace = torch.zeros((trace_cap, n), dtype=torch.int32, device=dev) if trace_cap else None
     opt = Options(h0_chars, spin_limit, inject_stall,
                   trace.data_ptr() if trace is not None and n else None, trace_cap,
@@ -310,7 +347,7 @@ def sa_build_ex(text, *, isa=False, workspace=None, h0_chars=0, spin_limit=0,
     st = Stats()
     rc = lib.sa_build_ex(t.data_ptr(), n, sa.data_ptr() if n else None,
                          isa_t.data_ptr() if isa_t is not None and n else None,
-                         workspace.data_ptr(), workspace.numel(), ctypes.byref(opt),
+                         ws_ptr, ws_bytes, ctypes.byref(opt),
                          ctypes.byref(st), _stream(stream))
     _check(rc, "sa_build_ex")
     return sa, isa_t, st.to_dict(), trace
@@ -332,16 +369,16 @@ def sa_build_batched(texts, offsets, sa_out=None, workspace=None, stream=None, s
     N = int(off[-1]) if count >= 0 else 0
     if sa_out is None:
         sa_out = torch.empty(N, dtype=torch.int32, device=t.device)
+    _dev_buf(sa_out, "sa_out", t.device, 4, N)
     wsb = int(lib.sa_batched_workspace_bytes(off.ctypes.data, count))
     if workspace is None and N:
         workspace = torch.empty(wsb, dtype=torch.uint8, device=t.device)
+    ws_ptr, ws_bytes = _dev_ws(workspace, t.device)
     st = Stats()
     opt = Options(h0_chars, 0, 0, None, 0, 0, refine_shape, sort_items, 1 if profile else 0,
                   multiplier, bucket_min, device_rounds, group_order)
     rc = lib.sa_build_batched_ex(t.data_ptr(), off.ctypes.data, count,
-                                 sa_out.data_ptr() if N else None,
-                                 workspace.data_ptr() if workspace is not None else None,
-                                 workspace.numel() if workspace is not None else 0,
+                                 sa_out.data_ptr() if N else None, ws_ptr, ws_bytes,
                                  ctypes.byref(opt), ctypes.byref(st), _stream(stream))
     _check(rc, "sa_build_batched")
     return (sa_out, st.to_dict()) if stats else sa_out
@@ -353,6 +390,7 @@ def sa_build_host(text: np.ndarray, sa_out: np.ndarray | None = None, stream=Non
     a = np.ascontiguousarray(text, dtype=np.uint8)
     if sa_out is None:
         sa_out = np.empty(a.size, dtype=np.uint32)
+    _host_out(sa_out, a.size, "sa_out")
     _check(lib.sa_build_host(a.ctypes.data, a.size, sa_out.ctypes.data, _stream(stream)),
            "sa_build_host")
     return sa_out
@@ -373,7 +411,10 @@ def sa_build_batched_host(texts, outs=None, stream=None) -> list:
     if outs is None:
         outs = [np.empty(a.size, dtype=np.uint32) for a in arrs]
     count = len(arrs)
-    assert len(outs) == count
+    if len(outs) != count:
+        raise ValueError("one output array per text")
+    for k, (a, o) in enumerate(zip(arrs, outs)):
+        _host_out(o, a.size, f"outs[{k}]")
     tp = (ctypes.c_void_p * max(count, 1))(*[a.ctypes.data if a.size else None for a in arrs])
     sp = (ctypes.c_void_p * max(count, 1))(*[o.ctypes.data if o.size else None for o in outs])
     ln = (ctypes.c_uint64 * max(count, 1))(*[a.size for a in arrs])
@@ -386,15 +427,19 @@ def sa_sort_pairs(keys, vals, begin_bit=0, end_bit=64, workspace=None, stream=No
     uint32) CUDA tensors by key bits [begin_bit, end_bit)."""
     torch = _torch()
     lib = load()
+    if not (isinstance(keys, torch.Tensor) and keys.is_cuda):
+        raise ValueError("keys must be a CUDA tensor")
     m = keys.numel()
-    assert vals.numel() == m and keys.is_cuda and vals.is_cuda
+    _dev_buf(keys, "keys", keys.device, 8, m)
+    _dev_buf(vals, "vals", keys.device, 4, m)
+    if vals.numel() != m:
+        raise ValueError("keys and vals must have the same length")
     if workspace is None and m > 1:
         workspace = torch.empty(int(lib.sa_sort_workspace_bytes(m)), dtype=torch.uint8,
                                 device=keys.device)
+    ws_ptr, ws_bytes = _dev_ws(workspace, keys.device)
     _check(lib.sa_sort_pairs(keys.data_ptr(), vals.data_ptr(), m, begin_bit, end_bit,
-                             workspace.data_ptr() if workspace is not None else None,
-                             workspace.numel() if workspace is not None else 0,
-                             _stream(stream)), "sa_sort_pairs")
+                             ws_ptr, ws_bytes, _stream(stream)), "sa_sort_pairs")
     return keys, vals
 
 
@@ -406,7 +451,7 @@ def sa_bwt(text, sa, stream=None):
     lib = load()
     t = _dev_u8(text)
     n = t.numel()
-    assert sa.numel() == n and sa.is_cuda
+    _dev_buf(sa, "sa", t.device, 4, n)
     bwt = torch.empty(n + 1, dtype=torch.uint8, device=t.device)
     prim = torch.zeros(1, dtype=torch.int64, device=t.device)
     _check(lib.sa_bwt(t.data_ptr() if n else None, n, sa.data_ptr() if n else None,
@@ -479,15 +524,14 @@ def sa_lcp(text, sa, workspace=None, stream=None):
     lib = load()
     t = _dev_u8(text)
     n = t.numel()
-    assert sa.numel() == n and sa.is_cuda
+    _dev_buf(sa, "sa", t.device, 4, n)
     lcp = torch.empty(n, dtype=torch.int32, device=t.device)
     if n and workspace is None:
         workspace = torch.empty(int(lib.sa_lcp_workspace_bytes(n)), dtype=torch.uint8,
                                 device=t.device)
+    ws_ptr, ws_bytes = _dev_ws(workspace, t.device)
     _check(lib.sa_lcp(t.data_ptr() if n else None, n, sa.data_ptr() if n else None,
-                      lcp.data_ptr() if n else None,
-                      workspace.data_ptr() if workspace is not None else None,
-                      workspace.numel() if workspace is not None else 0, _stream(stream)),
+                      lcp.data_ptr() if n else None, ws_ptr, ws_bytes, _stream(stream)),
            "sa_lcp")
     return lcp
 
@@ -523,6 +567,7 @@ class Server:
         a = np.ascontiguousarray(text, dtype=np.uint8)
         if out is None:
             out = np.empty(a.size, dtype=np.uint32)
+        _host_out(out, a.size, "out")
         t = ctypes.c_uint64()
         _check(self._lib.sa_server_submit(self._h, a.ctypes.data, a.size, out.ctypes.data,
                                           ctypes.byref(t)), "sa_server_submit")

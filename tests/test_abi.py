@@ -186,3 +186,42 @@ def test_no_alloc_limit_matches_its_scratch_array(lib):
     assert lib.sa_workspace_bytes((1 << 18) + 4096) > lib.sa_workspace_bytes(1 << 18)
     assert lib.sa_build_noalloc(None, (1 << 18) + 1, None, None) == 2
     assert lib.sa_pool_usage(None, None) == 1
+
+
+def test_binding_refuses_buffers_the_library_could_overrun():
+    """The binding checks every caller-provided buffer before a call: output
+    arrays of the wrong element size, length or layout, read-only arrays and
+    non-CUDA tensors are refused with ValueError, so no kernel or copy can
+    run past a buffer."""
+    import torch
+
+    import paper_1610_03007_gb300 as gbsa
+    text = np.frombuffer(b"mississippi", dtype=np.uint8)
+    good = np.empty(text.size, np.uint32)
+    assert gbsa._host_out(good, text.size, "out") is good
+    bad = [np.empty(text.size, np.uint64), np.empty(text.size - 1, np.uint32),
+           np.empty(2 * text.size, np.uint32)[::2]]
+    ro = np.empty(text.size, np.uint32)
+    ro.flags.writeable = False
+    bad.append(ro)
+    for b in bad:
+        with pytest.raises(ValueError):
+            gbsa._host_out(b, text.size, "out")
+        with pytest.raises(ValueError):
+            gbsa.sa_build_host(text, sa_out=b)
+        with pytest.raises(ValueError):
+            gbsa.sa_build_batched_host([text], [b])
+    with pytest.raises(ValueError):
+        gbsa.sa_build_batched_host([text, text], [good])
+    with gbsa.Server(budget_bytes=1 << 30, slots=1, simulate_ns_per_byte=1.0) as srv:
+        for b in bad:
+            with pytest.raises(ValueError):
+                srv.submit(text, out=b)
+    cpu = torch.zeros(16, dtype=torch.int32)
+    with pytest.raises(ValueError):
+        gbsa._dev_buf(cpu, "sa_out", torch.device("cuda:0"), 4, 16)
+    with pytest.raises(ValueError):
+        gbsa._dev_ws(cpu, torch.device("cuda:0"))
+    assert gbsa._dev_ws(None, torch.device("cuda:0")) == (None, 0)
+    with pytest.raises(ValueError):
+        gbsa.sa_sort_pairs(torch.zeros(8, dtype=torch.int64), torch.zeros(8, dtype=torch.int32))
